@@ -1,0 +1,215 @@
+/*
+ * bamg.h - C ABI of the blocked smoothed-aggregation AMG reuse phase on one GPU.
+ *
+ * The library implements the two recurring phases of a smoothed-aggregation
+ * AMG solve whose hierarchy is reused across solves (arxiv 2606.24748,
+ * Sec. 3.1): the numeric Galerkin recompute A_c = P^T A P on rectangular-block
+ * matrices, and the V-cycle under CG whose smoother is point-block Jacobi
+ * (Sec. 4.1) under Chebyshev acceleration.  Operators are assembled through
+ * blocked COO (Sec. 3.4, Sec. 5).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named "device" point to CUDA device memory of the device that
+ *    was current when the context was created; they are borrowed for the call
+ *    only (the call is stream ordered: the caller keeps them alive until the
+ *    stream reaches the work).  Pointers named "host" are read before return.
+ *  - Block values are row-major bs_r x bs_c blocks (element (r, c) at
+ *    r * bs_c + c).  Vectors are dof-ordered: dof = block * bs + component.
+ *  - Every call returns a bamg_status; on failure bamg_last_error() holds a
+ *    one-line description.  No C++ exception crosses this ABI and no kernel
+ *    traps: errors detected on the device (non-finite values, exhausted
+ *    waits) are recorded in a device error word and returned by the next call
+ *    that synchronizes (bamg_ctx_sync, bamg_cg_solve).
+ *  - The library allocates its own device memory (matrices, plans, the
+ *    hierarchy and work vectors) during the setup calls: bsr_create,
+ *    coo_preallocate, ptap_symbolic, mg_setup.  The recurring calls
+ *    (coo_set_values, ptap_numeric, mg_update, vcycle, cg_solve, spmv, spmm)
+ *    allocate nothing.
+ *  - Indices are int32 block indices; counts are int64.
+ */
+#ifndef BAMG_H
+#define BAMG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BAMG_API __attribute__((visibility("default")))
+#else
+#define BAMG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BAMG_OK = 0,
+  BAMG_ERR_INVALID = 1,        /* bad argument or size; nothing was launched */
+  BAMG_ERR_OOM = 2,            /* device allocation failed */
+  BAMG_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  BAMG_ERR_STATE = 4,          /* object used before the call that prepares it */
+  BAMG_ERR_NAN = 5,            /* a non-finite value was produced */
+  BAMG_ERR_BREAKDOWN = 6,      /* CG breakdown (p^T A p <= 0) or a non-SPD block */
+  BAMG_ERR_NOT_CONVERGED = 7,  /* CG reached maxit */
+  BAMG_ERR_TIMEOUT = 8         /* a bounded device wait ran out */
+} bamg_status;
+
+typedef enum { BAMG_FP64 = 0, BAMG_FP32 = 1 } bamg_prec;
+
+typedef struct bamg_ctx bamg_ctx;
+typedef struct bamg_bsr bamg_bsr;
+typedef struct bamg_ptap bamg_ptap;
+typedef struct bamg_mg bamg_mg;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t, borrowed, e.g. torch.cuda.current_stream().cuda_stream;
+ * NULL = the legacy default stream).  All work of objects made from this
+ * context is issued on that stream. */
+BAMG_API bamg_status bamg_ctx_create(void* cuda_stream, bamg_ctx** out);
+BAMG_API bamg_status bamg_ctx_destroy(bamg_ctx* ctx);
+/* Message of the last failed call on this context ("" if none).  Owned by
+ * the context, valid until the next call. */
+BAMG_API const char* bamg_last_error(const bamg_ctx* ctx);
+/* Wait for the context's stream, then turn the device error word into a
+ * status (and clear it). */
+BAMG_API bamg_status bamg_ctx_sync(bamg_ctx* ctx);
+
+/* ------------------------------------------------------- block matrices */
+
+/* Rectangular-block sparse matrix (Sec. 2.3: independent row and column block
+ * sizes; 3x3 fine operator, 3x6 prolongator, 6x6 coarse operators), nbr x nbc
+ * blocks of bs_r x bs_c, 1 <= bs_r, bs_c <= 8.  Empty until a pattern is set
+ * by bamg_bsr_coo_preallocate or produced by bamg_ptap_symbolic. */
+BAMG_API bamg_status bamg_bsr_create(bamg_ctx* ctx, int bs_r, int bs_c, int64_t nbr, int64_t nbc,
+                            bamg_bsr** out);
+BAMG_API bamg_status bamg_bsr_destroy(bamg_bsr* A);
+
+/* Blocked COO preallocation (Sec. 3.4, Sec. 5): declare the block
+ * coordinates of n contributions, bi[k] in [0, nbr), bj[k] in [0, nbc)
+ * (device int32 arrays of length n).  Duplicates are allowed and are summed
+ * by set_values; a contribution with bi[k] < 0 or bj[k] < 0 is ignored.
+ * Builds the block pattern (rows sorted by column) and the cached
+ * duplicate-summation plan.  BAMG_ERR_INVALID if an index is >= nbr / nbc
+ * (checked on the device before the pattern is built). */
+BAMG_API bamg_status bamg_bsr_coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi,
+                                     const int32_t* bj);
+/* Numeric blocked COO assembly (Sec. 5): v is a device array of n row-major
+ * bs_r*bs_c blocks in the order given to preallocate.  add = 0: each stored
+ * block becomes the sum of its contributions; add = 1: the sum is added.
+ * Deterministic (fixed summation order).  Increments the matrix version. */
+BAMG_API bamg_status bamg_bsr_coo_set_values(bamg_bsr* A, const double* v, int add);
+
+/* Sizes and version (any pointer may be NULL). */
+BAMG_API bamg_status bamg_bsr_info(const bamg_bsr* A, int* bs_r, int* bs_c, int64_t* nbr, int64_t* nbc,
+                          int64_t* nnzb, uint64_t* version);
+/* Copy the block pattern out: rowptr (nbr + 1) and colidx (nnzb), device. */
+BAMG_API bamg_status bamg_bsr_get_pattern(const bamg_bsr* A, int32_t* rowptr, int32_t* colidx);
+/* Copy the values out in pattern order: nnzb row-major blocks, device. */
+BAMG_API bamg_status bamg_bsr_get_values(const bamg_bsr* A, double* vals);
+/* Declare A symmetric (A = A^T); Galerkin products with A then compute the
+ * upper block triangle and mirror it.  The caller guarantees symmetry. */
+BAMG_API bamg_status bamg_bsr_set_symmetric(bamg_bsr* A, int symmetric);
+
+/* Blocked SpMV (Sec. 4.2): y = A x (transpose = 0, x has nbc*bs_c entries,
+ * y nbr*bs_r), device vectors of the given precision.  BAMG_FP32 computes
+ * with a float copy of the values, refreshed when the version changed.
+ * transpose = 1 is not supported (BAMG_ERR_INVALID): transposes are formed
+ * explicitly (the hierarchy caches R = P^T). */
+BAMG_API bamg_status bamg_bsr_spmv(bamg_bsr* A, const void* x, void* y, bamg_prec prec, int transpose);
+/* Multi-right-hand-side blocked product Y = A X for k right-hand sides
+ * (1 <= k <= 32), right-hand-side-minor layout: X[dof * k + j]. */
+BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, bamg_prec prec);
+
+/* ----------------------------------------------------- Galerkin product */
+
+/* Symbolic Galerkin product (Sec. 3.1, Sec. 3.5): A (n x n blocks of
+ * bs x bs) and P (n x nc blocks of bs x bs_p) must have patterns.  Creates the
+ * coarse matrix Ac (nc x nc blocks of bs_p x bs_p) with the structural
+ * pattern of P^T A P (every stored block counts, no value-based pruning) and
+ * a plan holding the intermediate pattern and the gather lists that the
+ * numeric phase reuses.  Ac is owned by the caller (bamg_bsr_destroy). */
+BAMG_API bamg_status bamg_ptap_symbolic(bamg_bsr* A, bamg_bsr* P, bamg_ptap** plan, bamg_bsr** Ac);
+/* Numeric Galerkin recompute with the reused pattern (Sec. 3.1 "hot PtAP",
+ * Sec. 3.5): Ac = P^T A P in FP64.  The plan caches a gather-friendly copy of
+ * P and rebuilds it only when P's version changed (state gate, Sec. 3.5).
+ * Increments Ac's version.  BAMG_ERR_STATE if A, P or Ac are not the
+ * matrices (patterns) the plan was built for. */
+BAMG_API bamg_status bamg_ptap_numeric(bamg_ptap* plan, bamg_bsr* A, bamg_bsr* P, bamg_bsr* Ac);
+/* Same product in the given precision; BAMG_FP32 writes only the float copy
+ * of Ac (used by FP32 V-cycles). */
+BAMG_API bamg_status bamg_ptap_numeric_prec(bamg_ptap* plan, bamg_bsr* A, bamg_bsr* P, bamg_bsr* Ac,
+                                   bamg_prec prec);
+BAMG_API bamg_status bamg_ptap_destroy(bamg_ptap* plan);
+
+/* ------------------------------------------------------------ multigrid */
+
+typedef struct {
+  int max_levels;           /* depth limit, >= 1 (default 10) */
+  int64_t max_coarse_dofs;  /* coarsen while a level has more dofs (default 2100) */
+  int grid[3];              /* fine node grid for geometric aggregates, x fastest;
+                               required (> 0) by bamg_mg_setup */
+  int cheb_degree;          /* Chebyshev steps per smoothing (default 2) */
+  double cheb_lower;        /* interval [lower, upper] * lambda_max (0.1, 1.1) */
+  double cheb_upper;
+  int power_its;            /* power iterations of the eigen-estimate (15) */
+  int precision;            /* bamg_prec of the V-cycle: FP64, or FP32 = mixed form
+                               (FP32 operators, smoother and vectors; FP64 CG,
+                               eigen-estimates and coarsest solve) */
+} bamg_mg_opts;
+
+typedef struct {
+  int iterations;     /* CG iterations taken */
+  int converged;      /* 1 if ||r|| <= rtol ||b|| */
+  double rnorm;       /* final recursive residual norm */
+  double bnorm;       /* ||b|| */
+  double true_rnorm;  /* ||b - A x|| recomputed at exit */
+} bamg_cg_info;
+
+BAMG_API void bamg_mg_opts_default(bamg_mg_opts* opts);
+
+/* Cold setup (Sec. 2.2, Sec. 3.2): A is the assembled fine operator (3x3
+ * blocks); coords (host, nbr x 3 doubles) and dirichlet (host, nbr bytes,
+ * 1 = clamped node) give the rigid-body near-null space.  Aggregates are
+ * cubes of 3x3x3 nodes of opts->grid (a remainder joins the last aggregate),
+ * the tentative prolongator is the per-aggregate QR of the rigid-body modes,
+ * the prolongator is smoothed by one damped-Jacobi step with
+ * omega = 4 / (3 lambda_max(D^-1 A)), coarse operators are Galerkin
+ * products; then bamg_mg_update runs once.  A stays owned by the caller and
+ * must outlive the hierarchy. */
+BAMG_API bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords,
+                          const uint8_t* dirichlet, const bamg_mg_opts* opts, bamg_mg** out);
+/* Hot reuse step (Sec. 3.1): with the prolongators fixed, recompute every
+ * Galerkin product from the current values of A, then the smoother data
+ * (block-diagonal inverses, eigen-estimates) and the coarsest factor. */
+BAMG_API bamg_status bamg_mg_update(bamg_mg* mg);
+/* One V-cycle x = M b from x = 0 (Sec. 2.1): FP64 device vectors of the fine
+ * size, in either precision form. */
+BAMG_API bamg_status bamg_vcycle(bamg_mg* mg, const double* b, double* x);
+/* Preconditioned CG (Sec. 4.1) on the fine operator, x0 = 0, stops when the
+ * unpreconditioned residual ||r|| <= rtol ||b||.  FP64 device vectors.
+ * Synchronizes once at exit to fill info (may be NULL).  Returns
+ * BAMG_ERR_NOT_CONVERGED after maxit iterations, BAMG_ERR_BREAKDOWN if
+ * p^T A p <= 0. */
+BAMG_API bamg_status bamg_cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit,
+                          bamg_cg_info* info);
+/* Per-block-row smoother weights of a level (device float array of the
+ * level's block-row count) scaling each row of the Chebyshev update;
+ * w = NULL restores the plain smoother. */
+BAMG_API bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w);
+/* Inspection: number of levels; a level's operator and prolongator (P is
+ * NULL on the coarsest level); its eigen-estimate and prolongator damping
+ * factor; its block-diagonal inverse (device, nbr row-major bs x bs blocks). */
+BAMG_API bamg_status bamg_mg_num_levels(const bamg_mg* mg, int* n);
+BAMG_API bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** A, bamg_bsr** P);
+BAMG_API bamg_status bamg_mg_get_level_scalars(const bamg_mg* mg, int level, double* lambda_max,
+                                      double* omega);
+BAMG_API bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* dinv);
+BAMG_API bamg_status bamg_mg_destroy(bamg_mg* mg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BAMG_H */

@@ -1,0 +1,272 @@
+"""Thin Python binding of libbamg (the C ABI declared in include/bamg.h).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: device buffers are passed as torch CUDA tensors (their
+data pointers), host buffers as numpy arrays, and handles as opaque
+ctypes pointers.  A non-zero status raises :class:`BamgError` with the
+library's last-error message.  All compute runs in the CUDA library; there is
+no fallback: if libbamg.so is missing or cannot be loaded, importing the
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbamg.so")
+
+BAMG_OK = 0
+STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG_ERR_CUDA", 4: "BAMG_ERR_STATE",
+                5: "BAMG_ERR_NAN", 6: "BAMG_ERR_BREAKDOWN", 7: "BAMG_ERR_NOT_CONVERGED", 8: "BAMG_ERR_TIMEOUT"}
+BAMG_FP64 = 0
+BAMG_FP32 = 1
+
+
+class BamgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class bamg_mg_opts(ctypes.Structure):
+    _fields_ = [("max_levels", ctypes.c_int), ("max_coarse_dofs", ctypes.c_int64),
+                ("grid", ctypes.c_int * 3), ("cheb_degree", ctypes.c_int),
+                ("cheb_lower", ctypes.c_double), ("cheb_upper", ctypes.c_double),
+                ("power_its", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class bamg_cg_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rnorm", ctypes.c_double),
+                ("bnorm", ctypes.c_double), ("true_rnorm", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_I64 = ctypes.c_int64
+_SIGS = {
+    "bamg_ctx_create": [_P, _PP],
+    "bamg_ctx_destroy": [_P],
+    "bamg_ctx_sync": [_P],
+    "bamg_bsr_create": [_P, ctypes.c_int, ctypes.c_int, _I64, _I64, _PP],
+    "bamg_bsr_destroy": [_P],
+    "bamg_bsr_coo_preallocate": [_P, _I64, _P, _P],
+    "bamg_bsr_coo_set_values": [_P, _P, ctypes.c_int],
+    "bamg_bsr_info": [_P, _P, _P, _P, _P, _P, _P],
+    "bamg_bsr_get_pattern": [_P, _P, _P],
+    "bamg_bsr_get_values": [_P, _P],
+    "bamg_bsr_set_symmetric": [_P, ctypes.c_int],
+    "bamg_bsr_spmv": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
+    "bamg_bsr_spmm": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
+    "bamg_ptap_symbolic": [_P, _P, _PP, _PP],
+    "bamg_ptap_numeric": [_P, _P, _P, _P],
+    "bamg_ptap_numeric_prec": [_P, _P, _P, _P, ctypes.c_int],
+    "bamg_ptap_destroy": [_P],
+    "bamg_mg_setup": [_P, _P, _P, _P, ctypes.POINTER(bamg_mg_opts), _PP],
+    "bamg_mg_update": [_P],
+    "bamg_vcycle": [_P, _P, _P],
+    "bamg_cg_solve": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
+    "bamg_mg_set_smoother_weights": [_P, ctypes.c_int, _P],
+    "bamg_mg_num_levels": [_P, ctypes.POINTER(ctypes.c_int)],
+    "bamg_mg_get_level": [_P, ctypes.c_int, _PP, _PP],
+    "bamg_mg_get_level_scalars": [_P, ctypes.c_int, _P, _P],
+    "bamg_mg_get_dinv": [_P, ctypes.c_int, _P],
+    "bamg_mg_destroy": [_P],
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbamg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libbamg.so not found at {LIB_PATH}: run paper_2606_24748_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.bamg_last_error.argtypes = [_P]
+        L.bamg_last_error.restype = ctypes.c_char_p
+        L.bamg_mg_opts_default.argtypes = [ctypes.POINTER(bamg_mg_opts)]
+        L.bamg_mg_opts_default.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _check(status: int, ctx) -> None:
+    if status != BAMG_OK:
+        msg = lib().bamg_last_error(ctx).decode() if ctx else ""
+        raise BamgError(status, msg)
+
+
+# ------------------------------------------------------------------ context
+def bamg_ctx_create(stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default)."""
+    s = getattr(stream, "cuda_stream", stream)
+    h = ctypes.c_void_p()
+    _check(lib().bamg_ctx_create(s, ctypes.byref(h)), None)
+    return h
+
+
+def bamg_ctx_destroy(ctx):
+    _check(lib().bamg_ctx_destroy(ctx), None)
+
+
+def bamg_last_error(ctx) -> str:
+    return lib().bamg_last_error(ctx).decode()
+
+
+def bamg_ctx_sync(ctx):
+    _check(lib().bamg_ctx_sync(ctx), ctx)
+
+
+# ---------------------------------------------------------- block matrices
+def bamg_bsr_create(ctx, bs_r: int, bs_c: int, nbr: int, nbc: int):
+    h = ctypes.c_void_p()
+    _check(lib().bamg_bsr_create(ctx, bs_r, bs_c, nbr, nbc, ctypes.byref(h)), ctx)
+    return h
+
+
+def bamg_bsr_destroy(A):
+    _check(lib().bamg_bsr_destroy(A), None)
+
+
+def bamg_bsr_coo_preallocate(ctx, A, bi, bj):
+    """bi, bj: int32 CUDA tensors of block coordinates."""
+    _check(lib().bamg_bsr_coo_preallocate(A, int(bi.numel()), _ptr(bi), _ptr(bj)), ctx)
+
+
+def bamg_bsr_coo_set_values(ctx, A, v, add: int = 0):
+    """v: float64 CUDA tensor of n row-major blocks."""
+    _check(lib().bamg_bsr_coo_set_values(A, _ptr(v), int(add)), ctx)
+
+
+def bamg_bsr_info(A) -> dict:
+    bs_r, bs_c = ctypes.c_int(), ctypes.c_int()
+    nbr, nbc, nnzb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    ver = ctypes.c_uint64()
+    _check(lib().bamg_bsr_info(A, ctypes.byref(bs_r), ctypes.byref(bs_c), ctypes.byref(nbr), ctypes.byref(nbc),
+                               ctypes.byref(nnzb), ctypes.byref(ver)), None)
+    return {"bs_r": bs_r.value, "bs_c": bs_c.value, "nbr": nbr.value, "nbc": nbc.value, "nnzb": nnzb.value,
+            "version": ver.value}
+
+
+def bamg_bsr_get_pattern(ctx, A, rowptr, colidx):
+    _check(lib().bamg_bsr_get_pattern(A, _ptr(rowptr), _ptr(colidx)), ctx)
+
+
+def bamg_bsr_get_values(ctx, A, vals):
+    _check(lib().bamg_bsr_get_values(A, _ptr(vals)), ctx)
+
+
+def bamg_bsr_set_symmetric(ctx, A, symmetric: int):
+    _check(lib().bamg_bsr_set_symmetric(A, int(symmetric)), ctx)
+
+
+def bamg_bsr_spmv(ctx, A, x, y, prec: int = BAMG_FP64, transpose: int = 0):
+    _check(lib().bamg_bsr_spmv(A, _ptr(x), _ptr(y), int(prec), int(transpose)), ctx)
+
+
+def bamg_bsr_spmm(ctx, A, X, Y, k: int, prec: int = BAMG_FP64):
+    _check(lib().bamg_bsr_spmm(A, _ptr(X), _ptr(Y), int(k), int(prec)), ctx)
+
+
+# ------------------------------------------------------------ Galerkin
+def bamg_ptap_symbolic(ctx, A, P):
+    plan, Ac = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().bamg_ptap_symbolic(A, P, ctypes.byref(plan), ctypes.byref(Ac)), ctx)
+    return plan, Ac
+
+
+def bamg_ptap_numeric(ctx, plan, A, P, Ac):
+    _check(lib().bamg_ptap_numeric(plan, A, P, Ac), ctx)
+
+
+def bamg_ptap_numeric_prec(ctx, plan, A, P, Ac, prec: int):
+    _check(lib().bamg_ptap_numeric_prec(plan, A, P, Ac, int(prec)), ctx)
+
+
+def bamg_ptap_destroy(plan):
+    _check(lib().bamg_ptap_destroy(plan), None)
+
+
+# ------------------------------------------------------------ multigrid
+def bamg_mg_opts_default() -> bamg_mg_opts:
+    o = bamg_mg_opts()
+    lib().bamg_mg_opts_default(ctypes.byref(o))
+    return o
+
+
+def bamg_mg_setup(ctx, A, coords: np.ndarray, dirichlet: np.ndarray, opts: bamg_mg_opts):
+    c = np.ascontiguousarray(coords, dtype=np.float64)
+    d = np.ascontiguousarray(dirichlet, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib().bamg_mg_setup(ctx, A, c.ctypes.data, d.ctypes.data, ctypes.byref(opts), ctypes.byref(h)), ctx)
+    return h
+
+
+def bamg_mg_update(ctx, mg):
+    _check(lib().bamg_mg_update(mg), ctx)
+
+
+def bamg_vcycle(ctx, mg, b, x):
+    _check(lib().bamg_vcycle(mg, _ptr(b), _ptr(x)), ctx)
+
+
+def bamg_cg_solve(ctx, mg, b, x, rtol: float, maxit: int, check: bool = True) -> dict:
+    info = bamg_cg_info()
+    st = lib().bamg_cg_solve(mg, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(info))
+    out = {"status": st, "iterations": info.iterations, "converged": bool(info.converged),
+           "rnorm": info.rnorm, "bnorm": info.bnorm, "true_rnorm": info.true_rnorm}
+    if check:
+        _check(st, ctx)
+    return out
+
+
+def bamg_mg_set_smoother_weights(ctx, mg, level: int, w):
+    _check(lib().bamg_mg_set_smoother_weights(mg, int(level), _ptr(w)), ctx)
+
+
+def bamg_mg_num_levels(mg) -> int:
+    n = ctypes.c_int()
+    _check(lib().bamg_mg_num_levels(mg, ctypes.byref(n)), None)
+    return n.value
+
+
+def bamg_mg_get_level(mg, level: int):
+    A, P = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().bamg_mg_get_level(mg, int(level), ctypes.byref(A), ctypes.byref(P)), None)
+    return A, (P if P.value else None)
+
+
+def bamg_mg_get_level_scalars(ctx, mg, level: int) -> tuple[float, float]:
+    lam, om = ctypes.c_double(), ctypes.c_double()
+    _check(lib().bamg_mg_get_level_scalars(mg, int(level), ctypes.byref(lam), ctypes.byref(om)), ctx)
+    return lam.value, om.value
+
+
+def bamg_mg_get_dinv(ctx, mg, level: int, out):
+    _check(lib().bamg_mg_get_dinv(mg, int(level), _ptr(out)), ctx)
+
+
+def bamg_mg_destroy(mg):
+    _check(lib().bamg_mg_destroy(mg), None)
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding declares."""
+    return sorted(list(_SIGS) + ["bamg_last_error", "bamg_mg_opts_default"])

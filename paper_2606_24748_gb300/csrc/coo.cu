@@ -1,0 +1,186 @@
+// Blocked COO assembly (Sec. 3.4, Sec. 5): block coordinates declared once,
+// duplicates summed by a cached plan, one gather-sum kernel per numeric
+// assembly writing straight into the sliced block storage.
+#include <cub/device/device_radix_sort.cuh>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace bamg {
+
+__global__ void k_coo_keys(const int32_t* __restrict__ bi, const int32_t* __restrict__ bj, int64_t n,
+                           int64_t nbr, int64_t nbc, unsigned long long* __restrict__ keys,
+                           int* __restrict__ idx, int* __restrict__ bad) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = bi[k], j = bj[k];
+    unsigned long long key = ~0ull;
+    if (i >= 0 && j >= 0) {
+      if (i >= nbr || j >= nbc) {
+        atomicExch(bad, 1);
+      } else {
+        key = ((unsigned long long)(unsigned)i << 32) | (unsigned)j;
+      }
+    }
+    keys[k] = key;
+    idx[k] = (int)k;
+  }
+}
+
+// out block k (pattern order), element e: sum of its contributions in sorted
+// (input) order; written into the sliced storage (and its float copy).
+template <int B>
+__global__ void k_coo_sum(const int* __restrict__ seg, const int* __restrict__ perm,
+                          const double* __restrict__ v, const int* __restrict__ slot_of, int64_t nnzb,
+                          double* __restrict__ vals, float* __restrict__ vals32, int add,
+                          int* __restrict__ err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb * B) return;
+  const int64_t k = t / B;
+  const int e = (int)(t - k * B);
+  const int s0 = seg[k], s1 = seg[k + 1];
+  double sum = 0.0;
+  for (int s = s0; s < s1; ++s) sum += __ldg(v + (int64_t)perm[s] * B + e);
+  const int64_t a = vidx<B>(slot_of[k], e);
+  if (add) sum += vals[a];
+  if (!isfinite(sum)) set_err(err, kDevNaN);
+  vals[a] = sum;
+  if (vals32) vals32[a] = (float)sum;
+}
+
+__global__ void k_coo_sum_any(const int* __restrict__ seg, const int* __restrict__ perm,
+                              const double* __restrict__ v, const int* __restrict__ slot_of, int64_t nnzb,
+                              int B, double* __restrict__ vals, float* __restrict__ vals32, int add,
+                              int* __restrict__ err) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb * B) return;
+  const int64_t k = t / B;
+  const int e = (int)(t - k * B);
+  double sum = 0.0;
+  for (int s = seg[k]; s < seg[k + 1]; ++s) sum += __ldg(v + (int64_t)perm[s] * B + e);
+  const int64_t slot = slot_of[k];
+  const int64_t a = (slot >> 5) * (32LL * B) + 32LL * e + (slot & 31);
+  if (add) sum += vals[a];
+  if (!isfinite(sum)) set_err(err, kDevNaN);
+  vals[a] = sum;
+  if (vals32) vals32[a] = (float)sum;
+}
+
+static Status coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const int32_t* bj) {
+  cudaStream_t st = A->ctx->stream;
+  if (n < 0 || n >= INT32_MAX) return make_status(BAMG_ERR_INVALID, "coo count %lld out of range", (long long)n);
+  if (n > 0 && (!bi || !bj)) return make_status(BAMG_ERR_INVALID, "null coordinate array");
+  bsr_release(A);
+  unsigned long long *keys = nullptr, *keys_s = nullptr;
+  int *idx = nullptr, *idx_s = nullptr, *bad = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  auto cleanup = [&]() {
+    dfree(keys, st);
+    dfree(keys_s, st);
+    dfree(idx, st);
+    dfree(bad, st);
+    dfree(tmp, st);
+  };
+  auto body = [&]() -> Status {
+    std::vector<int> rowptr(A->nbr + 1, 0), colidx, seg(1, 0);
+    if (n == 0) {
+      A->coo_n = 0;
+      BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx)));
+      return upload(&A->coo_seg, seg, st);
+    }
+    BAMG_TRY(dalloc(&keys, n, st));
+    BAMG_TRY(dalloc(&keys_s, n, st));
+    BAMG_TRY(dalloc(&idx, n, st));
+    BAMG_TRY(dalloc(&idx_s, n, st));
+    BAMG_TRY(dalloc(&bad, 1, st));
+    BAMG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    k_coo_keys<<<blocks, 256, 0, st>>>(bi, bj, n, A->nbr, A->nbc, keys, idx, bad);
+    BAMG_CUDA(cudaGetLastError());
+    int hbad = 0;
+    BAMG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BAMG_CUDA(cudaStreamSynchronize(st));
+    if (hbad) return make_status(BAMG_ERR_INVALID, "coo block index out of range (nbr=%lld nbc=%lld)",
+                                 (long long)A->nbr, (long long)A->nbc);
+    // stable radix sort: equal coordinates keep their input order
+    BAMG_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, keys, keys_s, idx, idx_s, (int)n, 0, 64, st));
+    BAMG_TRY(dalloc((char**)&tmp, (int64_t)tmp_bytes, st));
+    BAMG_CUDA(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, keys, keys_s, idx, idx_s, (int)n, 0, 64, st));
+    std::vector<unsigned long long> hk;
+    BAMG_TRY(download(hk, keys_s, n, st));
+    int64_t kept = 0;
+    for (int64_t k = 0; k < n; ++k) {
+      const unsigned long long key = hk[k];
+      if (key == ~0ull) break;
+      if (k == 0 || key != hk[k - 1]) {
+        const int i = (int)(key >> 32);
+        colidx.push_back((int)(key & 0xffffffffu));
+        rowptr[i + 1]++;
+        if (k > 0) seg.push_back((int)k);
+      }
+      kept = k + 1;
+    }
+    if (kept > 0) seg.push_back((int)kept);
+    for (int64_t i = 0; i < A->nbr; ++i) rowptr[i + 1] += rowptr[i];
+    A->coo_n = n;
+    BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx)));
+    BAMG_TRY(upload(&A->coo_seg, seg, st));
+    A->coo_perm = idx_s;
+    idx_s = nullptr;
+    BAMG_CUDA(cudaStreamSynchronize(st));
+    return Status{};
+  };
+  Status s = body();
+  cleanup();
+  dfree(idx_s, st);
+  return s;
+}
+
+static Status coo_set_values(bamg_bsr* A, const double* v, int add) {
+  if (!A->has_pattern || !A->coo_seg) return make_status(BAMG_ERR_STATE, "coo_set_values before coo_preallocate");
+  if (A->coo_n > 0 && !v) return make_status(BAMG_ERR_INVALID, "null value array");
+  cudaStream_t st = A->ctx->stream;
+  const int B = (int)A->block_elems();
+  const int64_t nt = A->nnzb * B;
+  // keep an existing float copy current in the same pass
+  float* v32 = (A->vals32 && A->vals32_version == A->version) ? A->vals32 : nullptr;
+  if (nt > 0) {
+    const unsigned blocks = (unsigned)((nt + 255) / 256);
+    if (B == 9)
+      k_coo_sum<9><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                           A->ctx->d_err);
+    else if (B == 36)
+      k_coo_sum<36><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                            A->ctx->d_err);
+    else if (B == 18)
+      k_coo_sum<18><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                            A->ctx->d_err);
+    else
+      k_coo_sum_any<<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, B, A->vals, v32, add,
+                                            A->ctx->d_err);
+    BAMG_CUDA(cudaGetLastError());
+  }
+  A->version++;
+  if (v32) A->vals32_version = A->version;
+  return Status{};
+}
+
+}  // namespace bamg
+
+using namespace bamg;
+
+extern "C" {
+
+bamg_status bamg_bsr_coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const int32_t* bj) {
+  if (!A) return BAMG_ERR_INVALID;
+  Status s = coo_preallocate(A, n, bi, bj);
+  return s.ok() ? BAMG_OK : fail(A->ctx, s);
+}
+
+bamg_status bamg_bsr_coo_set_values(bamg_bsr* A, const double* v, int add) {
+  if (!A) return BAMG_ERR_INVALID;
+  Status s = coo_set_values(A, v, add);
+  return s.ok() ? BAMG_OK : fail(A->ctx, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,551 @@
+// V-cycle (Sec. 2.1) with Chebyshev / point-block Jacobi smoothing (Sec. 4.1)
+// and preconditioned CG (Sec. 4.1), all as fused row kernels on the sliced
+// block storage.
+//
+// Chebyshev (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1,
+// preconditioned by the block diagonal D) is run with the residual carried by
+// the recurrence: a step with direction d_k does x += d_k, r -= A d_k and
+// d_{k+1} = c1_k d_k + c2_k W D^-1 r in one kernel (one SpMV), so after
+// pre-smoothing the residual needed for restriction is already there.
+// Every kernel takes an optional device flag `done`: when set (CG converged)
+// the kernel returns at once, which lets a whole CG iteration be captured in
+// one CUDA graph and launched in batches without a host round trip per
+// iteration.
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace bamg {
+
+template <int BS, typename T>
+__device__ __forceinline__ void dinv_apply(const T* __restrict__ dinv, int64_t i, const T (&r)[BS], T (&z)[BS]) {
+  const int64_t base = (i >> 5) * (32LL * BS * BS) + (i & 31);
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    T t = T(0);
+#pragma unroll
+    for (int c = 0; c < BS; ++c) t = fma(__ldg(dinv + base + 32 * (a * BS + c)), r[c], t);
+    z[a] = t;
+  }
+}
+
+#define BAMG_DONE_RETURN \
+  if (done && *done) return;
+
+// r = b; d = w Dinv b / theta; x = 0
+template <int BS, typename T>
+__global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* __restrict__ b, T* __restrict__ r,
+                                                           T* __restrict__ d, T* __restrict__ x,
+                                                           const T* __restrict__ dinv, const float* __restrict__ w,
+                                                           const double* __restrict__ scal, const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T bi[BS], z[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) bi[a] = b[i * BS + a];
+  dinv_apply<BS, T>(dinv, i, bi, z);
+  const T f = (T)(scal[kInvTheta] * (w ? (double)w[i] : 1.0));
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    r[i * BS + a] = bi[a];
+    d[i * BS + a] = f * z[a];
+    x[i * BS + a] = T(0);
+  }
+}
+
+// x += d_in; r -= A d_in; if has_next: d_out = c1 d_in + c2 w Dinv r
+template <int BS, typename T>
+__global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict__ sp, const int* __restrict__ col,
+                                                           const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                           const T* __restrict__ d_in, T* __restrict__ d_out,
+                                                           T* __restrict__ x, T* __restrict__ r,
+                                                           const T* __restrict__ dinv, const float* __restrict__ w,
+                                                           const double* __restrict__ scal, int k, int has_next,
+                                                           const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows_pad) return;
+  T acc[BS];
+  row_product<BS, BS, T, T, T>(sp, col, vals, d_in, i, acc);
+  if (i >= n) return;
+  T di[BS], ri[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    di[a] = d_in[i * BS + a];
+    ri[a] = r[i * BS + a] - acc[a];
+    r[i * BS + a] = ri[a];
+    x[i * BS + a] += di[a];
+  }
+  if (has_next) {
+    T z[BS];
+    dinv_apply<BS, T>(dinv, i, ri, z);
+    const T c1 = (T)scal[kCheb + 2 * k];
+    const T c2 = (T)(scal[kCheb + 2 * k + 1] * (w ? (double)w[i] : 1.0));
+#pragma unroll
+    for (int a = 0; a < BS; ++a) d_out[i * BS + a] = fma(c1, di[a], c2 * z[a]);
+  }
+}
+
+// r = b - A x; d = w Dinv r / theta   (x is read by the product: not written here)
+template <int BS, typename T>
+__global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restrict__ sp, const int* __restrict__ col,
+                                                            const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                            const T* __restrict__ x, const T* __restrict__ b,
+                                                            T* __restrict__ r, T* __restrict__ d,
+                                                            const T* __restrict__ dinv, const float* __restrict__ w,
+                                                            const double* __restrict__ scal, const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows_pad) return;
+  T acc[BS];
+  row_product<BS, BS, T, T, T>(sp, col, vals, x, i, acc);
+  if (i >= n) return;
+  T ri[BS], z[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    ri[a] = b[i * BS + a] - acc[a];
+    r[i * BS + a] = ri[a];
+  }
+  dinv_apply<BS, T>(dinv, i, ri, z);
+  const T f = (T)(scal[kInvTheta] * (w ? (double)w[i] : 1.0));
+#pragma unroll
+  for (int a = 0; a < BS; ++a) d[i * BS + a] = f * z[a];
+}
+
+template <typename T>
+__global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ x, const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m) x[t] += d[t];
+}
+
+// y = M v (restriction with R = P^T), or y += M v (prolongation with P)
+template <int BR, int BC, typename T>
+__global__ void __launch_bounds__(kRowThreads) k_transfer(const int* __restrict__ sp, const int* __restrict__ col,
+                                                          const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                          const T* __restrict__ v, T* __restrict__ y, int accumulate,
+                                                          const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= rows_pad) return;
+  T acc[BR];
+  row_product<BR, BC, T, T, T>(sp, col, vals, v, i, acc);
+  if (i >= n) return;
+#pragma unroll
+  for (int a = 0; a < BR; ++a) y[i * BR + a] = accumulate ? y[i * BR + a] + acc[a] : acc[a];
+}
+
+template <typename TS, typename TD>
+__global__ void k_cast_done(int64_t m, const TS* __restrict__ s, TD* __restrict__ d, const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m) d[t] = (TD)s[t];
+}
+
+// ------------------------------------------------------------------ V-cycle
+
+template <typename T>
+struct LevelPtrs {
+  T *b, *x, *r, *d0, *d1;
+  const T *dinv, *Avals, *Pvals, *Rvals;
+};
+static LevelPtrs<double> ptrs64(Level& L) {
+  return {L.b, L.x, L.r, L.d0, L.d1, L.dinv, L.A->vals, L.P ? L.P->vals : nullptr, L.R ? L.R->vals : nullptr};
+}
+static LevelPtrs<float> ptrs32(Level& L) {
+  return {L.b32, L.x32, L.r32, L.d032, L.d132, L.dinv32, L.A->vals32, L.P ? L.P->vals32 : nullptr,
+          L.R ? L.R->vals32 : nullptr};
+}
+template <typename T>
+LevelPtrs<T> level_ptrs(Level& L);
+template <>
+LevelPtrs<double> level_ptrs<double>(Level& L) { return ptrs64(L); }
+template <>
+LevelPtrs<float> level_ptrs<float>(Level& L) { return ptrs32(L); }
+
+template <int BS, typename T>
+static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
+  Level& L = mg->levels[l];
+  auto p = level_ptrs<T>(L);
+  const bamg_bsr* A = L.A;
+  const int64_t rows = A->nslices * kSlice;
+  const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
+  const unsigned gn = (unsigned)((L.n + kRowThreads - 1) / kRowThreads);
+  const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
+  const int m = mg->opts.cheb_degree;
+  k_cheb_init<BS, T><<<gn, kRowThreads, 0, st>>>(L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done);
+  T* d[2] = {p.d0, p.d1};
+  for (int k = 0; k < m; ++k)
+    k_cheb_step<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
+                                                   k + 1 < m ? 1 : 0, done);
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <int BS, typename T>
+static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
+  Level& L = mg->levels[l];
+  auto p = level_ptrs<T>(L);
+  const bamg_bsr* A = L.A;
+  const int64_t rows = A->nslices * kSlice;
+  const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
+  const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
+  const int m = mg->opts.cheb_degree;
+  k_cheb_rinit<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+                                                  p.d0, p.dinv, L.weights, sc, done);
+  T* d[2] = {p.d0, p.d1};
+  for (int k = 0; k + 1 < m; ++k)
+    k_cheb_step<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done);
+  const int64_t mm = L.n * BS;
+  k_axpy_done<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(mm, d[(m - 1) & 1], p.x, done);
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <int BR, int BC, typename T>
+static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int accumulate, const int* done,
+                       cudaStream_t st) {
+  const int64_t rows = M->nslices * kSlice;
+  if (rows == 0) return Status{};
+  k_transfer<BR, BC, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
+      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done);
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <typename T>
+Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
+  const int nl = (int)mg->levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = mg->levels[l];
+    Level& C = mg->levels[l + 1];
+    auto p = level_ptrs<T>(L);
+    auto pc = level_ptrs<T>(C);
+    if (L.bs == 3) {
+      BAMG_TRY((smooth_down<3, T>(mg, l, done, st)));
+      BAMG_TRY((transfer<6, 3, T>(L.R, p.Rvals, p.r, pc.b, 0, done, st)));
+    } else {
+      BAMG_TRY((smooth_down<6, T>(mg, l, done, st)));
+      BAMG_TRY((transfer<6, 6, T>(L.R, p.Rvals, p.r, pc.b, 0, done, st)));
+    }
+  }
+  {
+    auto p = level_ptrs<T>(mg->levels[nl - 1]);
+    BAMG_TRY(coarse_apply<T>(mg, p.b, p.x, done, st));
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    Level& L = mg->levels[l];
+    auto p = level_ptrs<T>(L);
+    auto pc = level_ptrs<T>(mg->levels[l + 1]);
+    if (L.bs == 3) {
+      BAMG_TRY((transfer<3, 6, T>(L.P, p.Pvals, pc.x, p.x, 1, done, st)));
+      BAMG_TRY((smooth_up<3, T>(mg, l, done, st)));
+    } else {
+      BAMG_TRY((transfer<6, 6, T>(L.P, p.Pvals, pc.x, p.x, 1, done, st)));
+      BAMG_TRY((smooth_up<6, T>(mg, l, done, st)));
+    }
+  }
+  return Status{};
+}
+
+template Status vcycle_on<double>(bamg_mg*, const int*, cudaStream_t);
+template Status vcycle_on<float>(bamg_mg*, const int*, cudaStream_t);
+
+// z = M r for FP64 vectors r (read) and z (written); in the mixed form the
+// cycle runs on float copies.
+static Status precond(bamg_mg* mg, const double* r, double* z, const int* done, cudaStream_t st) {
+  Level& L0 = mg->levels[0];
+  const int64_t m = L0.n * L0.bs;
+  const unsigned g = (unsigned)((m + 255) / 256);
+  if (mg->opts.precision == BAMG_FP32) {
+    k_cast_done<double, float><<<g, 256, 0, st>>>(m, r, L0.b32, done);
+    BAMG_TRY(vcycle_on<float>(mg, done, st));
+    k_cast_done<float, double><<<g, 256, 0, st>>>(m, L0.x32, z, done);
+  } else {
+    if (r != L0.b) k_cast_done<double, double><<<g, 256, 0, st>>>(m, r, L0.b, done);
+    BAMG_TRY(vcycle_on<double>(mg, done, st));
+    if (z != L0.x) k_cast_done<double, double><<<g, 256, 0, st>>>(m, L0.x, z, done);
+  }
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+// ------------------------------------------------------------------ CG
+
+__global__ void k_cg_setup(CgState* s, double rtol, int maxit) {
+  s->bnorm2 = 0.0;
+  s->rtol2 = rtol * rtol;
+  s->rz = s->pq = s->alpha = s->beta = s->rnorm2 = 0.0;
+  s->its = 0;
+  s->maxit = maxit;
+  s->done = s->converged = s->breakdown = 0;
+}
+
+// r = b, x = 0, ||b||^2
+__global__ void k_cg_init(int64_t m, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ x,
+                          CgState* s, double* partials, unsigned* counter) {
+  double local[1] = {0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const double v = b[t];
+    r[t] = v;
+    x[t] = 0.0;
+    local[0] = fma(v, v, local[0]);
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) {
+    s->bnorm2 = out[0];
+    s->rnorm2 = out[0];
+    if (!(out[0] > 0.0)) {
+      s->done = 1;
+      s->converged = 1;
+    }
+  }
+}
+
+// p = z, z_old = z, rz = r.z
+__global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double* __restrict__ z,
+                           double* __restrict__ p, double* __restrict__ zold, CgState* s, double* partials,
+                           unsigned* counter) {
+  if (s->done) return;
+  double local[1] = {0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const double zv = z[t];
+    p[t] = zv;
+    zold[t] = zv;
+    local[0] = fma(r[t], zv, local[0]);
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) s->rz = out[0];
+}
+
+// q = A p, alpha = rz / (p.q)
+__global__ void __launch_bounds__(kRowThreads) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
+                                                       const double* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                       const double* __restrict__ p, double* __restrict__ q,
+                                                       CgState* s, double* partials, unsigned* counter) {
+  if (s->done) return;
+  double local[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad; i += stride) {
+    double acc[3];
+    row_product<3, 3, double, double, double>(sp, col, vals, p, i, acc);
+    if (i < n) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        q[i * 3 + a] = acc[a];
+        local[0] = fma(p[i * 3 + a], acc[a], local[0]);
+      }
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) {
+    s->pq = out[0];
+    if (!(out[0] > 0.0)) {
+      s->breakdown = 1;
+      s->done = 1;
+    } else {
+      s->alpha = s->rz / out[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, ||r||^2, convergence test
+__global__ void k_cg_xr(int64_t m, const double* __restrict__ p, const double* __restrict__ q,
+                        double* __restrict__ x, double* __restrict__ r, CgState* s, double* partials,
+                        unsigned* counter) {
+  if (s->done) return;
+  const double alpha = s->alpha;
+  double local[1] = {0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    x[t] = fma(alpha, p[t], x[t]);
+    const double rv = fma(-alpha, q[t], r[t]);
+    r[t] = rv;
+    local[0] = fma(rv, rv, local[0]);
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) {
+    s->rnorm2 = out[0];
+    s->its += 1;
+    if (!isfinite(out[0])) {
+      s->breakdown = 1;
+      s->done = 1;
+    } else if (out[0] <= s->rtol2 * s->bnorm2) {
+      s->converged = 1;
+      s->done = 1;
+    } else if (s->its >= s->maxit) {
+      s->done = 1;
+    }
+  }
+}
+
+// beta = r.(z - z_old) / rz (Polak-Ribiere), rz = r.z
+__global__ void k_cg_dots(int64_t m, const double* __restrict__ r, const double* __restrict__ z,
+                          const double* __restrict__ zold, CgState* s, double* partials, unsigned* counter) {
+  if (s->done) return;
+  double local[2] = {0.0, 0.0};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const double rv = r[t];
+    local[0] = fma(rv, z[t], local[0]);
+    local[1] = fma(rv, zold[t], local[1]);
+  }
+  double out[2];
+  if (grid_reduce<2>(local, partials, counter, out) && threadIdx.x == 0) {
+    s->beta = (out[0] - out[1]) / s->rz;
+    s->rz = out[0];
+  }
+}
+
+// p = z + beta p, z_old = z
+__global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restrict__ p, double* __restrict__ zold,
+                       const CgState* s) {
+  if (s->done) return;
+  const double beta = s->beta;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    const double zv = z[t];
+    p[t] = fma(beta, p[t], zv);
+    zold[t] = zv;
+  }
+}
+
+// ||b - A x||^2 into s->pq (final true residual)
+__global__ void __launch_bounds__(kRowThreads) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
+                                                               const double* __restrict__ vals, int64_t n,
+                                                               int64_t rows_pad, const double* __restrict__ x,
+                                                               const double* __restrict__ b, double* out_norm2,
+                                                               double* partials, unsigned* counter) {
+  double local[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad; i += stride) {
+    double acc[3];
+    row_product<3, 3, double, double, double>(sp, col, vals, x, i, acc);
+    if (i < n) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double t = b[i * 3 + a] - acc[a];
+        local[0] = fma(t, t, local[0]);
+      }
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) *out_norm2 = out[0];
+}
+
+static unsigned vec_grid(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 1216)); }
+static unsigned row_grid(int64_t rows) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kRowThreads - 1) / kRowThreads, 1216));
+}
+
+// One CG iteration after the first preconditioner application.
+static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
+  bamg_ctx* ctx = mg->ctx;
+  Level& L0 = mg->levels[0];
+  const bamg_bsr* A = L0.A;
+  const int64_t m = L0.n * 3, rows = A->nslices * kSlice;
+  CgState* s = mg->cg;
+  const int* done = &s->done;
+  k_cg_Ap<<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+                                                  ctx->d_partials, ctx->d_counters + 2);
+  k_cg_xr<<<vec_grid(m), 256, 0, st>>>(m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3);
+  BAMG_TRY(precond(mg, r, z, done, st));
+  k_cg_dots<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->czold, s, ctx->d_partials, ctx->d_counters + 4);
+  k_cg_p<<<vec_grid(m), 256, 0, st>>>(m, z, mg->cp, mg->czold, s);
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+static Status cg_graph(bamg_mg* mg, double* r, double* z) {
+  if (mg->cg_graph) return Status{};
+  cudaStream_t cs = nullptr;
+  BAMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  Status s;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    s = cuda_status(e, "begin capture");
+  } else {
+    s = cg_iteration(mg, r, z, cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (s.ok() && e != cudaSuccess) s = cuda_status(e, "end capture");
+    if (s.ok()) {
+      e = cudaGraphInstantiate(&mg->cg_graph, g, 0);
+      if (e != cudaSuccess) {
+        s = cuda_status(e, "graph instantiate");
+        mg->cg_graph = nullptr;
+      }
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  return s;
+}
+
+static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit, bamg_cg_info* info) {
+  bamg_ctx* ctx = mg->ctx;
+  cudaStream_t st = ctx->stream;
+  Level& L0 = mg->levels[0];
+  const int64_t m = L0.n * 3;
+  const bool f64 = mg->opts.precision == BAMG_FP64;
+  double* r = f64 ? L0.b : mg->cr;  // the cycle reads its right-hand side in place
+  double* z = f64 ? L0.x : mg->cz;
+  CgState* s = mg->cg;
+  BAMG_TRY(cg_graph(mg, r, z));
+  k_cg_setup<<<1, 1, 0, st>>>(s, rtol, maxit);
+  k_cg_init<<<vec_grid(m), 256, 0, st>>>(m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5);
+  BAMG_TRY(precond(mg, r, z, &s->done, st));
+  k_cg_first<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6);
+  BAMG_CUDA(cudaGetLastError());
+  int launched = 0, chunk = 4;
+  while (launched < maxit) {
+    const int c = std::min(chunk, maxit - launched);
+    for (int k = 0; k < c; ++k) BAMG_CUDA(cudaGraphLaunch(mg->cg_graph, st));
+    launched += c;
+    BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    BAMG_CUDA(cudaStreamSynchronize(st));
+    if (mg->cg_host->done) break;
+  }
+  if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  const bamg_bsr* A = L0.A;
+  const int64_t rows = A->nslices * kSlice;
+  double* tr = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel + 8;
+  k_true_residual<<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+                                                          tr, ctx->d_partials, ctx->d_counters + 7);
+  double tr2 = 0.0;
+  BAMG_CUDA(cudaMemcpyAsync(&tr2, tr, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+  BAMG_TRY(check_device_error(ctx));
+  const CgState& h = *mg->cg_host;
+  if (info) {
+    info->iterations = h.its;
+    info->converged = h.converged;
+    info->rnorm = sqrt(h.rnorm2);
+    info->bnorm = sqrt(h.bnorm2);
+    info->true_rnorm = sqrt(tr2);
+  }
+  if (h.breakdown) return make_status(BAMG_ERR_BREAKDOWN, "CG breakdown after %d iterations", h.its);
+  if (!h.converged) return make_status(BAMG_ERR_NOT_CONVERGED, "CG did not converge in %d iterations", h.its);
+  return Status{};
+}
+
+}  // namespace bamg
+
+using namespace bamg;
+
+extern "C" {
+
+bamg_status bamg_vcycle(bamg_mg* mg, const double* b, double* x) {
+  if (!mg || !b || !x) return BAMG_ERR_INVALID;
+  Status s = precond(mg, b, x, nullptr, mg->ctx->stream);
+  return s.ok() ? BAMG_OK : fail(mg->ctx, s);
+}
+
+bamg_status bamg_cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit, bamg_cg_info* info) {
+  if (!mg || !b || maxit < 0 || !(rtol >= 0.0)) return BAMG_ERR_INVALID;
+  Status s = cg_solve(mg, b, x, rtol, maxit, info);
+  return s.ok() ? BAMG_OK : fail(mg->ctx, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Internal declarations of libbamg: object layouts, the sliced block storage,
+// status plumbing and the kernel launchers shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "bamg.h"
+
+namespace bamg {
+
+// Rows per slice of the sliced block storage: one warp, one row per lane.
+constexpr int kSlice = 32;
+// Threads per CTA of the row kernels (4 slices).
+constexpr int kRowThreads = 128;
+// CTAs of the fixed-grid reductions (a multiple of the 152 SMs of a GB300).
+constexpr int kRedBlocks = 608;
+constexpr int kRedThreads = 256;
+
+struct Status {
+  bamg_status code = BAMG_OK;
+  std::string msg;
+  bool ok() const { return code == BAMG_OK; }
+};
+
+}  // namespace bamg
+
+struct bamg_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  std::string err;
+  int* d_err = nullptr;            // device error word (first error code wins)
+  double* d_partials = nullptr;    // kRedBlocks partial sums x 4 lanes
+  unsigned* d_counters = nullptr;  // last-block counters (16 slots)
+};
+
+// Rectangular-block sparse matrix.  The pattern is kept in block-CSR form
+// (rows sorted by column) and, for the kernels, in a sliced form: rows are
+// grouped in slices of 32, each slice is padded to its longest row, and slot
+// t of row lane l in slice s is chunk (slice_ptr[s] + t), lane l, i.e. slot
+// index 32 * chunk + l.  Values live only in the sliced form, element e of a
+// slot at vals[32 * B * chunk + 32 * e + l] (B = bs_r * bs_c), so the 32 rows
+// of a slice read every element with one coalesced access.  Padding slots
+// hold zero values and a valid column.
+struct bamg_bsr {
+  bamg_ctx* ctx = nullptr;
+  int br = 0, bc = 0;
+  int64_t nbr = 0, nbc = 0, nnzb = 0;
+  bool has_pattern = false;
+  bool symmetric = false;
+  uint64_t version = 0;
+  // block-CSR pattern (device + host copies)
+  int* rowptr = nullptr;
+  int* colidx = nullptr;
+  std::vector<int> h_rowptr, h_colidx;
+  // sliced form
+  int64_t nslices = 0, nchunks = 0;
+  int* slice_ptr = nullptr;  // nslices + 1, in chunks
+  int* sell_col = nullptr;   // 32 * nchunks
+  int* slot_of = nullptr;    // nnzb: CSR block -> slot
+  int* diag_slot = nullptr;  // nbr (square blocks only, -1 if no diagonal block)
+  bool all_diag = false;     // every block row has its diagonal block
+  std::vector<int> h_slice_ptr, h_slot_of;
+  double* vals = nullptr;    // 32 * nchunks * B
+  float* vals32 = nullptr;   // float copy in the same layout
+  uint64_t vals32_version = ~0ull;
+  bool vals64_stale = false; // an FP32 Galerkin product wrote only vals32
+  uint64_t pattern_id = 0;   // changes whenever the pattern is rebuilt
+  // blocked COO plan
+  int64_t coo_n = 0;
+  int* coo_perm = nullptr;   // contributions in (row, col, input order) order
+  int* coo_seg = nullptr;    // nnzb + 1 offsets into coo_perm
+  int64_t block_elems() const { return (int64_t)br * bc; }
+  int64_t nslots() const { return nchunks * bamg::kSlice; }
+};
+
+// Galerkin product plan (Sec. 3.1, Sec. 3.5).  Stage 1 forms the intermediate
+// Z = A P block by block, stage 2 forms A_c = P^T Z; both gather, for each
+// output block, a fixed list of input block pairs (built once by the symbolic
+// phase), so the numeric phase has no atomics and a fixed summation order.
+// Output blocks are processed in order of decreasing list length so the
+// lane groups of a warp carry equal work.
+struct bamg_ptap {
+  bamg_ctx* ctx = nullptr;
+  const bamg_bsr* A = nullptr;
+  const bamg_bsr* P = nullptr;
+  bamg_bsr* Ac = nullptr;
+  uint64_t a_pid = 0, p_pid = 0, ac_pid = 0;
+  int bs = 0, bsp = 0;
+  bool symmetric = false;
+  // intermediate pattern Z = A P (host)
+  int64_t nz = 0;
+  std::vector<int> h_zrowptr, h_zcol;
+  // stage 1: items (Z blocks), their gather lists of (A slot, P block)
+  int64_t n1 = 0, e1 = 0;
+  int *s1_z = nullptr, *s1_off = nullptr, *s1_a = nullptr, *s1_p = nullptr;
+  // stage 2: items (A_c blocks, upper triangle if symmetric), lists of (P block, Z block)
+  int64_t n2 = 0, e2 = 0;
+  int *s2_slot = nullptr, *s2_tslot = nullptr, *s2_off = nullptr, *s2_p = nullptr, *s2_z = nullptr;
+  // work buffers and the state-gated prolongator-side cache (P in block order)
+  double* Z = nullptr;
+  float* Z32 = nullptr;
+  double* Pblk = nullptr;
+  float* Pblk32 = nullptr;
+  uint64_t pblk_version = ~0ull, pblk32_version = ~0ull;
+  uint64_t pblk_refreshes = 0;
+};
+
+namespace bamg {
+
+// Per-level device scalars (doubles): eigen-estimate, Chebyshev coefficients.
+enum LevelScalar : int {
+  kLam = 0,        // lambda_max estimate of D^-1 A
+  kInvTheta = 1,   // 1 / theta
+  kCheb = 2,       // (c1_k, c2_k) pairs for k = 0..degree-2 from here
+  kScalarsPerLevel = 32
+};
+
+// Dense Cholesky data of the coarsest level: the factor's inverse W = L^-1
+// (row-major, lower) and its transpose (row-major, upper), padded to a
+// multiple of the 32-wide tiles with an identity block.
+struct CoarseDense {
+  int64_t n = 0, npad = 0;
+  double* M = nullptr;   // npad x npad work array (factor, then W)
+  double* Wt = nullptr;  // npad x npad transpose of W
+  double* b64 = nullptr; // FP64 staging vectors (mixed form)
+  double* x64 = nullptr;
+  int* rows = nullptr;   // block row of every stored block of the coarsest operator
+};
+
+struct Level {
+  bamg_bsr* A = nullptr;     // operator (level 0 is borrowed from the caller)
+  bool own_A = false;
+  bamg_bsr* P = nullptr;     // prolongator from the next level
+  bamg_bsr* R = nullptr;     // R = P^T (cached, rebuilt when P's version changes)
+  int* rmap = nullptr;       // R block -> P block (pattern order)
+  uint64_t r_version = ~0ull;
+  bamg_ptap* plan = nullptr; // Galerkin plan A, P -> next level's A
+  int bs = 0;
+  int64_t n = 0;             // block rows
+  double omega = 0.0;        // prolongator damping used at setup
+  double* dinv = nullptr;    // block-diagonal inverse, slice-interleaved
+  float* dinv32 = nullptr;
+  float* weights = nullptr;  // per-block-row smoother weights (borrowed), or null
+  // vectors (FP64 and FP32 forms): right-hand side, iterate, residual, directions
+  double *b = nullptr, *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d032 = nullptr, *d132 = nullptr;
+};
+
+struct CgState {
+  double bnorm2, rtol2, rz, pq, alpha, beta, rnorm2, pad;
+  int its, maxit, done, converged, breakdown, pad2[3];
+};
+
+}  // namespace bamg
+
+struct bamg_mg {
+  bamg_ctx* ctx = nullptr;
+  bamg_mg_opts opts{};
+  std::vector<bamg::Level> levels;
+  double* scal = nullptr;            // levels x kScalarsPerLevel device scalars
+  bamg::CoarseDense coarse;
+  // CG work vectors (fine level, FP64) and state
+  double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *czold = nullptr;
+  bamg::CgState* cg = nullptr;
+  bamg::CgState* cg_host = nullptr;  // pinned
+  cudaGraphExec_t cg_graph = nullptr;
+  cudaGraphExec_t update_graph = nullptr;
+  double* power_w[2] = {nullptr, nullptr};
+};
+
+namespace bamg {
+
+// ------------------------------------------------------------ status helpers
+Status make_status(bamg_status code, const char* fmt, ...);
+bamg_status fail(bamg_ctx* ctx, const Status& s);
+Status cuda_status(cudaError_t e, const char* what);
+#define BAMG_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return ::bamg::cuda_status(e_, #call); \
+  } while (0)
+#define BAMG_TRY(expr)                   \
+  do {                                   \
+    ::bamg::Status s_ = (expr);          \
+    if (!s_.ok()) return s_;             \
+  } while (0)
+
+template <typename T>
+Status dalloc(T** p, int64_t n, cudaStream_t st) {
+  *p = nullptr;
+  if (n <= 0) return Status{};
+  cudaError_t e = cudaMallocAsync((void**)p, sizeof(T) * (size_t)n, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return make_status(BAMG_ERR_OOM, "device allocation of %lld bytes failed: %s",
+                       (long long)(sizeof(T) * (size_t)n), cudaGetErrorString(e));
+  }
+  return Status{};
+}
+template <typename T>
+void dfree(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+template <typename T>
+Status upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
+  BAMG_TRY(dalloc(dst, (int64_t)src.size(), st));
+  if (!src.empty())
+    BAMG_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st));
+  return Status{};
+}
+template <typename T>
+Status download(std::vector<T>& dst, const T* src, int64_t n, cudaStream_t st) {
+  dst.resize((size_t)n);
+  if (n > 0) BAMG_CUDA(cudaMemcpyAsync(dst.data(), src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, st));
+  BAMG_CUDA(cudaStreamSynchronize(st));
+  return Status{};
+}
+
+// Device error codes written into ctx->d_err.
+enum DevErr : int { kDevOk = 0, kDevNaN = 1, kDevBreakdown = 2, kDevTimeout = 3, kDevIndex = 4 };
+Status check_device_error(bamg_ctx* ctx);  // synchronizes the stream
+
+// ------------------------------------------------------------ pattern helpers
+// Build the sliced form (and device/host CSR copies) from a host CSR pattern;
+// allocates zeroed values.  Used by COO preallocation and the Galerkin symbolic.
+Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx);
+Status bsr_ensure_fp32(bamg_bsr* A);   // refresh vals32 if the version changed
+void bsr_release(bamg_bsr* A);
+
+// Galerkin plan construction; with want_ac = false only stage 1 (Z = A P) is
+// planned (used by prolongator smoothing).
+Status ptap_build(bamg_bsr* A, bamg_bsr* P, bool want_ac, bamg_ptap** plan, bamg_bsr** Ac);
+Status ptap_run(bamg_ptap* plan, bamg_bsr* A, bamg_bsr* P, bamg_bsr* Ac, bamg_prec prec, bool stage2);
+void ptap_release(bamg_ptap* plan);
+// Copy sliced values to block (pattern) order.
+Status launch_gather_blocks(const bamg_bsr* A, const double* vals, double* out, cudaStream_t st);
+
+// Hierarchy internals shared by the setup, cycle and coarse-solver units.
+Status mg_refresh_level(bamg_mg* mg, int l);            // Dinv, eigen-estimate, Chebyshev coefficients
+Status mg_refresh_restriction(bamg_mg* mg, int l);      // state-gated R = P^T
+Status coarse_factor(bamg_mg* mg);                      // dense Cholesky + inverse of the coarsest level
+template <typename T>
+Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t st);
+template <typename T>
+Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
+Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
+
+// ------------------------------------------------------------ kernel launchers
+// y = A x (row-block product) in precision T (double or float); x, y device.
+template <typename T>
+Status launch_spmv(const bamg_bsr* A, const T* vals, const T* x, T* y, cudaStream_t st);
+template <typename T>
+Status launch_spmm(const bamg_bsr* A, const T* vals, const T* X, T* Y, int k, cudaStream_t st);
+// Convert a sliced value array to float.
+Status launch_to_fp32(const double* src, float* dst, int64_t n, cudaStream_t st);
+
+}  // namespace bamg

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Patterns and aggregates must match bit-exactly; FP64 values to 1e-12
+normwise relative error (||X_gpu - X_oracle|| / ||X_oracle||)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov, multigrid as omg
+from oracle.assembly import coo_assemble_blocks
+from paper_2606_24748_gb300 import bamg as B
+from workloads.elasticity import Mesh, body_force
+
+from gpu_helpers import TOL64, GpuProblem, read_bsr, rel, same_pattern
+from oracle_cases import hierarchy, problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    B.lib()
+
+
+def random_stream(rng, nbr, nbc, br, bc, n, neg=True):
+    bi = rng.integers(-1 if neg else 0, nbr, n).astype(np.int32)
+    bj = rng.integers(-1 if neg else 0, nbc, n).astype(np.int32)
+    v = rng.standard_normal((n, br, bc))
+    return bi, bj, v
+
+
+@pytest.mark.parametrize("br,bc", [(3, 3), (6, 6), (3, 6), (6, 3), (2, 5)])
+def test_coo_assembly_and_spmv(br, bc):
+    rng = np.random.default_rng(br * 10 + bc)
+    nbr, nbc, n = 77, 53, 2000       # several slices and a ragged tail
+    bi, bj, v = random_stream(rng, nbr, nbc, br, bc, n)
+    ref = coo_assemble_blocks(nbr, nbc, br, bc, bi, bj, v)
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    A = B.bamg_bsr_create(ctx, br, bc, nbr, nbc)
+    try:
+        B.bamg_bsr_coo_preallocate(ctx, A, torch.from_numpy(bi).cuda(), torch.from_numpy(bj).cuda())
+        vt = torch.from_numpy(v).cuda()
+        B.bamg_bsr_coo_set_values(ctx, A, vt, 0)
+        got = read_bsr(ctx, A)
+        assert same_pattern(got, ref)
+        assert rel(got.vals, ref.vals) <= 1e-15
+        B.bamg_bsr_coo_set_values(ctx, A, vt, 1)          # ADD mode doubles every block
+        assert rel(read_bsr(ctx, A).vals, 2 * ref.vals) <= 1e-15
+        B.bamg_bsr_coo_set_values(ctx, A, vt, 0)
+        x = rng.standard_normal(nbc * bc)
+        y = torch.zeros(nbr * br, dtype=torch.float64, device="cuda")
+        B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).cuda(), y)
+        yref = ref.scalar() @ x
+        assert rel(y.cpu().numpy(), yref) <= 1e-14
+        y32 = torch.zeros(nbr * br, dtype=torch.float32, device="cuda")
+        B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x.astype(np.float32)).cuda(), y32, B.BAMG_FP32)
+        assert rel(y32.cpu().numpy(), yref) <= 1e-5
+        if (br, bc) != (2, 5):
+            k = 5
+            X = rng.standard_normal((nbc * bc, k))
+            Y = torch.zeros(nbr * br * k, dtype=torch.float64, device="cuda")
+            B.bamg_bsr_spmm(ctx, A, torch.from_numpy(X.copy()).cuda(), Y, k)
+            assert rel(Y.cpu().numpy().reshape(-1, k), ref.scalar() @ X) <= 1e-14
+    finally:
+        B.bamg_bsr_destroy(A)
+        B.bamg_ctx_destroy(ctx)
+
+
+def test_coo_rejects_out_of_range_index():
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    A = B.bamg_bsr_create(ctx, 3, 3, 4, 4)
+    try:
+        bi = torch.tensor([0, 1, 4], dtype=torch.int32, device="cuda")
+        bj = torch.tensor([0, 1, 1], dtype=torch.int32, device="cuda")
+        with pytest.raises(B.BamgError) as e:
+            B.bamg_bsr_coo_preallocate(ctx, A, bi, bj)
+        assert e.value.status == 1
+    finally:
+        B.bamg_bsr_destroy(A)
+        B.bamg_ctx_destroy(ctx)
+
+
+def test_general_galerkin_product_through_the_abi():
+    from oracle.galerkin import galerkin
+    rng = np.random.default_rng(11)
+    for (bs, bsp, n, nc) in ((3, 6, 150, 40), (6, 6, 90, 33)):
+        bi, bj, v = random_stream(rng, n, n, bs, bs, 1500, neg=False)
+        pi, pj, pv = random_stream(rng, n, nc, bs, bsp, 400, neg=False)
+        Aref = coo_assemble_blocks(n, n, bs, bs, bi, bj, v)
+        Pref = coo_assemble_blocks(n, nc, bs, bsp, pi, pj, pv)
+        ref = galerkin(Aref, Pref)
+        ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+        A = B.bamg_bsr_create(ctx, bs, bs, n, n)
+        P = B.bamg_bsr_create(ctx, bs, bsp, n, nc)
+        plan = Ac = None
+        try:
+            B.bamg_bsr_coo_preallocate(ctx, A, torch.from_numpy(bi).cuda(), torch.from_numpy(bj).cuda())
+            B.bamg_bsr_coo_set_values(ctx, A, torch.from_numpy(v).cuda(), 0)
+            B.bamg_bsr_coo_preallocate(ctx, P, torch.from_numpy(pi).cuda(), torch.from_numpy(pj).cuda())
+            B.bamg_bsr_coo_set_values(ctx, P, torch.from_numpy(pv).cuda(), 0)
+            plan, Ac = B.bamg_ptap_symbolic(ctx, A, P)
+            B.bamg_ptap_numeric(ctx, plan, A, P, Ac)
+            got = read_bsr(ctx, Ac)
+            assert same_pattern(got, ref)
+            assert rel(got.vals, ref.vals) <= TOL64
+            first = got.vals.copy()
+            B.bamg_ptap_numeric(ctx, plan, A, P, Ac)      # deterministic: bitwise equal
+            assert np.array_equal(read_bsr(ctx, Ac).vals, first)
+            B.bamg_ptap_numeric_prec(ctx, plan, A, P, Ac, B.BAMG_FP32)
+            with pytest.raises(B.BamgError):
+                B.bamg_bsr_get_values(ctx, Ac, torch.empty(10, dtype=torch.float64, device="cuda"))
+            B.bamg_ptap_numeric(ctx, plan, A, P, Ac)
+            assert np.array_equal(read_bsr(ctx, Ac).vals, first)
+        finally:
+            if plan is not None:
+                B.bamg_ptap_destroy(plan)
+                B.bamg_bsr_destroy(Ac)
+            B.bamg_bsr_destroy(P)
+            B.bamg_bsr_destroy(A)
+            B.bamg_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("ne", [8, 13, 24])
+def test_hierarchy_matches_oracle(ne):
+    """Assembled A, P and A_c of every level, eigen-estimates, damping and Dinv."""
+    mesh, s, Aref = problem(ne)
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        A = read_bsr(gp.ctx, gp.A)
+        assert same_pattern(A, Aref) and rel(A.vals, Aref.vals) <= 1e-15
+        nl = B.bamg_mg_num_levels(gp.mg)
+        assert nl == h.n_levels
+        for l in range(nl):
+            Al, Pl = B.bamg_mg_get_level(gp.mg, l)
+            ga = read_bsr(gp.ctx, Al)
+            assert same_pattern(ga, h.levels[l].A), f"level {l} operator pattern"
+            assert rel(ga.vals, h.levels[l].A.vals) <= TOL64, f"level {l} operator values"
+            if l + 1 < nl:
+                gpP = read_bsr(gp.ctx, Pl)
+                assert same_pattern(gpP, h.levels[l].P), f"level {l} prolongator pattern"
+                assert rel(gpP.vals, h.levels[l].P.vals) <= TOL64, f"level {l} prolongator values"
+                lam, om = B.bamg_mg_get_level_scalars(gp.ctx, gp.mg, l)
+                assert abs(om - h.levels[l].omega) <= 1e-12 * h.levels[l].omega
+                assert abs(lam - h.levels[l].lam) <= 1e-12 * h.levels[l].lam
+                d = torch.empty(h.levels[l].A.nbr * h.levels[l].A.bs_r ** 2, dtype=torch.float64, device="cuda")
+                B.bamg_mg_get_dinv(gp.ctx, gp.mg, l, d)
+                assert rel(d.cpu().numpy(), h.levels[l].Dinv.reshape(-1)) <= TOL64
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("ne", [8, 24])
+def test_vcycle_matches_oracle(ne):
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        rng = np.random.default_rng(ne)
+        b = rng.standard_normal(gp.mesh.n_dofs)
+        x = torch.zeros_like(torch.from_numpy(b)).cuda()
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x)
+        ref = omg.vcycle(h, b)
+        assert rel(x.cpu().numpy(), ref) <= TOL64
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("ne", [8, 24])
+def test_cg_matches_oracle(ne):
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        b = body_force(gp.mesh)
+        xr, its, info = krylov.pcg(h.levels[0].As, b, lambda r: omg.vcycle(h, r), 1e-8, 200)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x, 1e-8, 200)
+        assert out["converged"]
+        assert abs(out["iterations"] - its) <= 1
+        assert out["true_rnorm"] <= 1.05e-8 * np.linalg.norm(b)
+        assert rel(x.cpu().numpy(), xr) <= 1e-7
+    finally:
+        gp.close()
+
+
+def test_hot_update_matches_oracle():
+    ne = 13
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        for seed in (1, 2):
+            gp.reassemble(seed)
+            B.bamg_mg_update(gp.ctx, gp.mg)
+            _, _, A2 = problem(ne, seed=seed)
+            h2 = omg.update(h, A2)
+            for l in range(h2.n_levels):
+                Al, _ = B.bamg_mg_get_level(gp.mg, l)
+                assert rel(read_bsr(gp.ctx, Al).vals, h2.levels[l].A.vals) <= TOL64
+            b = body_force(gp.mesh)
+            x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+            B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x)
+            assert rel(x.cpu().numpy(), omg.vcycle(h2, b)) <= TOL64
+    finally:
+        gp.close()
+
+
+def test_mixed_precision_cg_reaches_tolerance():
+    ne = 24
+    h = hierarchy(ne)
+    gp = GpuProblem(ne, precision=B.BAMG_FP32)
+    try:
+        b = body_force(gp.mesh)
+        xr, its, _ = krylov.pcg(h.levels[0].As, b, lambda r: omg.vcycle(h, r), 1e-8, 200)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x, 1e-8, 200)
+        assert out["converged"] and out["true_rnorm"] <= 1.05e-8 * np.linalg.norm(b)
+        assert out["iterations"] <= its + 3
+        assert rel(x.cpu().numpy(), xr) <= 1e-6
+        z = torch.zeros_like(x)
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), z)
+        assert rel(z.cpu().numpy(), omg.vcycle(h, b)) <= 1e-4
+    finally:
+        gp.close()
+
+
+def test_nan_values_are_reported():
+    gp = GpuProblem(4)
+    try:
+        gp.vals[5, 1, 1] = float("nan")
+        B.bamg_bsr_coo_set_values(gp.ctx, gp.A, gp.vals, 0)
+        with pytest.raises(B.BamgError) as e:
+            B.bamg_ctx_sync(gp.ctx)
+        assert e.value.status == 5
+    finally:
+        gp.close()
+
+
+def test_cg_maxit_reports_not_converged():
+    gp = GpuProblem(8)
+    try:
+        b = torch.from_numpy(body_force(gp.mesh)).cuda()
+        x = torch.zeros_like(b)
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-12, 3, check=False)
+        assert out["status"] == 7 and out["iterations"] == 3 and not out["converged"]
+    finally:
+        gp.close()
