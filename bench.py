@@ -1,0 +1,476 @@
+#!/usr/bin/env python3
+"""Benchmark of the blocked SA-AMG reuse phase (3D elasticity, Q1 hexahedra).
+
+One step = one reuse step of the hot path on fresh synthetic input: blocked
+COO re-assembly of the perturbed operator, the Galerkin recompute
+A_c = P^T A P on every level, the smoother refresh (block-diagonal inverses,
+eigen-estimates, coarsest factorisation) and CG with the V(2,2) Chebyshev /
+point-block Jacobi V-cycle to rtol 1e-8.  Default workload: 64^3 elements
+(274,625 nodes, 823,875 dofs), 3 levels, FP64; the mixed-precision form is
+measured on the same workload for comparison.
+
+metric: algorithmic bytes of the step (byte model in
+paper_2606_24748_gb300/bytes_model.py) / step time, in GB/s, over all ranks.
+Multi-GPU runs are independent replicas (one problem per rank).
+"""
+import os
+import sys
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_24748_gb300 import bytes_model as bm  # noqa: E402
+from workloads.elasticity import (Mesh, body_force, coo_indices, coo_values, element_scale,  # noqa: E402
+                                  perturbation)
+
+METRIC = "PtAP+V-cycle HBM GB/s; CG time to rtol 1e-8, FP64 vs mixed/learned"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+RTOL = 1e-8
+MAXIT = 500
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ne", type=int, default=64, help="elements per direction")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- byte model
+def level_sizes(B, mg):
+    out = []
+    nl = B.bamg_mg_num_levels(mg)
+    for l in range(nl):
+        A, P = B.bamg_mg_get_level(mg, l)
+        a = B.bamg_bsr_info(A)
+        p = B.bamg_bsr_info(P) if P is not None else None
+        r = None
+        if p is not None:
+            r = {"nnzb": p["nnzb"], "nbr": p["nbc"], "nbc": p["nbr"], "bs_r": p["bs_c"], "bs_c": p["bs_r"]}
+        out.append({"A": a, "P": p, "R": r})
+    return out
+
+
+def step_bytes(levels, n_coo, precond_applications, cg_its, mixed, power_its=15):
+    """Algorithmic bytes of one reuse step (see bytes_model)."""
+    s = 4 if mixed else 8
+    A0 = levels[0]["A"]
+    parts = {}
+    parts["coo"] = bm.coo_bytes(n_coo, A0["nnzb"], 3, 3) + (A0["nnzb"] * 9 * 4 if mixed else 0)
+    ptap = 0
+    for l in range(len(levels) - 1):
+        ptap += bm.ptap_bytes(levels[l]["A"], levels[l]["P"], levels[l + 1]["A"], s)
+    parts["ptap"] = ptap
+    refresh = 0
+    for l in range(len(levels) - 1):
+        a = levels[l]["A"]
+        sa = 8 if (l == 0 or not mixed) else 4
+        n, bs = a["nbr"], a["bs_r"]
+        refresh += n * bs * bs * (sa + 8 + (4 if mixed else 0))                 # Dinv
+        refresh += (power_its + 1) * bm.spmv_bytes(a["nnzb"], n, n, bs, bs, sa)  # eigen-estimate
+    nc = levels[-1]["A"]["nbr"] * levels[-1]["A"]["bs_r"]
+    npad = -(-nc // 32) * 32
+    refresh += 3 * npad * npad * 8
+    parts["refresh"] = refresh
+    vc = sum(bm.vcycle_level_bytes(levels[l]["A"], levels[l]["P"], levels[l]["R"], s)
+             for l in range(len(levels) - 1)) + bm.coarse_solve_bytes(nc)
+    parts["vcycles"] = precond_applications * vc
+    parts["cg"] = cg_its * bm.cg_iteration_bytes(A0) + 4 * 8 * A0["nbr"] * 3
+    return sum(parts.values()), parts, vc
+
+
+# ---------------------------------------------------------------- our arm
+class Workload:
+    def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000):
+        self.B, self.torch = B, torch
+        self.mesh = Mesh(ne)
+        m = self.mesh
+        self.ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+        self.bi, self.bj = coo_indices(m, "cuda")
+        self.n_coo = int(self.bi.numel())
+        self.A = B.bamg_bsr_create(self.ctx, 3, 3, m.n_nodes, m.n_nodes)
+        B.bamg_bsr_coo_preallocate(self.ctx, self.A, self.bi, self.bj)
+        v0 = coo_values(m, nu, element_scale(m), "cuda")
+        B.bamg_bsr_coo_set_values(self.ctx, self.A, v0, 0)
+        o = B.bamg_mg_opts_default()
+        o.grid[0] = o.grid[1] = o.grid[2] = m.m
+        o.precision = B.BAMG_FP32 if precision == "mixed" else B.BAMG_FP64
+        self.mg = B.bamg_mg_setup(self.ctx, self.A, m.coords(), m.dirichlet(), o)
+        del v0
+        # per-step inputs (perturbed operators), resident in HBM
+        self.inputs = [coo_values(m, nu, element_scale(m, delta=perturbation(m.n_el, seed0 + k)), "cuda")
+                       for k in range(n_inputs)]
+        self.b = torch.from_numpy(body_force(m)).cuda()
+        self.x = torch.zeros_like(self.b)
+        self.levels = level_sizes(B, self.mg)
+        self.mixed = precision == "mixed"
+
+    def step(self, k):
+        B = self.B
+        B.bamg_bsr_coo_set_values(self.ctx, self.A, self.inputs[k % len(self.inputs)], 0)
+        B.bamg_mg_update(self.ctx, self.mg)
+        return B.bamg_cg_solve(self.ctx, self.mg, self.b, self.x, RTOL, MAXIT)
+
+    def close(self):
+        B = self.B
+        B.bamg_mg_destroy(self.mg)
+        B.bamg_bsr_destroy(self.A)
+        B.bamg_ctx_destroy(self.ctx)
+
+
+def timed(torch, dist, fn, K):
+    st = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    outs = [fn(k) for k in range(K)]
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1), outs
+
+
+def run_ours(args):
+    import torch
+    from paper_2606_24748_gb300 import bamg as B
+
+    if not os.path.exists(B.LIB_PATH):
+        from paper_2606_24748_gb300.build import build
+        build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    K, W = args.steps, args.warmup
+    wl = Workload(B, torch, args.ne, 0.3, args.precision, n_inputs=min(K + W, 8))
+    for k in range(W):
+        wl.step(k)
+    clocks = Clocks(local)
+    B.bamg_ctx_profile(wl.ctx, 1)
+    launches0 = B.bamg_kernel_launches()
+    clocks.start()
+    ms, outs = timed(torch, dist, lambda k: wl.step(W + k), K)
+    clk = clocks.stop()
+    launches = B.bamg_kernel_launches() - launches0
+    prof = {name: B.bamg_ctx_profile_read(wl.ctx, slot) for name, slot in B.PROF_SLOTS.items()}
+    B.bamg_ctx_profile(wl.ctx, 0)
+    its = [o["iterations"] for o in outs]
+    ms_step = ms / K
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    per_step = [step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]
+    bytes_step = float(np.mean(per_step))
+    value = world * bytes_step / (ms_step / 1e3) / 1e9
+    _, parts, vc_bytes = step_bytes(wl.levels, wl.n_coo, its[-1] + 1, its[-1], wl.mixed)
+
+    roof = roofline(wl, prof, B)
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if wl.mixed else "f64",
+        "data": "synthetic: seeded Q1 elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
+        "config": {"workload": f"elasticity {args.ne}^3 Q1 elements, {wl.mesh.n_dofs} dofs, "
+                               f"{len(wl.levels)}-level SA-AMG, reuse step (COO re-assembly, PtAP all levels, "
+                               f"smoother refresh, PCG V(2,2) Chebyshev to rtol 1e-8), "
+                               f"{'mixed FP32/FP64' if wl.mixed else 'FP64'}",
+                   "elements": args.ne, "dofs": wl.mesh.n_dofs, "levels": len(wl.levels),
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (value stream %.2f GB, fine operator %.2f GB)" % (
+                       wl.n_coo * 72 / 1e9, wl.levels[0]["A"]["nnzb"] * 76 / 1e9)},
+        "cg_iterations": its, "bytes_per_step": int(bytes_step),
+        "bytes_parts": {k: int(v) for k, v in parts.items()},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk,
+        "kernel_ms": {k: {"total_ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items()},
+    }
+    # phases (separate, untimed pass for the breakdown)
+    result["phases_ms"] = phases(wl, torch, B)
+    if not args.no_e2e:
+        result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
+    if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
+        wl.close()
+        wl = None
+        result["mixed"] = compare_mixed(args, torch, B)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(samples=1)
+    if wl is not None:
+        wl.close()
+    if dist:
+        dist.destroy_process_group()
+    return result if rank == 0 else None
+
+
+def roofline(wl, prof, B):
+    """Dominant kernel of the timed region: algorithmic bytes/flops per launch / mean duration."""
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    lv = wl.levels
+    A0 = lv[0]["A"]
+    s = 4 if wl.mixed else 8
+    n, nnzb = A0["nbr"], A0["nnzb"]
+    cand = {}
+    if prof["cheb_step_l0"][1]:
+        # launches alternate between has_next (pre-smoothing step 0, post step 0) and the last pre step
+        bts = (2 * bm.cheb_step_bytes(nnzb, n, 3, s, True) + bm.cheb_step_bytes(nnzb, n, 3, s, False)) / 3
+        fl = 2 * nnzb * 9 + n * (2 * 9 + 8)
+        cand["cheb_step_l0"] = (prof["cheb_step_l0"], bts, fl)
+    if prof["ptap_stage1_l0"][1]:
+        P0, A1 = lv[0]["P"], lv[1]["A"]
+        bts = bm.ptap_bytes(A0, P0, A1, s)
+        cand["ptap_l0"] = ((prof["ptap_stage1_l0"][0] + prof["ptap_stage2_l0"][0], prof["ptap_stage1_l0"][1]), bts,
+                           None)
+    if prof["cg_ap"][1]:
+        bts = bm.spmv_bytes(nnzb, n, n, 3, 3, 8) + 8 * 3 * n
+        cand["cg_ap"] = (prof["cg_ap"], bts, 2 * nnzb * 9 + 6 * n)
+    if not cand:
+        return None
+    name = max(cand, key=lambda k: cand[k][0][0])
+    (tot, cnt), bts, fl = cand[name]
+    avg_s = tot / cnt / 1e3
+    gbs = bts / avg_s / 1e9
+    out = {"kernel": name, "launches": cnt, "avg_ms": round(avg_s * 1e3, 4), "bytes_per_launch": int(bts),
+           "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3), "traffic": None}
+    fp64_bound = (not wl.mixed) and fl is not None and (fl / (FP64_PEAK_TFLOPS * 1e12)) > (bts / (hbm * 1e9))
+    if fp64_bound:
+        tf = fl / avg_s / 1e12
+        out.update({"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 3),
+                    "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"})
+    else:
+        out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(gbs / hbm, 3), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"})
+    return out
+
+
+def phases(wl, torch, B):
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, fn in (("coo_assembly", lambda: B.bamg_bsr_coo_set_values(wl.ctx, wl.A, wl.inputs[0], 0)),
+                     ("mg_update", lambda: B.bamg_mg_update(wl.ctx, wl.mg)),
+                     ("cg_solve", lambda: B.bamg_cg_solve(wl.ctx, wl.mg, wl.b, wl.x, RTOL, MAXIT))):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1), 3)
+    return out
+
+
+def e2e(wl, torch, B, dist, K, W, world, per_step):
+    """Same step through the C ABI with host buffers: the value stream and b
+    copied from pinned host memory, the solution read back, every step."""
+    n_host = min(2, len(wl.inputs))
+    host_in = [t.cpu().pin_memory() for t in wl.inputs[:n_host]]
+    host_b = wl.b.cpu().pin_memory()
+    host_x = torch.empty_like(host_b).pin_memory()
+    dev_in = torch.empty_like(wl.inputs[0])
+
+    def step(k):
+        dev_in.copy_(host_in[k % n_host], non_blocking=True)
+        wl.b.copy_(host_b, non_blocking=True)
+        B.bamg_bsr_coo_set_values(wl.ctx, wl.A, dev_in, 0)
+        B.bamg_mg_update(wl.ctx, wl.mg)
+        out = B.bamg_cg_solve(wl.ctx, wl.mg, wl.b, wl.x, RTOL, MAXIT)
+        host_x.copy_(wl.x, non_blocking=True)
+        return out
+
+    for k in range(min(W, 2)):
+        step(k)
+    ms, outs = timed(torch, dist, step, K)
+    ms_step = ms / K
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    its = [o["iterations"] for o in outs]
+    bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]))
+    return {"value": round(world * bytes_step / (ms_step / 1e3) / 1e9, 2), "unit": "GB/s",
+            "ms_per_step": round(ms_step, 4),
+            "h2d_bytes_per_step": int(host_in[0].numel() * 8 + host_b.numel() * 8),
+            "d2h_bytes_per_step": int(host_x.numel() * 8)}
+
+
+def compare_mixed(args, torch, B):
+    """Time to rtol 1e-8 of the mixed-precision form on the same workload."""
+    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=2)
+    for k in range(2):
+        wl.step(k)
+    K = max(3, min(args.steps, 10))
+    ms, outs = timed(torch, None, lambda k: wl.step(k), K)
+    ph = phases(wl, torch, B)
+    x = wl.x.clone()
+    its = [o["iterations"] for o in outs]
+    res = {"ms_per_step": round(ms / K, 4), "cg_iterations": its, "phases_ms": ph,
+           "true_residual_rel": outs[-1]["true_rnorm"] / outs[-1]["bnorm"]}
+    wl.close()
+    del x
+    return res
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def oracle_step_sample(ne=24, seed=1):
+    """One reuse step of the oracle on a smaller mesh of the same problem."""
+    from oracle import krylov
+    from oracle import multigrid as omg
+    from oracle.assembly import coo_assemble_blocks
+    m = Mesh(ne)
+    bi, bj = coo_indices(m)
+    bi, bj = bi.numpy(), bj.numpy()
+    v0 = coo_values(m, 0.3, element_scale(m)).numpy()
+    h = omg.setup(coo_assemble_blocks(m.n_nodes, m.n_nodes, 3, 3, bi, bj, v0), m.coords(), m.dirichlet(), m.grid)
+    v = coo_values(m, 0.3, element_scale(m, delta=perturbation(m.n_el, seed))).numpy()
+    b = body_force(m)
+    t0 = time.perf_counter()
+    A = coo_assemble_blocks(m.n_nodes, m.n_nodes, 3, 3, bi, bj, v)
+    h2 = omg.update(h, A)
+    x, its, info = krylov.pcg(h2.levels[0].As, b, lambda r: omg.vcycle(h2, r), RTOL, MAXIT)
+    dt = time.perf_counter() - t0
+    levels = []
+    for l, L in enumerate(h2.levels):
+        a = {"nnzb": L.A.nnzb, "nbr": L.A.nbr, "nbc": L.A.nbc, "bs_r": L.A.bs_r, "bs_c": L.A.bs_c}
+        p = r = None
+        if L.P is not None:
+            p = {"nnzb": L.P.nnzb, "nbr": L.P.nbr, "nbc": L.P.nbc, "bs_r": L.P.bs_r, "bs_c": L.P.bs_c}
+            r = {"nnzb": L.P.nnzb, "nbr": L.P.nbc, "nbc": L.P.nbr, "bs_r": L.P.bs_c, "bs_c": L.P.bs_r}
+        levels.append({"A": a, "P": p, "R": r})
+    nbytes = step_bytes(levels, int(bi.size), its + 1, its, False)[0]
+    return dt, nbytes, its
+
+
+def cpu_baseline(samples=1, ne=24):
+    tot_t, tot_b = 0.0, 0.0
+    for k in range(samples):
+        dt, nb, _ = oracle_step_sample(ne, seed=k + 1)
+        tot_t += dt
+        tot_b += nb
+    return {"value": round(tot_b / tot_t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{samples} oracle reuse step(s) (COO assembly, Galerkin products, smoother refresh, "
+                      f"PCG to 1e-8) of the same elasticity problem at {ne}^3 elements "
+                      f"({3 * (ne + 1) ** 3} dofs), single-threaded scipy/numpy on the host",
+            "seconds": round(tot_t, 2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    K, W = args.steps, args.warmup
+    ne = 16
+    for k in range(W):
+        oracle_step_sample(ne, seed=100 + k)
+    tt, tb = 0.0, 0.0
+    for k in range(K):
+        dt, nb, _ = oracle_step_sample(ne, seed=k + 1)
+        tt += dt
+        tb += nb
+    value = tb / tt / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": round(tt / K * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: seeded Q1 elasticity", "config": {"workload": f"oracle sample: {ne}^3 elements"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "kind": "oracle", "cores": 1,
+                             "sample": f"oracle reuse step on {ne}^3 elements per step"},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -76,6 +76,28 @@ BAMG_API const char* bamg_last_error(const bamg_ctx* ctx);
  * status (and clear it). */
 BAMG_API bamg_status bamg_ctx_sync(bamg_ctx* ctx);
 
+/* Kernel timing for benchmarks.  While enabled, the library brackets the
+ * launches of the kernels listed in bamg_prof_slot with CUDA events on the
+ * context's stream (inside CUDA graphs as external event-record nodes) and
+ * accumulates their device time.  Enabling resets the totals.  _read waits
+ * for the stream, then returns the total milliseconds and launch count of a
+ * slot (kernels that only returned early are not counted). */
+typedef enum {
+  BAMG_PROF_CHEB_STEP_L0 = 0,   /* fused Chebyshev step on the finest level */
+  BAMG_PROF_CHEB_RINIT_L0 = 1,  /* fused residual + first direction, finest level */
+  BAMG_PROF_PTAP_STAGE1_L0 = 2, /* Galerkin stage Z = A P, finest level */
+  BAMG_PROF_PTAP_STAGE2_L0 = 3, /* Galerkin stage A_c = P^T Z, finest level */
+  BAMG_PROF_CG_AP = 4,          /* CG product q = A p */
+  BAMG_PROF_COO = 5,            /* blocked COO numeric assembly */
+  BAMG_PROF_COARSE_FACTOR = 6,  /* whole coarsest-level factorisation */
+  BAMG_PROF_COUNT = 7
+} bamg_prof_slot;
+BAMG_API bamg_status bamg_ctx_profile(bamg_ctx* ctx, int enable);
+BAMG_API bamg_status bamg_ctx_profile_read(bamg_ctx* ctx, int slot, double* total_ms, int64_t* launches);
+/* Number of kernels this library has launched in this process (kernels run
+ * through CUDA graphs included, counted per graph launch). */
+BAMG_API uint64_t bamg_kernel_launches(void);
+
 /* ------------------------------------------------------- block matrices */
 
 /* Rectangular-block sparse matrix (Sec. 2.3: independent row and column block
@@ -122,6 +144,16 @@ BAMG_API bamg_status bamg_bsr_spmv(bamg_bsr* A, const void* x, void* y, bamg_pre
  * (1 <= k <= 32), right-hand-side-minor layout: X[dof * k + j]. */
 BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, bamg_prec prec);
 
+/* Lanes per block row used by this matrix's row kernels (a power of two in
+ * 1..32): 1 = one row per lane (long matrices), more lanes for few, long rows
+ * (restrictions, coarse levels).  _autotune times the FP64 product for every
+ * width on the context's stream and keeps the fastest (allocates two work
+ * vectors; returns the choice and its time in ms, either may be NULL).
+ * Results do not depend on the choice beyond summation order. */
+BAMG_API bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms);
+BAMG_API bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes);
+BAMG_API bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes);
+
 /* ----------------------------------------------------- Galerkin product */
 
 /* Symbolic Galerkin product (Sec. 3.1, Sec. 3.5): A (n x n blocks of
@@ -157,6 +189,8 @@ typedef struct {
   int precision;            /* bamg_prec of the V-cycle: FP64, or FP32 = mixed form
                                (FP32 operators, smoother and vectors; FP64 CG,
                                eigen-estimates and coarsest solve) */
+  int autotune;             /* 1 (default): bamg_bsr_autotune every level's
+                               operator, prolongator and restriction at setup */
 } bamg_mg_opts;
 
 typedef struct {

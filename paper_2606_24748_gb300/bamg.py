@@ -23,6 +23,8 @@ STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG
                 5: "BAMG_ERR_NAN", 6: "BAMG_ERR_BREAKDOWN", 7: "BAMG_ERR_NOT_CONVERGED", 8: "BAMG_ERR_TIMEOUT"}
 BAMG_FP64 = 0
 BAMG_FP32 = 1
+PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
+              "coo": 5, "coarse_factor": 6}
 
 
 class BamgError(RuntimeError):
@@ -35,7 +37,7 @@ class bamg_mg_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int), ("max_coarse_dofs", ctypes.c_int64),
                 ("grid", ctypes.c_int * 3), ("cheb_degree", ctypes.c_int),
                 ("cheb_lower", ctypes.c_double), ("cheb_upper", ctypes.c_double),
-                ("power_its", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("power_its", ctypes.c_int), ("precision", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class bamg_cg_info(ctypes.Structure):
@@ -50,6 +52,8 @@ _SIGS = {
     "bamg_ctx_create": [_P, _PP],
     "bamg_ctx_destroy": [_P],
     "bamg_ctx_sync": [_P],
+    "bamg_ctx_profile": [_P, ctypes.c_int],
+    "bamg_ctx_profile_read": [_P, ctypes.c_int, _P, _P],
     "bamg_bsr_create": [_P, ctypes.c_int, ctypes.c_int, _I64, _I64, _PP],
     "bamg_bsr_destroy": [_P],
     "bamg_bsr_coo_preallocate": [_P, _I64, _P, _P],
@@ -59,6 +63,9 @@ _SIGS = {
     "bamg_bsr_get_values": [_P, _P],
     "bamg_bsr_set_symmetric": [_P, ctypes.c_int],
     "bamg_bsr_spmv": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
+    "bamg_bsr_autotune": [_P, _P, _P],
+    "bamg_bsr_set_lanes": [_P, ctypes.c_int],
+    "bamg_bsr_get_lanes": [_P, _P],
     "bamg_bsr_spmm": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
     "bamg_ptap_symbolic": [_P, _P, _PP, _PP],
     "bamg_ptap_numeric": [_P, _P, _P, _P],
@@ -94,6 +101,8 @@ def lib() -> ctypes.CDLL:
         L.bamg_last_error.restype = ctypes.c_char_p
         L.bamg_mg_opts_default.argtypes = [ctypes.POINTER(bamg_mg_opts)]
         L.bamg_mg_opts_default.restype = None
+        L.bamg_kernel_launches.argtypes = []
+        L.bamg_kernel_launches.restype = ctypes.c_uint64
         _lib = L
     return _lib
 
@@ -132,6 +141,20 @@ def bamg_last_error(ctx) -> str:
 
 def bamg_ctx_sync(ctx):
     _check(lib().bamg_ctx_sync(ctx), ctx)
+
+
+def bamg_ctx_profile(ctx, enable: int):
+    _check(lib().bamg_ctx_profile(ctx, int(enable)), ctx)
+
+
+def bamg_ctx_profile_read(ctx, slot: int) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().bamg_ctx_profile_read(ctx, int(slot), ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def bamg_kernel_launches() -> int:
+    return int(lib().bamg_kernel_launches())
 
 
 # ---------------------------------------------------------- block matrices
@@ -175,6 +198,22 @@ def bamg_bsr_get_values(ctx, A, vals):
 
 def bamg_bsr_set_symmetric(ctx, A, symmetric: int):
     _check(lib().bamg_bsr_set_symmetric(A, int(symmetric)), ctx)
+
+
+def bamg_bsr_autotune(ctx, A) -> tuple[int, float]:
+    lanes, ms = ctypes.c_int(), ctypes.c_float()
+    _check(lib().bamg_bsr_autotune(A, ctypes.byref(lanes), ctypes.byref(ms)), ctx)
+    return lanes.value, ms.value
+
+
+def bamg_bsr_set_lanes(ctx, A, lanes: int):
+    _check(lib().bamg_bsr_set_lanes(A, int(lanes)), ctx)
+
+
+def bamg_bsr_get_lanes(A) -> int:
+    v = ctypes.c_int()
+    _check(lib().bamg_bsr_get_lanes(A, ctypes.byref(v)), None)
+    return v.value
 
 
 def bamg_bsr_spmv(ctx, A, x, y, prec: int = BAMG_FP64, transpose: int = 0):
@@ -269,4 +308,4 @@ def bamg_mg_destroy(mg):
 
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding declares."""
-    return sorted(list(_SIGS) + ["bamg_last_error", "bamg_mg_opts_default"])
+    return sorted(list(_SIGS) + ["bamg_last_error", "bamg_mg_opts_default", "bamg_kernel_launches"])

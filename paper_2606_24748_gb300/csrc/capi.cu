@@ -8,6 +8,74 @@
 
 namespace bamg {
 
+std::atomic<unsigned long long> g_launches{0};
+thread_local bool g_capturing = false;
+
+static ProfPair* prof_slot_pair(bamg_ctx* ctx, int* idx) {
+  Prof& p = ctx->prof;
+  if (p.sink) {  // no event creation while a stream is being captured
+    if (p.sink_used >= p.sink->size()) return nullptr;
+    *idx = (int)p.sink_used++;
+    return &(*p.sink)[*idx];
+  }
+  if (p.eager_used >= p.eager.size()) {
+    ProfPair q;
+    if (cudaEventCreate(&q.a) != cudaSuccess || cudaEventCreate(&q.b) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    p.eager.push_back(q);
+  }
+  *idx = (int)p.eager_used++;
+  return &p.eager[*idx];
+}
+
+static cudaError_t record(cudaEvent_t e, cudaStream_t st) {
+  return g_capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+}
+
+int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st) {
+  if (!ctx || !ctx->prof.on || slot < 0) return -1;
+  int idx = -1;
+  ProfPair* q = prof_slot_pair(ctx, &idx);
+  if (!q) return -1;
+  q->slot = slot;
+  q->pos = ctx->prof.pos;
+  if (record(q->a, st) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return idx;
+}
+
+void prof_end(bamg_ctx* ctx, int idx, cudaStream_t st) {
+  if (idx < 0 || !ctx->prof.on) return;
+  Prof& p = ctx->prof;
+  std::vector<ProfPair>& v = p.sink ? *p.sink : p.eager;
+  if (record(v[idx].b, st) != cudaSuccess) cudaGetLastError();
+}
+
+// Accumulate the first `count` pairs.  Graph-owned pairs carry the CG
+// iteration position: the A p product ran in positions < active_ap, the
+// preconditioner in positions < active_vc (later launches returned at once).
+void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int active_ap, int active_vc) {
+  Prof& p = ctx->prof;
+  for (size_t i = 0; i < count && i < pairs.size(); ++i) {
+    const ProfPair& q = pairs[i];
+    if (active_ap >= 0) {
+      const int lim = q.slot == BAMG_PROF_CG_AP ? active_ap : active_vc;
+      if (q.pos >= lim) continue;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      p.ms[q.slot] += ms;
+      p.n[q.slot] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+}
+
 Status make_status(bamg_status code, const char* fmt, ...) {
   Status s;
   s.code = code;
@@ -129,6 +197,8 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   A->vals32_version = ~0ull;
   A->vals64_stale = false;
   A->has_pattern = true;
+  A->vec = default_vec(A);
+  A->vec_tuned = false;
   A->version++;
   static uint64_t next_pattern_id = 0;
   A->pattern_id = ++next_pattern_id;
@@ -156,7 +226,7 @@ __global__ void k_to_fp32(const double* __restrict__ s, float* __restrict__ d, i
 Status launch_to_fp32(const double* src, float* dst, int64_t n, cudaStream_t st) {
   if (n <= 0) return Status{};
   const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_to_fp32<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+  { k_to_fp32<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -175,7 +245,7 @@ Status launch_gather_blocks(const bamg_bsr* A, const double* vals, double* out, 
   const int B = (int)A->block_elems();
   const int64_t n = A->nnzb * B;
   if (n == 0) return Status{};
-  k_get_values_any<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A->slot_of, vals, out, A->nnzb, B);
+  { k_get_values_any<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A->slot_of, vals, out, A->nnzb, B); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -215,6 +285,10 @@ bamg_status bamg_ctx_create(void* cuda_stream, bamg_ctx** out) {
 
 bamg_status bamg_ctx_destroy(bamg_ctx* c) {
   if (!c) return BAMG_OK;
+  for (auto& q : c->prof.eager) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
   dfree(c->d_err, c->stream);
   dfree(c->d_partials, c->stream);
   dfree(c->d_counters, c->stream);
@@ -224,6 +298,33 @@ bamg_status bamg_ctx_destroy(bamg_ctx* c) {
 }
 
 const char* bamg_last_error(const bamg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+bamg_status bamg_ctx_profile(bamg_ctx* c, int enable) {
+  if (!c) return BAMG_ERR_INVALID;
+  Prof& p = c->prof;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, cuda_status(cudaGetLastError(), "profile"));
+  p.on = enable != 0;
+  p.epoch++;
+  p.eager_used = 0;
+  for (int k = 0; k < BAMG_PROF_COUNT; ++k) {
+    p.ms[k] = 0.0;
+    p.n[k] = 0;
+  }
+  return BAMG_OK;
+}
+
+bamg_status bamg_ctx_profile_read(bamg_ctx* c, int slot, double* total_ms, int64_t* launches) {
+  if (!c || slot < 0 || slot >= BAMG_PROF_COUNT) return BAMG_ERR_INVALID;
+  Prof& p = c->prof;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, cuda_status(cudaGetLastError(), "profile"));
+  prof_harvest(c, p.eager, p.eager_used, -1, -1);
+  p.eager_used = 0;
+  if (total_ms) *total_ms = p.ms[slot];
+  if (launches) *launches = p.n[slot];
+  return BAMG_OK;
+}
+
+uint64_t bamg_kernel_launches(void) { return g_launches.load(); }
 
 bamg_status bamg_ctx_sync(bamg_ctx* c) {
   if (!c) return BAMG_ERR_INVALID;
@@ -298,6 +399,28 @@ bamg_status bamg_bsr_set_symmetric(bamg_bsr* A, int symmetric) {
   if (symmetric && (A->br != A->bc || A->nbr != A->nbc))
     return fail(A->ctx, make_status(BAMG_ERR_INVALID, "only square matrices can be symmetric"));
   A->symmetric = symmetric != 0;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms) {
+  if (!A) return BAMG_ERR_INVALID;
+  Status s = bsr_autotune(A, ms);
+  if (!s.ok()) return fail(A->ctx, s);
+  if (lanes) *lanes = A->vec;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
+  if (!A) return BAMG_ERR_INVALID;
+  if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
+    return fail(A->ctx, make_status(BAMG_ERR_INVALID, "lanes must be a power of two in [1, 32]"));
+  A->vec = lanes;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes) {
+  if (!A || !lanes) return BAMG_ERR_INVALID;
+  *lanes = A->vec;
   return BAMG_OK;
 }
 

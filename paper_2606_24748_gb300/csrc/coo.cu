@@ -95,7 +95,7 @@ static Status coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const i
     BAMG_TRY(dalloc(&bad, 1, st));
     BAMG_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32);
-    k_coo_keys<<<blocks, 256, 0, st>>>(bi, bj, n, A->nbr, A->nbc, keys, idx, bad);
+    { k_coo_keys<<<blocks, 256, 0, st>>>(bi, bj, n, A->nbr, A->nbc, keys, idx, bad); BAMG_COUNT_LAUNCH; }
     BAMG_CUDA(cudaGetLastError());
     int hbad = 0;
     BAMG_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -146,18 +146,20 @@ static Status coo_set_values(bamg_bsr* A, const double* v, int add) {
   float* v32 = (A->vals32 && A->vals32_version == A->version) ? A->vals32 : nullptr;
   if (nt > 0) {
     const unsigned blocks = (unsigned)((nt + 255) / 256);
+    const int pm = prof_begin(A->ctx, BAMG_PROF_COO, st);
     if (B == 9)
-      k_coo_sum<9><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
-                                           A->ctx->d_err);
+      { k_coo_sum<9><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                           A->ctx->d_err); BAMG_COUNT_LAUNCH; }
     else if (B == 36)
-      k_coo_sum<36><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
-                                            A->ctx->d_err);
+      { k_coo_sum<36><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                            A->ctx->d_err); BAMG_COUNT_LAUNCH; }
     else if (B == 18)
-      k_coo_sum<18><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
-                                            A->ctx->d_err);
+      { k_coo_sum<18><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
+                                            A->ctx->d_err); BAMG_COUNT_LAUNCH; }
     else
-      k_coo_sum_any<<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, B, A->vals, v32, add,
-                                            A->ctx->d_err);
+      { k_coo_sum_any<<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, B, A->vals, v32, add,
+                                            A->ctx->d_err); BAMG_COUNT_LAUNCH; }
+    prof_end(A->ctx, pm, st);
     BAMG_CUDA(cudaGetLastError());
   }
   A->version++;

@@ -56,20 +56,23 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* _
 }
 
 // x += d_in; r -= A d_in; if has_next: d_out = c1 d_in + c2 w Dinv r
-template <int BS, typename T>
+template <int BS, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict__ sp, const int* __restrict__ col,
-                                                           const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                           const T* __restrict__ vals, int64_t n, int64_t nthreads,
                                                            const T* __restrict__ d_in, T* __restrict__ d_out,
                                                            T* __restrict__ x, T* __restrict__ r,
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
                                                            const double* __restrict__ scal, int k, int has_next,
                                                            const int* done) {
   BAMG_DONE_RETURN
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= rows_pad) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  int64_t i;
+  int sub;
+  row_of_thread<V>(t, i, sub);
   T acc[BS];
-  row_product<BS, BS, T, T, T>(sp, col, vals, d_in, i, acc);
-  if (i >= n) return;
+  row_product<BS, BS, V, T, T, T>(sp, col, vals, d_in, i, sub, acc);
+  if (sub != 0 || i >= n) return;
   T di[BS], ri[BS];
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
@@ -89,19 +92,22 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
 }
 
 // r = b - A x; d = w Dinv r / theta   (x is read by the product: not written here)
-template <int BS, typename T>
+template <int BS, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restrict__ sp, const int* __restrict__ col,
-                                                            const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                            const T* __restrict__ vals, int64_t n, int64_t nthreads,
                                                             const T* __restrict__ x, const T* __restrict__ b,
                                                             T* __restrict__ r, T* __restrict__ d,
                                                             const T* __restrict__ dinv, const float* __restrict__ w,
                                                             const double* __restrict__ scal, const int* done) {
   BAMG_DONE_RETURN
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= rows_pad) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  int64_t i;
+  int sub;
+  row_of_thread<V>(t, i, sub);
   T acc[BS];
-  row_product<BS, BS, T, T, T>(sp, col, vals, x, i, acc);
-  if (i >= n) return;
+  row_product<BS, BS, V, T, T, T>(sp, col, vals, x, i, sub, acc);
+  if (sub != 0 || i >= n) return;
   T ri[BS], z[BS];
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
@@ -122,17 +128,20 @@ __global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ 
 }
 
 // y = M v (restriction with R = P^T), or y += M v (prolongation with P)
-template <int BR, int BC, typename T>
+template <int BR, int BC, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_transfer(const int* __restrict__ sp, const int* __restrict__ col,
-                                                          const T* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                          const T* __restrict__ vals, int64_t n, int64_t nthreads,
                                                           const T* __restrict__ v, T* __restrict__ y, int accumulate,
                                                           const int* done) {
   BAMG_DONE_RETURN
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= rows_pad) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  int64_t i;
+  int sub;
+  row_of_thread<V>(t, i, sub);
   T acc[BR];
-  row_product<BR, BC, T, T, T>(sp, col, vals, v, i, acc);
-  if (i >= n) return;
+  row_product<BR, BC, V, T, T, T>(sp, col, vals, v, i, sub, acc);
+  if (sub != 0 || i >= n) return;
 #pragma unroll
   for (int a = 0; a < BR; ++a) y[i * BR + a] = accumulate ? y[i * BR + a] + acc[a] : acc[a];
 }
@@ -170,17 +179,20 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
-  const int64_t rows = A->nslices * kSlice;
+  const int64_t rows = row_threads(A);
   const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
   const unsigned gn = (unsigned)((L.n + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
-  k_cheb_init<BS, T><<<gn, kRowThreads, 0, st>>>(L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done);
+  { k_cheb_init<BS, T><<<gn, kRowThreads, 0, st>>>(L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; }
   T* d[2] = {p.d0, p.d1};
-  for (int k = 0; k < m; ++k)
-    k_cheb_step<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+  for (int k = 0; k < m; ++k) {
+    const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
+    BAMG_DISPATCH_V(A->vec, { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                    d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                   k + 1 < m ? 1 : 0, done);
+                                                   k + 1 < m ? 1 : 0, done); BAMG_COUNT_LAUNCH; })
+    prof_end(mg->ctx, pm, st);
+  }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -190,18 +202,23 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
-  const int64_t rows = A->nslices * kSlice;
+  const int64_t rows = row_threads(A);
   const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
-  k_cheb_rinit<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
-                                                  p.d0, p.dinv, L.weights, sc, done);
+  const int pr = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_RINIT_L0 : -1, st);
+  BAMG_DISPATCH_V(A->vec, { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+                                                  p.d0, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; })
+  prof_end(mg->ctx, pr, st);
   T* d[2] = {p.d0, p.d1};
-  for (int k = 0; k + 1 < m; ++k)
-    k_cheb_step<BS, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
-                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done);
+  for (int k = 0; k + 1 < m; ++k) {
+    const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
+    BAMG_DISPATCH_V(A->vec, { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done); BAMG_COUNT_LAUNCH; })
+    prof_end(mg->ctx, pm, st);
+  }
   const int64_t mm = L.n * BS;
-  k_axpy_done<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(mm, d[(m - 1) & 1], p.x, done);
+  { k_axpy_done<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(mm, d[(m - 1) & 1], p.x, done); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -209,10 +226,10 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
 template <int BR, int BC, typename T>
 static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int accumulate, const int* done,
                        cudaStream_t st) {
-  const int64_t rows = M->nslices * kSlice;
+  const int64_t rows = row_threads(M);
   if (rows == 0) return Status{};
-  k_transfer<BR, BC, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
-      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done);
+  BAMG_DISPATCH_V(M->vec, { k_transfer<BR, BC, V, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
+      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -262,13 +279,13 @@ static Status precond(bamg_mg* mg, const double* r, double* z, const int* done, 
   const int64_t m = L0.n * L0.bs;
   const unsigned g = (unsigned)((m + 255) / 256);
   if (mg->opts.precision == BAMG_FP32) {
-    k_cast_done<double, float><<<g, 256, 0, st>>>(m, r, L0.b32, done);
+    { k_cast_done<double, float><<<g, 256, 0, st>>>(m, r, L0.b32, done); BAMG_COUNT_LAUNCH; }
     BAMG_TRY(vcycle_on<float>(mg, done, st));
-    k_cast_done<float, double><<<g, 256, 0, st>>>(m, L0.x32, z, done);
+    { k_cast_done<float, double><<<g, 256, 0, st>>>(m, L0.x32, z, done); BAMG_COUNT_LAUNCH; }
   } else {
-    if (r != L0.b) k_cast_done<double, double><<<g, 256, 0, st>>>(m, r, L0.b, done);
+    if (r != L0.b) { k_cast_done<double, double><<<g, 256, 0, st>>>(m, r, L0.b, done); BAMG_COUNT_LAUNCH; }
     BAMG_TRY(vcycle_on<double>(mg, done, st));
-    if (z != L0.x) k_cast_done<double, double><<<g, 256, 0, st>>>(m, L0.x, z, done);
+    if (z != L0.x) { k_cast_done<double, double><<<g, 256, 0, st>>>(m, L0.x, z, done); BAMG_COUNT_LAUNCH; }
   }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
@@ -323,17 +340,21 @@ __global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double
 }
 
 // q = A p, alpha = rz / (p.q)
+template <int V>
 __global__ void __launch_bounds__(kRowThreads) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
-                                                       const double* __restrict__ vals, int64_t n, int64_t rows_pad,
+                                                       const double* __restrict__ vals, int64_t n, int64_t nthreads,
                                                        const double* __restrict__ p, double* __restrict__ q,
                                                        CgState* s, double* partials, unsigned* counter) {
   if (s->done) return;
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad; i += stride) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+    int64_t i;
+    int sub;
+    row_of_thread<V>(t, i, sub);
     double acc[3];
-    row_product<3, 3, double, double, double>(sp, col, vals, p, i, acc);
-    if (i < n) {
+    row_product<3, 3, V, double, double, double>(sp, col, vals, p, i, sub, acc);
+    if (sub == 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         q[i * 3 + a] = acc[a];
@@ -412,17 +433,21 @@ __global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restri
 }
 
 // ||b - A x||^2 into s->pq (final true residual)
+template <int V>
 __global__ void __launch_bounds__(kRowThreads) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
                                                                const double* __restrict__ vals, int64_t n,
-                                                               int64_t rows_pad, const double* __restrict__ x,
+                                                               int64_t nthreads, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* out_norm2,
                                                                double* partials, unsigned* counter) {
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad; i += stride) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+    int64_t i;
+    int sub;
+    row_of_thread<V>(t, i, sub);
     double acc[3];
-    row_product<3, 3, double, double, double>(sp, col, vals, x, i, acc);
-    if (i < n) {
+    row_product<3, 3, V, double, double, double>(sp, col, vals, x, i, sub, acc);
+    if (sub == 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double t = b[i * 3 + a] - acc[a];
@@ -444,44 +469,101 @@ static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
   Level& L0 = mg->levels[0];
   const bamg_bsr* A = L0.A;
-  const int64_t m = L0.n * 3, rows = A->nslices * kSlice;
+  const int64_t m = L0.n * 3, rows = row_threads(A);
   CgState* s = mg->cg;
   const int* done = &s->done;
-  k_cg_Ap<<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
-                                                  ctx->d_partials, ctx->d_counters + 2);
-  k_cg_xr<<<vec_grid(m), 256, 0, st>>>(m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3);
+  const int pa = prof_begin(ctx, BAMG_PROF_CG_AP, st);
+  BAMG_DISPATCH_V(A->vec, { k_cg_Ap<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+                                                  ctx->d_partials, ctx->d_counters + 2); BAMG_COUNT_LAUNCH; })
+  prof_end(ctx, pa, st);
+  { k_cg_xr<<<vec_grid(m), 256, 0, st>>>(m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3); BAMG_COUNT_LAUNCH; }
   BAMG_TRY(precond(mg, r, z, done, st));
-  k_cg_dots<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->czold, s, ctx->d_partials, ctx->d_counters + 4);
-  k_cg_p<<<vec_grid(m), 256, 0, st>>>(m, z, mg->cp, mg->czold, s);
+  { k_cg_dots<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->czold, s, ctx->d_partials, ctx->d_counters + 4); BAMG_COUNT_LAUNCH; }
+  { k_cg_p<<<vec_grid(m), 256, 0, st>>>(m, z, mg->cp, mg->czold, s); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
 
+static void cg_graphs_release(bamg_mg* mg) {
+  for (auto g : mg->cg_graphs)
+    if (g) cudaGraphExecDestroy(g);
+  mg->cg_graphs.clear();
+  for (auto& v : mg->cg_pairs)
+    for (auto& q : v) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+  mg->cg_pairs.clear();
+  mg->cg_pairs_used.clear();
+}
+
+constexpr int kCgChunk = 4;  // iterations launched between convergence checks
+
+// Capture one CG iteration into a graph; with profiling on, one graph per
+// position in a chunk so that each owns its timing events.
 static Status cg_graph(bamg_mg* mg, double* r, double* z) {
-  if (mg->cg_graph) return Status{};
+  bamg_ctx* ctx = mg->ctx;
+  if (!mg->cg_graphs.empty() && mg->cg_graph_epoch == ctx->prof.epoch) return Status{};
+  cg_graphs_release(mg);
+  const int ng = ctx->prof.on ? kCgChunk : 1;
   cudaStream_t cs = nullptr;
   BAMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaGraph_t g = nullptr;
+  mg->cg_pairs.resize(ng);
+  mg->cg_pairs_used.assign(ng, 0);
+  if (ctx->prof.on)
+    for (auto& v : mg->cg_pairs) {
+      v.resize(16);
+      for (auto& q : v) {
+        BAMG_CUDA(cudaEventCreate(&q.a));
+        BAMG_CUDA(cudaEventCreate(&q.b));
+      }
+    }
   Status s;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    s = cuda_status(e, "begin capture");
-  } else {
+  for (int p = 0; p < ng && s.ok(); ++p) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      s = cuda_status(e, "begin capture");
+      break;
+    }
+    g_capturing = true;
+    ctx->prof.sink = &mg->cg_pairs[p];
+    ctx->prof.sink_used = 0;
+    ctx->prof.pos = p;
     s = cg_iteration(mg, r, z, cs);
+    mg->cg_pairs_used[p] = ctx->prof.sink_used;
+    ctx->prof.sink = nullptr;
+    ctx->prof.pos = 0;
+    g_capturing = false;
     e = cudaStreamEndCapture(cs, &g);
     if (s.ok() && e != cudaSuccess) s = cuda_status(e, "end capture");
     if (s.ok()) {
-      e = cudaGraphInstantiate(&mg->cg_graph, g, 0);
-      if (e != cudaSuccess) {
-        s = cuda_status(e, "graph instantiate");
-        mg->cg_graph = nullptr;
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      cudaGraphGetNodes(g, nodes.data(), &nn);
+      uint64_t kn = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
       }
+      mg->cg_graph_kernels = kn;
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      if (e != cudaSuccess)
+        s = cuda_status(e, "graph instantiate");
+      else
+        mg->cg_graphs.push_back(ex);
     }
     if (g) cudaGraphDestroy(g);
   }
   cudaStreamDestroy(cs);
+  if (!s.ok()) cg_graphs_release(mg);
+  mg->cg_graph_epoch = ctx->prof.epoch;
   return s;
 }
+
+void mg_release_graphs(bamg_mg* mg) { cg_graphs_release(mg); }
 
 static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit, bamg_cg_info* info) {
   bamg_ctx* ctx = mg->ctx;
@@ -493,26 +575,39 @@ static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int
   double* z = f64 ? L0.x : mg->cz;
   CgState* s = mg->cg;
   BAMG_TRY(cg_graph(mg, r, z));
-  k_cg_setup<<<1, 1, 0, st>>>(s, rtol, maxit);
-  k_cg_init<<<vec_grid(m), 256, 0, st>>>(m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5);
+  { k_cg_setup<<<1, 1, 0, st>>>(s, rtol, maxit); BAMG_COUNT_LAUNCH; }
+  { k_cg_init<<<vec_grid(m), 256, 0, st>>>(m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5); BAMG_COUNT_LAUNCH; }
   BAMG_TRY(precond(mg, r, z, &s->done, st));
-  k_cg_first<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6);
+  { k_cg_first<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
-  int launched = 0, chunk = 4;
-  while (launched < maxit) {
-    const int c = std::min(chunk, maxit - launched);
-    for (int k = 0; k < c; ++k) BAMG_CUDA(cudaGraphLaunch(mg->cg_graph, st));
+  BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+  BAMG_CUDA(cudaStreamSynchronize(st));
+  int launched = 0;
+  int its_before = mg->cg_host->its;
+  const int ng = (int)mg->cg_graphs.size();
+  while (launched < maxit && !mg->cg_host->done) {
+    const int c = std::min(kCgChunk, maxit - launched);
+    for (int k = 0; k < c; ++k) {
+      BAMG_CUDA(cudaGraphLaunch(mg->cg_graphs[k % ng], st));
+      g_launches.fetch_add(mg->cg_graph_kernels, std::memory_order_relaxed);
+    }
     launched += c;
     BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     BAMG_CUDA(cudaStreamSynchronize(st));
-    if (mg->cg_host->done) break;
+    if (ng > 1) {
+      const int its_now = mg->cg_host->its;
+      const int active_ap = its_now - its_before;
+      const int active_vc = active_ap - (mg->cg_host->done ? 1 : 0);
+      for (int k = 0; k < c; ++k) prof_harvest(ctx, mg->cg_pairs[k], mg->cg_pairs_used[k], active_ap, active_vc);
+      its_before = its_now;
+    }
   }
   if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   const bamg_bsr* A = L0.A;
-  const int64_t rows = A->nslices * kSlice;
+  const int64_t rows = row_threads(A);
   double* tr = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel + 8;
-  k_true_residual<<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
-                                                          tr, ctx->d_partials, ctx->d_counters + 7);
+  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+                                                          tr, ctx->d_partials, ctx->d_counters + 7); BAMG_COUNT_LAUNCH; })
   double tr2 = 0.0;
   BAMG_CUDA(cudaMemcpyAsync(&tr2, tr, sizeof(double), cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));

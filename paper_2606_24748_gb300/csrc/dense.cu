@@ -7,6 +7,8 @@
 // Tiled right-looking algorithms, one kernel per tile step:
 //   Cholesky   for k: factor tile (k,k); L(i,k) = A(i,k) L(k,k)^-T; A(i,j) -= L(i,k) L(j,k)^T
 //   W = L^-1   for i: W(i,k) = L(i,i)^-1 (delta_ik I - S(i,k)), k <= i;  S(r,k) += L(r,i) W(i,k), r > i
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "device.cuh"
@@ -37,67 +39,14 @@ __global__ void k_dense_init(double* __restrict__ M, int64_t n, int64_t npad) {
   M[t] = (i == j && i >= n) ? 1.0 : 0.0;
 }
 
-// Factor the diagonal tile (k, k) in shared memory (unblocked, right-looking).
-__global__ void __launch_bounds__(256) k_potrf_tile(double* __restrict__ M, int64_t ld, int k, int* err) {
-  __shared__ double a[kT][kT + 1];
-  const int tid = threadIdx.x;
-  double* base = M + (int64_t)k * kT * ld + (int64_t)k * kT;
-  for (int e = tid; e < kT * kT; e += blockDim.x) a[e / kT][e % kT] = base[(int64_t)(e / kT) * ld + e % kT];
-  __syncthreads();
-  for (int j = 0; j < kT; ++j) {
-    if (tid == 0) {
-      double d = a[j][j];
-      if (!(d > 0.0)) {
-        set_err(err, kDevBreakdown);
-        d = 1.0;
-      }
-      a[j][j] = sqrt(d);
-    }
-    __syncthreads();
-    if (tid > j && tid < kT) a[tid][j] /= a[j][j];
-    __syncthreads();
-    for (int e = tid; e < kT * kT; e += blockDim.x) {
-      const int i = e / kT, l = e % kT;
-      if (l > j && i >= l) a[i][l] -= a[i][j] * a[l][j];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < kT * kT; e += blockDim.x) {
-    const int i = e / kT, l = e % kT;
-    base[(int64_t)i * ld + l] = l <= i ? a[i][l] : 0.0;
-  }
-}
-
-// L(i,k) = A(i,k) L(k,k)^-T for tiles i = k+1 .. nt-1 (one CTA per tile).
-__global__ void __launch_bounds__(128) k_trsm_tiles(double* __restrict__ M, int64_t ld, int k) {
-  __shared__ double L[kT][kT + 1], X[kT][kT + 1];
-  const int i = k + 1 + blockIdx.x;
-  const int tid = threadIdx.x;
-  const double* lb = M + (int64_t)k * kT * ld + (int64_t)k * kT;
-  double* xb = M + (int64_t)i * kT * ld + (int64_t)k * kT;
-  for (int e = tid; e < kT * kT; e += blockDim.x) {
-    L[e / kT][e % kT] = lb[(int64_t)(e / kT) * ld + e % kT];
-    X[e / kT][e % kT] = xb[(int64_t)(e / kT) * ld + e % kT];
-  }
-  __syncthreads();
-  if (tid < kT) {  // row tid of X solves x L^T = a, i.e. sum_{l<=j} x_l L[j][l] = a_j
-    for (int j = 0; j < kT; ++j) {
-      double t = X[tid][j];
-      for (int l = 0; l < j; ++l) t -= X[tid][l] * L[j][l];
-      X[tid][j] = t / L[j][j];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < kT * kT; e += blockDim.x) xb[(int64_t)(e / kT) * ld + e % kT] = X[e / kT][e % kT];
-}
-
 // Tile GEMM update C -= A B^T (trailing Cholesky update) or C += A B (inverse
 // accumulation), 256 threads, 4 outputs each.
 template <bool kSyrk>
 __device__ __forceinline__ void tile_update(double* __restrict__ C, const double* __restrict__ Ab,
-                                            const double* __restrict__ Bb, int64_t ld) {
-  __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
+                                            const double* __restrict__ Bb, int64_t ld, double (*As)[kT + 1],
+                                            double (*Bs)[kT + 1]) {
   const int tid = threadIdx.x;
+  __syncthreads();
   for (int e = tid; e < kT * kT; e += blockDim.x) {
     As[e / kT][e % kT] = Ab[(int64_t)(e / kT) * ld + e % kT];
     Bs[e / kT][e % kT] = Bb[(int64_t)(e / kT) * ld + e % kT];
@@ -118,53 +67,135 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
   }
 }
 
-// A(i,j) -= L(i,k) L(j,k)^T for k < j <= i < nt; blockIdx enumerates (i, j).
-__global__ void __launch_bounds__(256) k_syrk_tiles(double* __restrict__ M, int64_t ld, int k, int nt) {
-  const int T = nt - k - 1;
-  int idx = blockIdx.x, i = 0;
-  while (idx > i) {  // row-major lower triangle of a T x T tile grid
-    idx -= i + 1;
-    ++i;
-  }
-  const int j = idx;
-  const int gi = k + 1 + i, gj = k + 1 + j;
-  (void)T;
-  tile_update<true>(M + (int64_t)gi * kT * ld + (int64_t)gj * kT, M + (int64_t)gi * kT * ld + (int64_t)k * kT,
-                    M + (int64_t)gj * kT * ld + (int64_t)k * kT, ld);
-}
-
-// W(i,k) = L(i,i)^-1 (delta_ik I - S(i,k)) for k = 0..i, S accumulated in W.
-__global__ void __launch_bounds__(128) k_winv_tiles(const double* __restrict__ Lm, double* __restrict__ W, int64_t ld,
-                                                    int i) {
-  __shared__ double L[kT][kT + 1], X[kT][kT + 1];
-  const int k = blockIdx.x;
+// Cholesky of the diagonal tile (k, k) in shared memory and the inverse of
+// the factor (one CTA); L is written back, L^-1 to Linv.
+__device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __restrict__ Linv, int* err,
+                          double (*a)[kT + 1], double (*w)[kT + 1]) {
   const int tid = threadIdx.x;
-  const double* lb = Lm + (int64_t)i * kT * ld + (int64_t)i * kT;
-  double* wb = W + (int64_t)i * kT * ld + (int64_t)k * kT;
-  for (int e = tid; e < kT * kT; e += blockDim.x) {
-    const int r = e / kT, c = e % kT;
-    L[r][c] = lb[(int64_t)r * ld + c];
-    X[r][c] = ((k == i && r == c) ? 1.0 : 0.0) - wb[(int64_t)r * ld + c];
-  }
+  double* base = M + (int64_t)k * kT * ld + (int64_t)k * kT;
   __syncthreads();
-  if (tid < kT) {  // column tid: forward substitution L x = rhs
-    for (int r = 0; r < kT; ++r) {
-      double t = X[r][tid];
-      for (int l = 0; l < r; ++l) t -= L[r][l] * X[l][tid];
-      X[r][tid] = t / L[r][r];
+  for (int e = tid; e < kT * kT; e += blockDim.x) a[e / kT][e % kT] = base[(int64_t)(e / kT) * ld + e % kT];
+  __syncthreads();
+  for (int j = 0; j < kT; ++j) {
+    if (tid == 0) {
+      double d = a[j][j];
+      if (!(d > 0.0)) {
+        set_err(err, kDevBreakdown);
+        d = 1.0;
+      }
+      a[j][j] = sqrt(d);
     }
+    __syncthreads();
+    if (tid > j && tid < kT) a[tid][j] /= a[j][j];
+    __syncthreads();
+    for (int e = tid; e < kT * kT; e += blockDim.x) {
+      const int i = e / kT, l = e % kT;
+      if (l > j && i >= l) a[i][l] -= a[i][j] * a[l][j];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < kT * kT; e += blockDim.x) wb[(int64_t)(e / kT) * ld + e % kT] = X[e / kT][e % kT];
+  // rows of W = L^-1 one at a time; 8 threads per column split the dot product
+  const int c = tid >> 3, part = tid & 7;
+  for (int r = 0; r < kT; ++r) {
+    double t = 0.0;
+    if (c < r)
+      for (int l = c + part; l < r; l += 8) t = fma(a[r][l], w[l][c], t);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (part == 0) w[r][c] = (c <= r) ? (((r == c) ? 1.0 : 0.0) - t) / a[r][r] : 0.0;
+    __syncthreads();
+  }
+  for (int e = tid; e < kT * kT; e += blockDim.x) {
+    const int i = e / kT, l = e % kT;
+    base[(int64_t)i * ld + l] = l <= i ? a[i][l] : 0.0;
+    Linv[e] = w[i][l];
+  }
 }
 
-// S(r,k) += L(r,i) W(i,k) for r = i+1..nt-1, k = 0..i; blockIdx = (r - i - 1) * (i + 1) + k.
-__global__ void __launch_bounds__(256) k_wupdate_tiles(const double* __restrict__ Lm, double* __restrict__ W,
-                                                       int64_t ld, int i) {
-  const int r = i + 1 + blockIdx.x / (i + 1);
-  const int k = blockIdx.x % (i + 1);
-  tile_update<false>(W + (int64_t)r * kT * ld + (int64_t)k * kT, Lm + (int64_t)r * kT * ld + (int64_t)i * kT,
-                     W + (int64_t)i * kT * ld + (int64_t)k * kT, ld);
+// Rows [r0, r0 + 8) of X = A Linv^T (Cholesky panel), in place over A.
+__device__ void panel_rows(double* __restrict__ Xt, int64_t ld, const double* __restrict__ Linv, int r0,
+                           double (*a)[kT + 1], double (*w)[kT + 1]) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < kT * kT; e += blockDim.x) w[e / kT][e % kT] = Linv[e];
+  for (int e = tid; e < 8 * kT; e += blockDim.x) a[e / kT][e % kT] = Xt[(int64_t)(r0 + e / kT) * ld + e % kT];
+  __syncthreads();
+  const int r = tid / kT, c = tid % kT;  // 8 x 32 outputs
+  double t = 0.0;
+#pragma unroll 8
+  for (int l = 0; l < kT; ++l) t = fma(a[r][l], w[c][l], t);
+  Xt[(int64_t)(r0 + r) * ld + c] = t;
+}
+
+// Columns [c0, c0 + 8) of W(i,k) = Linv (delta I - S), in place over S.
+__device__ void winv_cols(double* __restrict__ St, int64_t ld, const double* __restrict__ Linv, int c0, bool diag,
+                          double (*a)[kT + 1], double (*w)[kT + 1]) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < kT * kT; e += blockDim.x) w[e / kT][e % kT] = Linv[e];
+  for (int e = tid; e < kT * 8; e += blockDim.x) {
+    const int r = e / 8, c = e % 8;
+    a[r][c] = ((diag && r == c0 + c) ? 1.0 : 0.0) - St[(int64_t)r * ld + c0 + c];
+  }
+  __syncthreads();
+  const int r = tid / 8, c = tid % 8;  // 32 x 8 outputs
+  double t = 0.0;
+#pragma unroll 8
+  for (int l = 0; l < kT; ++l) t = fma(w[r][l], a[l][c], t);
+  St[(int64_t)r * ld + c0 + c] = t;
+}
+
+// Whole coarsest factorisation in one cooperative launch (256 threads per
+// CTA, every CTA runs the same sequence of grid barriers):
+//   Cholesky, step k:  factor + invert tile (k,k) | panel L(i,k) = A(i,k) L(k,k)^-T
+//                      | trailing A(i,j) -= L(i,k) L(j,k)^T
+//   W = L^-1, row i:   W(i,k) = L(i,i)^-1 (delta I - S(i,k)), k <= i
+//                      | S(r,k) += L(r,i) W(i,k), r > i, k <= i   (S accumulated in W)
+__global__ void __launch_bounds__(256) k_dense_factor(double* __restrict__ F, double* __restrict__ W, int64_t ld,
+                                                      int nt, double* __restrict__ Dinv, int* err) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ double a[kT][kT + 1], w[kT][kT + 1];
+  const int G = gridDim.x, b = blockIdx.x;
+  for (int k = 0; k < nt; ++k) {
+    if (b == 0) diag_tile(F, ld, k, Dinv + (int64_t)k * kT * kT, err, a, w);
+    __threadfence();
+    grid.sync();
+    for (int item = b; item < (nt - k - 1) * 4; item += G) {
+      const int i = k + 1 + item / 4;
+      panel_rows(F + (int64_t)i * kT * ld + (int64_t)k * kT, ld, Dinv + (int64_t)k * kT * kT, (item % 4) * 8, a, w);
+    }
+    __threadfence();
+    grid.sync();
+    const int T = nt - k - 1;
+    for (int item = b; item < T * (T + 1) / 2; item += G) {
+      int idx = item, i = 0;
+      while (idx > i) {  // row-major lower triangle (i, j), j <= i
+        idx -= i + 1;
+        ++i;
+      }
+      const int gi = k + 1 + i, gj = k + 1 + idx;
+      tile_update<true>(F + (int64_t)gi * kT * ld + (int64_t)gj * kT, F + (int64_t)gi * kT * ld + (int64_t)k * kT,
+                        F + (int64_t)gj * kT * ld + (int64_t)k * kT, ld, a, w);
+    }
+    __threadfence();
+    grid.sync();
+  }
+  for (int i = 0; i < nt; ++i) {
+    for (int item = b; item < (i + 1) * 4; item += G) {
+      const int k = item / 4;
+      winv_cols(W + (int64_t)i * kT * ld + (int64_t)k * kT, ld, Dinv + (int64_t)i * kT * kT, (item % 4) * 8, k == i,
+                a, w);
+    }
+    __threadfence();
+    grid.sync();
+    for (int item = b; item < (nt - i - 1) * (i + 1); item += G) {
+      const int r = i + 1 + item / (i + 1), k = item % (i + 1);
+      tile_update<false>(W + (int64_t)r * kT * ld + (int64_t)k * kT, F + (int64_t)r * kT * ld + (int64_t)i * kT,
+                         W + (int64_t)i * kT * ld + (int64_t)k * kT, ld, a, w);
+    }
+    __threadfence();
+    grid.sync();
+  }
 }
 
 __global__ void k_transpose_dense(const double* __restrict__ S, double* __restrict__ D, int64_t n) {
@@ -213,7 +244,8 @@ Status coarse_factor(bamg_mg* mg) {
   // transpose then overwrites the factor with W^T.
   double* F = D.Wt;
   double* W = D.M;
-  k_dense_init<<<(unsigned)((npad * npad + 255) / 256), 256, 0, st>>>(F, n, npad);
+  const int pm = prof_begin(ctx, BAMG_PROF_COARSE_FACTOR, st);
+  { k_dense_init<<<(unsigned)((npad * npad + 255) / 256), 256, 0, st>>>(F, n, npad); BAMG_COUNT_LAUNCH; }
   const bamg_bsr* A = C.A;
   if (!D.rows) {
     std::vector<int> rows(A->nnzb);
@@ -228,32 +260,35 @@ Status coarse_factor(bamg_mg* mg) {
     const unsigned b = (unsigned)((nt_fill + 255) / 256);
     if (bs == 6) {
       if (A->vals64_stale)
-        k_dense_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad);
+        { k_dense_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
       else
-        k_dense_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad);
+        { k_dense_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
     } else {
       if (A->vals64_stale)
-        k_dense_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad);
+        { k_dense_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
       else
-        k_dense_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad);
-    }
-  }
-  for (int k = 0; k < nt; ++k) {
-    k_potrf_tile<<<1, 256, 0, st>>>(F, npad, k, ctx->d_err);
-    if (k + 1 < nt) {
-      k_trsm_tiles<<<nt - k - 1, 128, 0, st>>>(F, npad, k);
-      const int T = nt - k - 1;
-      k_syrk_tiles<<<T * (T + 1) / 2, 256, 0, st>>>(F, npad, k, nt);
+        { k_dense_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
     }
   }
   BAMG_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * npad * npad, st));
-  for (int i = 0; i < nt; ++i) {
-    k_winv_tiles<<<i + 1, 128, 0, st>>>(F, W, npad, i);
-    if (i + 1 < nt) k_wupdate_tiles<<<(nt - i - 1) * (i + 1), 256, 0, st>>>(F, W, npad, i);
+  if (!D.dinv_tiles) BAMG_TRY(dalloc(&D.dinv_tiles, (int64_t)nt * kT * kT, st));
+  {
+    int per_sm = 0;
+    BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
+    const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
+    int64_t ld = npad;
+    int ntl = nt;
+    double* dt = D.dinv_tiles;
+    int* err = ctx->d_err;
+    void* args[] = {&F, &W, &ld, &ntl, &dt, &err};
+    if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
+    BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, st));
+    BAMG_COUNT_LAUNCH;
   }
   // Wt = W^T (the factor in F is no longer needed)
   dim3 tg((unsigned)nt, (unsigned)nt);
-  k_transpose_dense<<<tg, 256, 0, st>>>(W, F, npad);
+  { k_transpose_dense<<<tg, 256, 0, st>>>(W, F, npad); BAMG_COUNT_LAUNCH; }
+  prof_end(ctx, pm, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -263,8 +298,8 @@ Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t
   CoarseDense& D = mg->coarse;
   const int64_t n = D.n;
   const unsigned g = (unsigned)((n * 32 + 255) / 256);
-  k_tri_mv<T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, D.x64, 1, done);
-  k_tri_mv<double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, D.x64, x, 0, done);
+  { k_tri_mv<T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, D.x64, 1, done); BAMG_COUNT_LAUNCH; }
+  { k_tri_mv<double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, D.x64, x, 0, done); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }

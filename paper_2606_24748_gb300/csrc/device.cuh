@@ -18,16 +18,22 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// One thread per block row: acc[r] = sum over the row's blocks of A_blk[r][:] . x_blk.
-// The 32 rows of a slice share the slice's chunk range, so the loop is uniform
-// across the warp and every value / column load is one coalesced access.
-// Matrix values and columns are streamed (evict-first); x is gathered through
-// the read-only path, where neighbouring rows hit the same lines.
-template <int BR, int BC, typename TM, typename TA, typename TX>
+// Block-row product acc[r] = sum over the row's blocks of A_blk[r][:] . x_blk,
+// computed by V lanes per row (V divides 32).  With V = 1 a row is one lane
+// and the 32 rows of a slice share the slice's chunk range, so the loop is
+// uniform across the warp and every value / column load is one coalesced
+// access with no cross-lane reduction.  Matrices with few, long rows (the
+// restriction R = P^T, coarse levels) use V > 1: the V lanes of a row take
+// every V-th chunk and the partial sums are combined with a fixed xor
+// shuffle tree, after which every lane of the group holds the row sums.
+// Matrix values and columns are streamed (evict-first); x is gathered
+// through the read-only path, where neighbouring rows hit the same lines.
+// `row` is the thread's row; `sub` its lane within the row's group.
+template <int BR, int BC, int V, typename TM, typename TA, typename TX>
 __device__ __forceinline__ void row_product(const int* __restrict__ slice_ptr,
                                             const int* __restrict__ col,
                                             const TM* __restrict__ vals,
-                                            const TX* __restrict__ x, int64_t row,
+                                            const TX* __restrict__ x, int64_t row, int sub,
                                             TA (&acc)[BR]) {
   const int64_t s = row >> 5;
   const int lane = (int)(row & 31);
@@ -35,7 +41,7 @@ __device__ __forceinline__ void row_product(const int* __restrict__ slice_ptr,
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = TA(0);
 #pragma unroll 2
-  for (int c = c0; c < c1; ++c) {
+  for (int c = c0 + sub; c < c1; c += V) {
     const int64_t slot = (int64_t)c * 32 + lane;
     const int j = __ldcs(col + slot);
     const TM* v = vals + (int64_t)c * (32 * BR * BC) + lane;
@@ -47,7 +53,31 @@ __device__ __forceinline__ void row_product(const int* __restrict__ slice_ptr,
 #pragma unroll
       for (int q = 0; q < BC; ++q) acc[r] = fma((TA)__ldcs(v + 32 * (r * BC + q)), xv[q], acc[r]);
   }
+  if (V > 1) {
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int o = V / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  }
 }
+
+// Thread -> (row, sub-lane) for V lanes per row.
+template <int V>
+__device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub) {
+  row = t / V;
+  sub = (int)(t - row * V);
+}
+
+// Run `body` with the compile-time lane count matching v (1..32).
+#define BAMG_DISPATCH_V(v, ...)                \
+  switch (v) {                                 \
+    case 32: { constexpr int V = 32; __VA_ARGS__; } break; \
+    case 16: { constexpr int V = 16; __VA_ARGS__; } break; \
+    case 8: { constexpr int V = 8; __VA_ARGS__; } break;   \
+    case 4: { constexpr int V = 4; __VA_ARGS__; } break;   \
+    case 2: { constexpr int V = 2; __VA_ARGS__; } break;   \
+    default: { constexpr int V = 1; __VA_ARGS__; } break;  \
+  }
 
 // Deterministic grid reduction of NV doubles: every CTA reduces its threads'
 // values with a fixed shuffle tree, writes its partials, and the last CTA to

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -27,7 +28,35 @@ struct Status {
   bool ok() const { return code == BAMG_OK; }
 };
 
+// Kernel launch count (launches captured into a graph are counted when the
+// graph is launched, by its kernel-node count).
+extern std::atomic<unsigned long long> g_launches;
+extern thread_local bool g_capturing;
+inline void count_launch() {
+  if (!g_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+struct ProfPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int slot = 0;
+  int pos = 0;  // CG iteration position (graph-owned pairs)
+};
+
+struct Prof {
+  bool on = false;
+  uint64_t epoch = 0;
+  std::vector<ProfPair> eager;
+  size_t eager_used = 0;
+  std::vector<ProfPair>* sink = nullptr;  // graph-owned pairs (created before capture)
+  size_t sink_used = 0;
+  int pos = 0;
+  double ms[BAMG_PROF_COUNT] = {};
+  int64_t n[BAMG_PROF_COUNT] = {};
+};
+
 }  // namespace bamg
+
+#define BAMG_COUNT_LAUNCH ::bamg::count_launch()
 
 struct bamg_ctx {
   cudaStream_t stream = nullptr;
@@ -37,6 +66,7 @@ struct bamg_ctx {
   int* d_err = nullptr;            // device error word (first error code wins)
   double* d_partials = nullptr;    // kRedBlocks partial sums x 4 lanes
   unsigned* d_counters = nullptr;  // last-block counters (16 slots)
+  bamg::Prof prof;
 };
 
 // Rectangular-block sparse matrix.  The pattern is kept in block-CSR form
@@ -65,6 +95,8 @@ struct bamg_bsr {
   int* slot_of = nullptr;    // nnzb: CSR block -> slot
   int* diag_slot = nullptr;  // nbr (square blocks only, -1 if no diagonal block)
   bool all_diag = false;     // every block row has its diagonal block
+  int vec = 1;               // lanes per block row of the row kernels (1..32, power of 2)
+  bool vec_tuned = false;
   std::vector<int> h_slice_ptr, h_slot_of;
   double* vals = nullptr;    // 32 * nchunks * B
   float* vals32 = nullptr;   // float copy in the same layout
@@ -109,6 +141,7 @@ struct bamg_ptap {
   float* Pblk32 = nullptr;
   uint64_t pblk_version = ~0ull, pblk32_version = ~0ull;
   uint64_t pblk_refreshes = 0;
+  int prof_stage1 = -1, prof_stage2 = -1;  // profiling slots of the two stages (-1: none)
 };
 
 namespace bamg {
@@ -131,6 +164,7 @@ struct CoarseDense {
   double* b64 = nullptr; // FP64 staging vectors (mixed form)
   double* x64 = nullptr;
   int* rows = nullptr;   // block row of every stored block of the coarsest operator
+  double* dinv_tiles = nullptr;  // inverses of the 32x32 diagonal tiles of L
 };
 
 struct Level {
@@ -169,8 +203,11 @@ struct bamg_mg {
   double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *czold = nullptr;
   bamg::CgState* cg = nullptr;
   bamg::CgState* cg_host = nullptr;  // pinned
-  cudaGraphExec_t cg_graph = nullptr;
-  cudaGraphExec_t update_graph = nullptr;
+  std::vector<cudaGraphExec_t> cg_graphs;  // one, or one per iteration position when profiling
+  std::vector<std::vector<bamg::ProfPair>> cg_pairs;
+  std::vector<size_t> cg_pairs_used;
+  uint64_t cg_graph_epoch = ~0ull;
+  uint64_t cg_graph_kernels = 0;
   double* power_w[2] = {nullptr, nullptr};
 };
 
@@ -227,6 +264,11 @@ Status download(std::vector<T>& dst, const T* src, int64_t n, cudaStream_t st) {
 enum DevErr : int { kDevOk = 0, kDevNaN = 1, kDevBreakdown = 2, kDevTimeout = 3, kDevIndex = 4 };
 Status check_device_error(bamg_ctx* ctx);  // synchronizes the stream
 
+// Profiling marks (no-ops when profiling is off).  Return / take an index.
+int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st);
+void prof_end(bamg_ctx* ctx, int idx, cudaStream_t st);
+void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int active_ap, int active_vc);
+
 // ------------------------------------------------------------ pattern helpers
 // Build the sliced form (and device/host CSR copies) from a host CSR pattern;
 // allocates zeroed values.  Used by COO preallocation and the Galerkin symbolic.
@@ -251,6 +293,7 @@ Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t
 template <typename T>
 Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
+void mg_release_graphs(bamg_mg* mg);
 
 // ------------------------------------------------------------ kernel launchers
 // y = A x (row-block product) in precision T (double or float); x, y device.
@@ -260,5 +303,10 @@ template <typename T>
 Status launch_spmm(const bamg_bsr* A, const T* vals, const T* X, T* Y, int k, cudaStream_t st);
 // Convert a sliced value array to float.
 Status launch_to_fp32(const double* src, float* dst, int64_t n, cudaStream_t st);
+// Lanes-per-row choice: a size heuristic, and the measured choice (times the
+// FP64 product for every width and keeps the fastest).
+int default_vec(const bamg_bsr* A);
+Status bsr_autotune(bamg_bsr* A, float* best_ms);
+inline int64_t row_threads(const bamg_bsr* A) { return A->nslices * kSlice * (int64_t)A->vec; }
 
 }  // namespace bamg

@@ -234,23 +234,26 @@ __global__ void k_start_vector(double* __restrict__ v, int64_t n) {
 
 // One power step w_out = D^-1 A (w_in / ||w_in||) with D the block diagonal
 // (dinv) or the scalar diagonal; ||w_out|| goes to *norm_out.
-template <int BS, typename TM>
+template <int BS, int V, typename TM>
 __global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restrict__ slice_ptr,
                                                             const int* __restrict__ col, const TM* __restrict__ vals,
                                                             const int* __restrict__ diag_slot,
                                                             const double* __restrict__ dinv, int scalar_diag,
                                                             const double* __restrict__ w_in,
                                                             double* __restrict__ w_out, const double* norm_in,
-                                                            double* norm_out, int64_t n, int64_t rows_pad,
+                                                            double* norm_out, int64_t n, int64_t nthreads,
                                                             double* partials, unsigned* counter) {
   constexpr int B = BS * BS;
   const double s = norm_in ? 1.0 / *norm_in : 1.0;
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < rows_pad; row += stride) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+    int64_t row;
+    int sub;
+    row_of_thread<V>(t, row, sub);
     double acc[BS];
-    row_product<BS, BS, TM, double, double>(slice_ptr, col, vals, w_in, row, acc);
-    if (row < n) {
+    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w_in, row, sub, acc);
+    if (sub == 0 && row < n) {
       double z[BS];
       if (scalar_diag) {
         const int64_t ds = diag_slot[row];
@@ -279,20 +282,23 @@ __global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restric
 
 // Rayleigh quotient w^T A w / w^T D w; in block mode also the Chebyshev data
 // for the interval [lower, upper] * lambda (Saad, Alg. 12.1 coefficients).
-template <int BS, typename TM>
+template <int BS, int V, typename TM>
 __global__ void __launch_bounds__(kRowThreads) k_rayleigh(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const TM* __restrict__ vals,
                                                           const int* __restrict__ diag_slot, int scalar_diag,
-                                                          const double* __restrict__ w, int64_t n, int64_t rows_pad,
+                                                          const double* __restrict__ w, int64_t n, int64_t nthreads,
                                                           double* partials, unsigned* counter, double* out_scal,
                                                           double lower, double upper, int degree) {
   constexpr int B = BS * BS;
   double local[2] = {0.0, 0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < rows_pad; row += stride) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+    int64_t row;
+    int sub;
+    row_of_thread<V>(t, row, sub);
     double acc[BS];
-    row_product<BS, BS, TM, double, double>(slice_ptr, col, vals, w, row, acc);
-    if (row < n) {
+    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w, row, sub, acc);
+    if (sub == 0 && row < n) {
       const int64_t ds = diag_slot[row];
       double wi[BS];
 #pragma unroll
@@ -339,21 +345,21 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
                          double* out_scal) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
-  const int64_t n = A->nbr, rows = A->nslices * kSlice;
+  const int64_t n = A->nbr, rows = row_threads(A);
   double* w[2] = {mg->power_w[0], mg->power_w[1]};
   double* norms = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel;  // 2 scratch slots
   const unsigned g = red_grid(rows);
-  k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS);
+  { k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS); BAMG_COUNT_LAUNCH; }
   for (int it = 0; it < mg->opts.power_its; ++it) {
     const double* nin = it == 0 ? nullptr : norms + ((it + 1) & 1);
-    k_power_step<BS, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
+    BAMG_DISPATCH_V(A->vec, { k_power_step<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, w[it & 1], w[(it + 1) & 1], nin,
-                                                    norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters);
+                                                    norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
-  k_rayleigh<BS, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
+  BAMG_DISPATCH_V(A->vec, { k_rayleigh<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
                                                 w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
-                                                mg->opts.cheb_upper, mg->opts.cheb_degree);
+                                                mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -381,14 +387,14 @@ Status mg_refresh_level(bamg_mg* mg, int l) {
   if (L.n > 0) {
     if (L.bs == 3) {
       if (A->vals64_stale)
-        k_block_inverse<3, float><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals32, L.dinv, d32, ctx->d_err);
+        { k_block_inverse<3, float><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals32, L.dinv, d32, ctx->d_err); BAMG_COUNT_LAUNCH; }
       else
-        k_block_inverse<3, double><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals, L.dinv, d32, ctx->d_err);
+        { k_block_inverse<3, double><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals, L.dinv, d32, ctx->d_err); BAMG_COUNT_LAUNCH; }
     } else {
       if (A->vals64_stale)
-        k_block_inverse<6, float><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals32, L.dinv, d32, ctx->d_err);
+        { k_block_inverse<6, float><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals32, L.dinv, d32, ctx->d_err); BAMG_COUNT_LAUNCH; }
       else
-        k_block_inverse<6, double><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals, L.dinv, d32, ctx->d_err);
+        { k_block_inverse<6, double><<<b, 128, 0, st>>>(L.n, A->diag_slot, A->vals, L.dinv, d32, ctx->d_err); BAMG_COUNT_LAUNCH; }
     }
     BAMG_CUDA(cudaGetLastError());
   }
@@ -403,9 +409,9 @@ Status mg_refresh_restriction(bamg_mg* mg, int l) {
   if (nt > 0) {
     const unsigned b = (unsigned)((nt + 255) / 256);
     if (L.bs == 3)
-      k_transpose_blocks<3><<<b, 256, 0, st>>>(L.R->nnzb, L.rmap, L.R->slot_of, L.P->slot_of, L.P->vals, L.R->vals);
+      { k_transpose_blocks<3><<<b, 256, 0, st>>>(L.R->nnzb, L.rmap, L.R->slot_of, L.P->slot_of, L.P->vals, L.R->vals); BAMG_COUNT_LAUNCH; }
     else
-      k_transpose_blocks<6><<<b, 256, 0, st>>>(L.R->nnzb, L.rmap, L.R->slot_of, L.P->slot_of, L.P->vals, L.R->vals);
+      { k_transpose_blocks<6><<<b, 256, 0, st>>>(L.R->nnzb, L.rmap, L.R->slot_of, L.P->slot_of, L.P->vals, L.R->vals); BAMG_COUNT_LAUNCH; }
     BAMG_CUDA(cudaGetLastError());
   }
   L.R->version++;
@@ -419,7 +425,7 @@ static Status bsr_upload_values(bamg_bsr* A, const std::vector<double>& v) {
   BAMG_TRY(upload(&tmp, v, st));
   const int B = (int)A->block_elems();
   const int64_t nt = A->nnzb * B;
-  if (nt > 0) k_scatter_values<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A->slot_of, tmp, A->vals, A->nnzb, B);
+  if (nt > 0) { k_scatter_values<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(A->slot_of, tmp, A->vals, A->nnzb, B); BAMG_COUNT_LAUNCH; }
   cudaError_t e = cudaGetLastError();
   cudaStreamSynchronize(st);
   dfree(tmp, st);
@@ -468,8 +474,7 @@ static Status alloc_vectors(bamg_mg* mg) {
 
 static void mg_release(bamg_mg* mg) {
   cudaStream_t st = mg->ctx->stream;
-  if (mg->cg_graph) cudaGraphExecDestroy(mg->cg_graph);
-  if (mg->update_graph) cudaGraphExecDestroy(mg->update_graph);
+  mg_release_graphs(mg);
   for (auto& L : mg->levels) {
     if (L.plan) {
       ptap_release(L.plan);
@@ -486,6 +491,7 @@ static void mg_release(bamg_mg* mg) {
                      &mg->power_w[1], &mg->coarse.M, &mg->coarse.Wt, &mg->coarse.b64, &mg->coarse.x64})
     dfree(*p, st);
   dfree(mg->coarse.rows, st);
+  dfree(mg->coarse.dinv_tiles, st);
   dfree(mg->cg, st);
   if (mg->cg_host) cudaFreeHost(mg->cg_host);
   cudaStreamSynchronize(st);
@@ -589,11 +595,11 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       if (nt > 0) {
         const unsigned b = (unsigned)((nt + 255) / 256);
         if (bs == 3)
-          k_smooth_prolongator<3><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
-                                                     L.A->vals, L.omega, P->slot_of, P->vals);
+          { k_smooth_prolongator<3><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
+                                                     L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
         else
-          k_smooth_prolongator<6><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
-                                                     L.A->vals, L.omega, P->slot_of, P->vals);
+          { k_smooth_prolongator<6><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
+                                                     L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
       }
       cudaError_t e = cudaGetLastError();
       cudaStreamSynchronize(st);
@@ -627,6 +633,10 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
     bamg_bsr* Ac = nullptr;
     BAMG_TRY(ptap_build(L.A, P, true, &L.plan, &Ac));
     bamg_ptap* plan = L.plan;
+    if (l == 0) {
+      plan->prof_stage1 = BAMG_PROF_PTAP_STAGE1_L0;
+      plan->prof_stage2 = BAMG_PROF_PTAP_STAGE2_L0;
+    }
     ap_guard.reset();
     Pt_guard.reset();
     Level C;
@@ -685,6 +695,7 @@ void bamg_mg_opts_default(bamg_mg_opts* o) {
   o->cheb_upper = 1.1;
   o->power_its = 15;
   o->precision = BAMG_FP64;
+  o->autotune = 1;
 }
 
 bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, const uint8_t* dirichlet,
@@ -712,6 +723,13 @@ bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, cons
   mg->opts = o;
   Status s = mg_setup_impl(mg, A, coords, dirichlet);
   if (s.ok()) s = mg_update_impl(mg);
+  if (s.ok() && o.autotune) {
+    for (auto& L : mg->levels) {
+      if (s.ok()) s = bsr_autotune(L.A, nullptr);
+      if (s.ok() && L.P) s = bsr_autotune(L.P, nullptr);
+      if (s.ok() && L.R) s = bsr_autotune(L.R, nullptr);
+    }
+  }
   if (s.ok()) s = check_device_error(ctx);
   if (!s.ok()) {
     mg_release(mg);
@@ -731,10 +749,7 @@ bamg_status bamg_mg_update(bamg_mg* mg) {
 bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w) {
   if (!mg || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
   mg->levels[level].weights = const_cast<float*>(w);
-  if (mg->cg_graph) {
-    cudaGraphExecDestroy(mg->cg_graph);
-    mg->cg_graph = nullptr;
-  }
+  mg_release_graphs(mg);  // the captured iteration holds the old pointer
   return BAMG_OK;
 }
 
@@ -780,7 +795,7 @@ bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* out) {
   const Level& L = mg->levels[level];
   const int B = L.bs * L.bs;
   const int64_t nt = L.n * B;
-  if (nt > 0) k_dinv_rowmajor<<<(unsigned)((nt + 255) / 256), 256, 0, mg->ctx->stream>>>(L.n, B, L.dinv, out);
+  if (nt > 0) { k_dinv_rowmajor<<<(unsigned)((nt + 255) / 256), 256, 0, mg->ctx->stream>>>(L.n, B, L.dinv, out); BAMG_COUNT_LAUNCH; }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BAMG_OK : fail(mg->ctx, cuda_status(e, "get_dinv"));
 }

@@ -356,25 +356,29 @@ static Status run_stages(bamg_ptap* pl, const T* Avals, const T* Pblk, T* Z, T* 
   auto blocks_for = [&](int64_t items) { return (unsigned)((items + (int64_t)G * 8 - 1) / ((int64_t)G * 8)); };
   if (pl->n1 > 0) {
     const unsigned b = blocks_for(pl->n1);
+    const int pm = prof_begin(pl->ctx, pl->prof_stage1, st);
     if (pl->bs == 3 && pl->bsp == 6)
-      k_ptap_stage1<3, 6, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z);
+      { k_ptap_stage1<3, 6, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z); BAMG_COUNT_LAUNCH; }
     else if (pl->bs == 6 && pl->bsp == 6)
-      k_ptap_stage1<6, 6, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z);
+      { k_ptap_stage1<6, 6, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z); BAMG_COUNT_LAUNCH; }
     else
-      k_ptap_stage1<3, 3, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z);
+      { k_ptap_stage1<3, 3, T><<<b, 256, 0, st>>>(pl->n1, pl->s1_z, pl->s1_off, pl->s1_a, pl->s1_p, Avals, Pblk, Z); BAMG_COUNT_LAUNCH; }
+    prof_end(pl->ctx, pm, st);
     BAMG_CUDA(cudaGetLastError());
   }
   if (stage2 && pl->n2 > 0) {
     const unsigned b = blocks_for(pl->n2);
+    const int pm = prof_begin(pl->ctx, pl->prof_stage2, st);
     if (pl->bs == 3 && pl->bsp == 6)
-      k_ptap_stage2<3, 6, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
-                                                Pblk, Z, Acvals);
+      { k_ptap_stage2<3, 6, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
+                                                Pblk, Z, Acvals); BAMG_COUNT_LAUNCH; }
     else if (pl->bs == 6 && pl->bsp == 6)
-      k_ptap_stage2<6, 6, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
-                                                Pblk, Z, Acvals);
+      { k_ptap_stage2<6, 6, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
+                                                Pblk, Z, Acvals); BAMG_COUNT_LAUNCH; }
     else
-      k_ptap_stage2<3, 3, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
-                                                Pblk, Z, Acvals);
+      { k_ptap_stage2<3, 3, T><<<b, 256, 0, st>>>(pl->n2, pl->s2_slot, pl->s2_tslot, pl->s2_off, pl->s2_p, pl->s2_z,
+                                                Pblk, Z, Acvals); BAMG_COUNT_LAUNCH; }
+    prof_end(pl->ctx, pm, st);
     BAMG_CUDA(cudaGetLastError());
   }
   return Status{};

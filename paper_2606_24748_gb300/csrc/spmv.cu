@@ -1,20 +1,25 @@
 // Blocked SpMV and multi-right-hand-side SpMM on the sliced block storage
 // (Sec. 4.2: one column index per block; FP64 or FP32 values).
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.h"
 
 namespace bamg {
 
-template <int BR, int BC, typename T>
+template <int BR, int BC, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_spmv(const int* __restrict__ slice_ptr,
                                                       const int* __restrict__ col, const T* __restrict__ vals,
                                                       const T* __restrict__ x, T* __restrict__ y, int64_t nbr,
-                                                      int64_t nrows_pad) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= nrows_pad) return;
+                                                      int64_t nthreads) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nthreads) return;
+  int64_t row;
+  int sub;
+  row_of_thread<V>(t, row, sub);
   T acc[BR];
-  row_product<BR, BC, T, T, T>(slice_ptr, col, vals, x, row, acc);
-  if (row < nbr) {
+  row_product<BR, BC, V, T, T, T>(slice_ptr, col, vals, x, row, sub, acc);
+  if (sub == 0 && row < nbr) {
 #pragma unroll
     for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
   }
@@ -85,23 +90,89 @@ __global__ void __launch_bounds__(256) k_spmm(const int* __restrict__ slice_ptr,
 }
 
 template <typename T>
-Status launch_spmv(const bamg_bsr* A, const T* vals, const T* x, T* y, cudaStream_t st) {
-  const int64_t rows = A->nslices * kSlice;
-  if (rows == 0) return Status{};
-  const unsigned blocks = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
-#define BAMG_SPMV_CASE(R, C)                                                                                     \
-  if (A->br == R && A->bc == C) {                                                                                \
-    k_spmv<R, C, T><<<blocks, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, A->nbr, rows);        \
-    BAMG_CUDA(cudaGetLastError());                                                                               \
-    return Status{};                                                                                             \
+static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* x, T* y, cudaStream_t st) {
+  const int64_t nt = A->nslices * kSlice * (int64_t)vec;
+  if (nt == 0) return Status{};
+  const unsigned blocks = (unsigned)((nt + kRowThreads - 1) / kRowThreads);
+#define BAMG_SPMV_CASE(R, C)                                                                                  \
+  if (A->br == R && A->bc == C) {                                                                             \
+    BAMG_DISPATCH_V(vec, { k_spmv<R, C, V, T><<<blocks, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, \
+                                                                           A->nbr, nt); BAMG_COUNT_LAUNCH; }) \
+    BAMG_CUDA(cudaGetLastError());                                                                            \
+    return Status{};                                                                                          \
   }
   BAMG_SPMV_CASE(3, 3)
   BAMG_SPMV_CASE(6, 6)
   BAMG_SPMV_CASE(3, 6)
   BAMG_SPMV_CASE(6, 3)
 #undef BAMG_SPMV_CASE
-  k_spmv_any<T><<<blocks, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, A->nbr, rows, A->br, A->bc);
+  const int64_t rows = A->nslices * kSlice;
+  { k_spmv_any<T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, A->nbr, rows, A->br, A->bc); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <typename T>
+Status launch_spmv(const bamg_bsr* A, const T* vals, const T* x, T* y, cudaStream_t st) {
+  return launch_spmv_v<T>(A, A->vec, vals, x, y, st);
+}
+
+int default_vec(const bamg_bsr* A) {
+  // enough threads to cover the GPU (152 SMs x ~1k threads), no more lanes
+  // than the average row has blocks, at most a warp
+  const int64_t target = 152 * 1024;
+  const double avg = A->nbr > 0 ? (double)A->nnzb / (double)A->nbr : 1.0;
+  int v = 1;
+  while (v < 32 && A->nbr * v < target && 2 * v <= avg) v *= 2;
+  return v;
+}
+
+// Measured choice of the lanes per row (tile / warp mapping):
+// time the FP64 product y = A x for each width on the context's stream and
+// keep the fastest.  Cold path (setup); allocates two work vectors.
+Status bsr_autotune(bamg_bsr* A, float* best_ms) {
+  if (!A->has_pattern) return make_status(BAMG_ERR_STATE, "autotune needs a pattern");
+  cudaStream_t st = A->ctx->stream;
+  double *x = nullptr, *y = nullptr;
+  BAMG_TRY(dalloc(&x, std::max<int64_t>(1, A->nbc * A->bc), st));
+  BAMG_TRY(dalloc(&y, std::max<int64_t>(1, A->nbr * A->br), st));
+  BAMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * std::max<int64_t>(1, A->nbc * A->bc), st));
+  cudaEvent_t e0, e1;
+  BAMG_CUDA(cudaEventCreate(&e0));
+  BAMG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestv = A->vec;
+  Status s;
+  const bool special = (A->br == 3 || A->br == 6) && (A->bc == 3 || A->bc == 6);
+  for (int v = 1; v <= 32 && special; v *= 2) {
+    s = launch_spmv_v<double>(A, v, A->vals, x, y, st);
+    if (!s.ok()) break;
+    float tot = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      s = launch_spmv_v<double>(A, v, A->vals, x, y, st);
+      cudaEventRecord(e1, st);
+      if (!s.ok()) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (!s.ok()) break;
+    if (tot / 3 < best * 0.98f) {
+      best = tot / 3;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  dfree(x, st);
+  dfree(y, st);
+  if (!s.ok()) return s;
+  A->vec = bestv;
+  A->vec_tuned = true;
+  if (best_ms) *best_ms = best;
   return Status{};
 }
 
@@ -112,7 +183,7 @@ Status launch_spmm(const bamg_bsr* A, const T* vals, const T* X, T* Y, int k, cu
   const unsigned blocks = (unsigned)((nt + 255) / 256);
 #define BAMG_SPMM_CASE(R, C)                                                                   \
   if (A->br == R && A->bc == C) {                                                              \
-    k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); \
+    { k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
     BAMG_CUDA(cudaGetLastError());                                                             \
     return Status{};                                                                           \
   }

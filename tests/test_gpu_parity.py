@@ -244,3 +244,53 @@ def test_cg_maxit_reports_not_converged():
         assert out["status"] == 7 and out["iterations"] == 3 and not out["converged"]
     finally:
         gp.close()
+
+
+@pytest.mark.parametrize("br,bc", [(3, 3), (6, 6), (6, 3), (3, 6)])
+def test_lane_choice_invariance(br, bc):
+    """Every lanes-per-row width gives the oracle's product; the tuner picks one of them."""
+    rng = np.random.default_rng(7 + br + bc)
+    nbr, nbc, n = 45, 300, 6000                 # few, long rows
+    bi, bj, v = random_stream(rng, nbr, nbc, br, bc, n, neg=False)
+    ref = coo_assemble_blocks(nbr, nbc, br, bc, bi, bj, v)
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    A = B.bamg_bsr_create(ctx, br, bc, nbr, nbc)
+    try:
+        B.bamg_bsr_coo_preallocate(ctx, A, torch.from_numpy(bi).cuda(), torch.from_numpy(bj).cuda())
+        B.bamg_bsr_coo_set_values(ctx, A, torch.from_numpy(v).cuda(), 0)
+        x = rng.standard_normal(nbc * bc)
+        yref = ref.scalar() @ x
+        for lanes in (1, 2, 4, 8, 16, 32):
+            B.bamg_bsr_set_lanes(ctx, A, lanes)
+            y = torch.zeros(nbr * br, dtype=torch.float64, device="cuda")
+            B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).cuda(), y)
+            assert rel(y.cpu().numpy(), yref) <= 1e-14, lanes
+        lanes, ms = B.bamg_bsr_autotune(ctx, A)
+        assert lanes in (1, 2, 4, 8, 16, 32) and ms > 0
+        with pytest.raises(B.BamgError):
+            B.bamg_bsr_set_lanes(ctx, A, 3)
+    finally:
+        B.bamg_bsr_destroy(A)
+        B.bamg_ctx_destroy(ctx)
+
+
+def test_autotuned_hierarchy_gives_same_cycle():
+    """The tuned lane widths change only the summation order."""
+    ne = 13
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        b = np.random.default_rng(5).standard_normal(gp.mesh.n_dofs)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x)
+        for l in range(B.bamg_mg_num_levels(gp.mg)):
+            Al, Pl = B.bamg_mg_get_level(gp.mg, l)
+            B.bamg_bsr_set_lanes(gp.ctx, Al, 1)
+            if Pl is not None:
+                B.bamg_bsr_set_lanes(gp.ctx, Pl, 32)
+        x1 = torch.zeros_like(x)
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x1)
+        ref = omg.vcycle(h, b)
+        assert rel(x.cpu().numpy(), ref) <= TOL64 and rel(x1.cpu().numpy(), ref) <= TOL64
+    finally:
+        gp.close()
