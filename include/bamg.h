@@ -154,6 +154,28 @@ BAMG_API bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms);
 BAMG_API bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes);
 BAMG_API bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes);
 
+/* Residual norm ||b - A x||_2 for a square operator with 3x3 or 6x6 blocks,
+ * written to *norm (device double) on A's context stream; x, b are device
+ * FP64 vectors.  This entry point allocates no device memory at all, for
+ * callers that cannot call cudaMalloc: code running inside a CUDA host
+ * callback (where CUDA calls that allocate are not allowed), or components
+ * of a larger application whose device memory is all pre-reserved by its own
+ * pool.  The paper has no counterpart; it is an operational addition.
+ *  - Scratch: the reduction's partial sums live in a file-scope device array
+ *    of 4096 doubles (32 KB) plus one counter, which every GPU that loads the
+ *    library holds until the process exits.  One partial per 128 thread
+ *    slots: a matrix needs (block rows rounded up to 32) x (lanes per row)
+ *    <= 4096 x 128 = 524,288 slots (e.g. 524,288 block rows at one lane per
+ *    row); larger ones return BAMG_ERR_INVALID with the sizes in the message.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and leaves its last contents there; the
+ *    counter is cleared at the start of each call.  Calls that overlap on the
+ *    GPU (different streams, or several in flight) race on the scratch. */
+BAMG_API bamg_status bamg_bsr_residual_norm_noalloc(const bamg_bsr* A, const double* x, const double* b,
+                                                    double* norm);
+
 /* ----------------------------------------------------- Galerkin product */
 
 /* Symbolic Galerkin product (Sec. 3.1, Sec. 3.5): A (n x n blocks of

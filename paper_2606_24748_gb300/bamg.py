@@ -64,6 +64,7 @@ _SIGS = {
     "bamg_bsr_set_symmetric": [_P, ctypes.c_int],
     "bamg_bsr_spmv": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
     "bamg_bsr_autotune": [_P, _P, _P],
+    "bamg_bsr_residual_norm_noalloc": [_P, _P, _P, _P],
     "bamg_bsr_set_lanes": [_P, ctypes.c_int],
     "bamg_bsr_get_lanes": [_P, _P],
     "bamg_bsr_spmm": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
@@ -214,6 +215,12 @@ def bamg_bsr_get_lanes(A) -> int:
     v = ctypes.c_int()
     _check(lib().bamg_bsr_get_lanes(A, ctypes.byref(v)), None)
     return v.value
+
+
+def bamg_bsr_residual_norm_noalloc(ctx, A, x, b, norm):
+    """||b - A x||_2 into the one-element float64 CUDA tensor `norm`, without
+    any device allocation (see include/bamg.h)."""
+    _check(lib().bamg_bsr_residual_norm_noalloc(A, _ptr(x), _ptr(b), _ptr(norm)), ctx)
 
 
 def bamg_bsr_spmv(ctx, A, x, y, prec: int = BAMG_FP64, transpose: int = 0):
