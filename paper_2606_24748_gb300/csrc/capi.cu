@@ -197,7 +197,7 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   A->vals32_version = ~0ull;
   A->vals64_stale = false;
   A->has_pattern = true;
-  A->vec = default_vec(A);
+  A->vec = A->vec32 = default_vec(A);
   A->vec_tuned = false;
   A->version++;
   static uint64_t next_pattern_id = 0;
@@ -414,7 +414,7 @@ bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
   if (!A) return BAMG_ERR_INVALID;
   if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
     return fail(A->ctx, make_status(BAMG_ERR_INVALID, "lanes must be a power of two in [1, 32]"));
-  A->vec = lanes;
+  A->vec = A->vec32 = lanes;
   return BAMG_OK;
 }
 

@@ -179,7 +179,7 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
-  const int64_t rows = row_threads(A);
+  const int64_t rows = row_threads_for<T>(A);
   const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
   const unsigned gn = (unsigned)((L.n + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
@@ -188,7 +188,7 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
-    BAMG_DISPATCH_V(A->vec, { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                    d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
                                                    k + 1 < m ? 1 : 0, done); BAMG_COUNT_LAUNCH; })
     prof_end(mg->ctx, pm, st);
@@ -202,18 +202,18 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
-  const int64_t rows = row_threads(A);
+  const int64_t rows = row_threads_for<T>(A);
   const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
   const int pr = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_RINIT_L0 : -1, st);
-  BAMG_DISPATCH_V(A->vec, { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+  BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
                                                   p.d0, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; })
   prof_end(mg->ctx, pr, st);
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k + 1 < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
-    BAMG_DISPATCH_V(A->vec, { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                    d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done); BAMG_COUNT_LAUNCH; })
     prof_end(mg->ctx, pm, st);
   }
@@ -226,9 +226,9 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
 template <int BR, int BC, typename T>
 static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int accumulate, const int* done,
                        cudaStream_t st) {
-  const int64_t rows = row_threads(M);
+  const int64_t rows = row_threads_for<T>(M);
   if (rows == 0) return Status{};
-  BAMG_DISPATCH_V(M->vec, { k_transfer<BR, BC, V, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
+  BAMG_DISPATCH_V(lanes_for<T>(M), { k_transfer<BR, BC, V, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
       M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};

@@ -146,52 +146,68 @@ __device__ void winv_cols(double* __restrict__ St, int64_t ld, const double* __r
 }
 
 // Whole coarsest factorisation in one cooperative launch (256 threads per
-// CTA, every CTA runs the same sequence of grid barriers):
-//   Cholesky, step k:  factor + invert tile (k,k) | panel L(i,k) = A(i,k) L(k,k)^-T
-//                      | trailing A(i,j) -= L(i,k) L(j,k)^T
-//   W = L^-1, row i:   W(i,k) = L(i,i)^-1 (delta I - S(i,k)), k <= i
-//                      | S(r,k) += L(r,i) W(i,k), r > i, k <= i   (S accumulated in W)
+// CTA; every CTA runs the same sequence of grid barriers).  One sweep over the
+// 32-wide tile columns k computes the Cholesky factor L and W = L^-1 together:
+//   phase 1:  L(i,k) = A(i,k) L(k,k)^-T, i > k            (panel, row stripes)
+//             W(k,j) = L(k,k)^-1 (delta_kj I - S(k,j)), j <= k   (column stripes)
+//   phase 2:  A(i,j) -= L(i,k) L(j,k)^T, k < j <= i         (trailing update)
+//             S(r,j) += L(r,k) W(k,j), r > k, j <= k         (S accumulated in W)
+//             CTA 0 first updates tile (k+1,k+1), then factors and inverts it
+// so each step needs two barriers, and the inverse's updates fill the SMs
+// that the shrinking trailing matrix leaves idle.
 __global__ void __launch_bounds__(256) k_dense_factor(double* __restrict__ F, double* __restrict__ W, int64_t ld,
                                                       int nt, double* __restrict__ Dinv, int* err) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[kT][kT + 1], w[kT][kT + 1];
   const int G = gridDim.x, b = blockIdx.x;
+  if (b == 0) diag_tile(F, ld, 0, Dinv, err, a, w);
+  __threadfence();
+  grid.sync();
   for (int k = 0; k < nt; ++k) {
-    if (b == 0) diag_tile(F, ld, k, Dinv + (int64_t)k * kT * kT, err, a, w);
-    __threadfence();
-    grid.sync();
-    for (int item = b; item < (nt - k - 1) * 4; item += G) {
-      const int i = k + 1 + item / 4;
-      panel_rows(F + (int64_t)i * kT * ld + (int64_t)k * kT, ld, Dinv + (int64_t)k * kT * kT, (item % 4) * 8, a, w);
-    }
-    __threadfence();
-    grid.sync();
-    const int T = nt - k - 1;
-    for (int item = b; item < T * (T + 1) / 2; item += G) {
-      int idx = item, i = 0;
-      while (idx > i) {  // row-major lower triangle (i, j), j <= i
-        idx -= i + 1;
-        ++i;
+    const double* Lkk_inv = Dinv + (int64_t)k * kT * kT;
+    // phase 1
+    const int n_panel = (nt - k - 1) * 4, n_winv = (k + 1) * 4;
+    for (int item = b; item < n_panel + n_winv; item += G) {
+      if (item < n_panel) {
+        const int i = k + 1 + item / 4;
+        panel_rows(F + (int64_t)i * kT * ld + (int64_t)k * kT, ld, Lkk_inv, (item % 4) * 8, a, w);
+      } else {
+        const int it = item - n_panel, j = it / 4;
+        winv_cols(W + (int64_t)k * kT * ld + (int64_t)j * kT, ld, Lkk_inv, (it % 4) * 8, j == k, a, w);
       }
-      const int gi = k + 1 + i, gj = k + 1 + idx;
-      tile_update<true>(F + (int64_t)gi * kT * ld + (int64_t)gj * kT, F + (int64_t)gi * kT * ld + (int64_t)k * kT,
-                        F + (int64_t)gj * kT * ld + (int64_t)k * kT, ld, a, w);
     }
     __threadfence();
     grid.sync();
-  }
-  for (int i = 0; i < nt; ++i) {
-    for (int item = b; item < (i + 1) * 4; item += G) {
-      const int k = item / 4;
-      winv_cols(W + (int64_t)i * kT * ld + (int64_t)k * kT, ld, Dinv + (int64_t)i * kT * kT, (item % 4) * 8, k == i,
-                a, w);
+    // phase 2
+    const int T = nt - k - 1;
+    const int n_trail = T * (T + 1) / 2, n_wupd = T * (k + 1);
+    if (b == 0 && T > 0) {
+      const int g = k + 1;
+      tile_update<true>(F + (int64_t)g * kT * ld + (int64_t)g * kT, F + (int64_t)g * kT * ld + (int64_t)k * kT,
+                        F + (int64_t)g * kT * ld + (int64_t)k * kT, ld, a, w);
+      __syncthreads();
+      __threadfence_block();
+      diag_tile(F, ld, g, Dinv + (int64_t)g * kT * kT, err, a, w);
     }
-    __threadfence();
-    grid.sync();
-    for (int item = b; item < (nt - i - 1) * (i + 1); item += G) {
-      const int r = i + 1 + item / (i + 1), k = item % (i + 1);
-      tile_update<false>(W + (int64_t)r * kT * ld + (int64_t)k * kT, F + (int64_t)r * kT * ld + (int64_t)i * kT,
-                         W + (int64_t)i * kT * ld + (int64_t)k * kT, ld, a, w);
+    // item 0 of the trailing update is tile (k+1,k+1), done by CTA 0 above
+    for (int item = (b == 0 ? G : b); item < n_trail + n_wupd; item += G) {
+      if (item == 0) continue;
+      if (item < n_trail) {
+        int idx = item, i = 0;
+        while (idx > i) {  // row-major lower triangle (i, j), j <= i
+          idx -= i + 1;
+          ++i;
+        }
+        const int gi = k + 1 + i, gj = k + 1 + idx;
+        tile_update<true>(F + (int64_t)gi * kT * ld + (int64_t)gj * kT,
+                          F + (int64_t)gi * kT * ld + (int64_t)k * kT, F + (int64_t)gj * kT * ld + (int64_t)k * kT,
+                          ld, a, w);
+      } else {
+        const int it = item - n_trail;
+        const int r = k + 1 + it / (k + 1), j = it % (k + 1);
+        tile_update<false>(W + (int64_t)r * kT * ld + (int64_t)j * kT, F + (int64_t)r * kT * ld + (int64_t)k * kT,
+                           W + (int64_t)k * kT * ld + (int64_t)j * kT, ld, a, w);
+      }
     }
     __threadfence();
     grid.sync();

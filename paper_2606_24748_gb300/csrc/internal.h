@@ -95,7 +95,8 @@ struct bamg_bsr {
   int* slot_of = nullptr;    // nnzb: CSR block -> slot
   int* diag_slot = nullptr;  // nbr (square blocks only, -1 if no diagonal block)
   bool all_diag = false;     // every block row has its diagonal block
-  int vec = 1;               // lanes per block row of the row kernels (1..32, power of 2)
+  int vec = 1;               // lanes per block row of the FP64 row kernels (1..32, power of 2)
+  int vec32 = 1;             // the same for kernels reading the FP32 copy
   bool vec_tuned = false;
   std::vector<int> h_slice_ptr, h_slot_of;
   double* vals = nullptr;    // 32 * nchunks * B
@@ -308,5 +309,13 @@ Status launch_to_fp32(const double* src, float* dst, int64_t n, cudaStream_t st)
 int default_vec(const bamg_bsr* A);
 Status bsr_autotune(bamg_bsr* A, float* best_ms);
 inline int64_t row_threads(const bamg_bsr* A) { return A->nslices * kSlice * (int64_t)A->vec; }
+template <typename T>
+inline int lanes_for(const bamg_bsr* A) {
+  return sizeof(T) == 4 ? A->vec32 : A->vec;
+}
+template <typename T>
+inline int64_t row_threads_for(const bamg_bsr* A) {
+  return A->nslices * kSlice * (int64_t)lanes_for<T>(A);
+}
 
 }  // namespace bamg

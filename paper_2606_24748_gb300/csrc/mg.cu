@@ -345,18 +345,18 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
                          double* out_scal) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
-  const int64_t n = A->nbr, rows = row_threads(A);
+  const int64_t n = A->nbr, rows = row_threads_for<TM>(A);
   double* w[2] = {mg->power_w[0], mg->power_w[1]};
   double* norms = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel;  // 2 scratch slots
   const unsigned g = red_grid(rows);
   { k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS); BAMG_COUNT_LAUNCH; }
   for (int it = 0; it < mg->opts.power_its; ++it) {
     const double* nin = it == 0 ? nullptr : norms + ((it + 1) & 1);
-    BAMG_DISPATCH_V(A->vec, { k_power_step<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
+    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
-  BAMG_DISPATCH_V(A->vec, { k_rayleigh<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
+  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
                                                 w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
                                                 mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
@@ -366,8 +366,11 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
 
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal) {
   Level& L = mg->levels[l];
-  const bamg_bsr* A = L.A;
-  const bool f32 = A->vals64_stale;
+  bamg_bsr* A = L.A;
+  // The mixed form estimates the spectrum of the operator its smoother applies
+  // (the FP32 copy), in FP64 arithmetic.
+  const bool f32 = A->vals64_stale || (mg->opts.precision == BAMG_FP32 && !scalar_diag);
+  if (f32) BAMG_TRY(bsr_ensure_fp32(A));
   if (L.bs == 3)
     return f32 ? power_impl<3, float>(mg, A, A->vals32, L.dinv, scalar_diag, out_scal)
                : power_impl<3, double>(mg, A, A->vals, L.dinv, scalar_diag, out_scal);
