@@ -45,6 +45,7 @@ class Level:
     lam: float = 0.0
     chol: np.ndarray | None = None     # lower Cholesky factor (coarsest level)
     Bc: np.ndarray | None = None
+    weights: np.ndarray | None = None  # per-block-row smoother weights (None = plain)
 
 
 @dataclasses.dataclass
@@ -87,7 +88,7 @@ def refresh(h: Hierarchy) -> None:
             L.Ps = L.P.scalar()
     for L in h.levels[:-1]:
         L.Dinv = block_diag_inverse(L.A)
-        L.lam = block_jacobi_lambda(L.A, L.As, L.Dinv)
+        L.lam = block_jacobi_lambda(L.A, L.As, L.Dinv, L.weights)
     C = h.levels[-1]
     C.chol = np.linalg.cholesky(C.A.dense())
 
@@ -112,7 +113,28 @@ def vcycle(h: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
     L = h.levels[level]
     if level == h.n_levels - 1:
         return coarse_solve(L, b)
-    x, r = chebyshev(L.As, L.Dinv, b, None, L.lam, h.degree, want_residual=True)
+    x, r = chebyshev(L.As, L.Dinv, b, None, L.lam, h.degree, want_residual=True, weights=L.weights)
     ec = vcycle(h, L.Ps.T @ r, level + 1)
     x = x + L.Ps @ ec
-    return chebyshev(L.As, L.Dinv, b, x, L.lam, h.degree)
+    return chebyshev(L.As, L.Dinv, b, x, L.lam, h.degree, weights=L.weights)
+
+
+def set_weights(h: Hierarchy, weights: list) -> None:
+    """Per-block-row smoother weights for the non-coarsest levels (None entries
+    keep the plain smoother); the eigen-estimates are refreshed for W D^{-1} A."""
+    for L, w in zip(h.levels[:-1], weights):
+        L.weights = None if w is None else np.asarray(w, dtype=np.float32).astype(np.float64)
+    refresh(h)
+
+
+def stationary(h: Hierarchy, b: np.ndarray, its: int) -> list[float]:
+    """Residual norms of x_{k+1} = x_k + M (b - A x_k), x_0 = 0."""
+    As = h.levels[0].As
+    x = np.zeros_like(b)
+    r = b.copy()
+    out = [float(np.linalg.norm(r))]
+    for _ in range(its):
+        x = x + vcycle(h, r)
+        r = b - As @ x
+        out.append(float(np.linalg.norm(r)))
+    return out

@@ -63,21 +63,33 @@ def power_lambda(As: sp.spmatrix, apply_dinv, quad_d, its: int = POWER_ITS) -> f
 
 
 def block_jacobi_lambda(A: BlockMatrix, As: sp.spmatrix | None = None,
-                        Dinv: np.ndarray | None = None) -> float:
+                        Dinv: np.ndarray | None = None, weights: np.ndarray | None = None) -> float:
+    """Largest eigenvalue estimate of W D^{-1} A (W = per-block-row weights, I if None):
+    the Rayleigh quotient of A v = lam M v with M = D W^{-1}."""
     As = A.scalar() if As is None else As
     D = diagonal_blocks(A)
     Dinv = np.linalg.inv(D) if Dinv is None else Dinv
-    return power_lambda(As, lambda v: apply_blocks(Dinv, v),
-                        lambda v: float(v @ apply_blocks(D, v)))
+    bs = D.shape[1]
+    wr = np.ones(A.nbr) if weights is None else np.asarray(weights, dtype=np.float64)
+    wd = np.repeat(wr, bs)
+    return power_lambda(As, lambda v: wd * apply_blocks(Dinv, v),
+                        lambda v: float(v @ (apply_blocks(D, v) / wd)))
 
 
 def chebyshev(As: sp.spmatrix, Dinv: np.ndarray, b: np.ndarray, x0: np.ndarray | None,
-              lam: float, degree: int = 2, want_residual: bool = False):
-    """Degree-``degree`` Chebyshev smoothing of A x = b from x0 (None = zero).
+              lam: float, degree: int = 2, want_residual: bool = False,
+              weights: np.ndarray | None = None):
+    """Degree-``degree`` Chebyshev smoothing of A x = b from x0 (None = zero),
+    preconditioned by W D^{-1} (W = per-block-row weights, I if None).
 
     Returns x, and also r = b - A x (carried by the recurrence) when
     ``want_residual``; in that case one more product A d is taken.
     """
+    if weights is not None:
+        wd = np.repeat(np.asarray(weights, dtype=np.float64), Dinv.shape[1])
+        apply = lambda v: wd * apply_blocks(Dinv, v)  # noqa: E731
+    else:
+        apply = lambda v: apply_blocks(Dinv, v)  # noqa: E731
     alpha, beta = CHEB_LOWER * lam, CHEB_UPPER * lam
     theta = 0.5 * (beta + alpha)
     delta = 0.5 * (beta - alpha)
@@ -88,7 +100,7 @@ def chebyshev(As: sp.spmatrix, Dinv: np.ndarray, b: np.ndarray, x0: np.ndarray |
     else:
         x = x0.copy()
         r = b - As @ x
-    d = apply_blocks(Dinv, r) / theta
+    d = apply(r) / theta
     rho = 1.0 / sigma
     for k in range(degree):
         x = x + d
@@ -98,6 +110,6 @@ def chebyshev(As: sp.spmatrix, Dinv: np.ndarray, b: np.ndarray, x0: np.ndarray |
         if k == degree - 1:
             break
         rho_new = 1.0 / (2.0 * sigma - rho)
-        d = rho_new * rho * d + (2.0 * rho_new / delta) * apply_blocks(Dinv, r)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * apply(r)
         rho = rho_new
     return (x, r) if want_residual else x
