@@ -251,8 +251,10 @@ BAMG_API bamg_status bamg_vcycle(bamg_mg* mg, const double* b, double* x);
 BAMG_API bamg_status bamg_cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit,
                           bamg_cg_info* info);
 /* Per-block-row smoother weights of a level (device float array of the
- * level's block-row count) scaling each row of the Chebyshev update;
- * w = NULL restores the plain smoother. */
+ * level's block-row count, borrowed) scaling each row of the Chebyshev
+ * update, i.e. the smoother is preconditioned by W D^-1; w = NULL restores
+ * the plain smoother.  The eigen-estimate of W D^-1 A is refreshed by the
+ * next bamg_mg_update. */
 BAMG_API bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w);
 /* Inspection: number of levels; a level's operator and prolongator (P is
  * NULL on the coarsest level); its eigen-estimate and prolongator damping
@@ -263,6 +265,54 @@ BAMG_API bamg_status bamg_mg_get_level_scalars(const bamg_mg* mg, int level, dou
                                       double* omega);
 BAMG_API bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* dinv);
 BAMG_API bamg_status bamg_mg_destroy(bamg_mg* mg);
+
+/* --------------------------------------------- learned smoother weights */
+
+/* Per-block-row smoother weights predicted by a small MLP (not in the paper;
+ * a learned extension of the point-block Jacobi / Chebyshev smoother): 8
+ * features of each block row -> 64 -> 64 -> 1 (ReLU), weight
+ * w = 0.5 + 1.5 sigmoid(z).  Parameters, inputs and hidden activations are
+ * rounded to bfloat16, products accumulated in FP32 (FP32 master parameters,
+ * Adam).  Parameter layout (floats): W1[8][64], b1[64], W2[64][64], b2[64],
+ * w3[64], b3.  X is n x 8 row-major floats, t and w are n floats (device).
+ * Training is deterministic (fixed-order gradient reductions). */
+typedef struct bamg_mlp bamg_mlp;
+BAMG_API bamg_status bamg_mlp_num_params(int* n);
+/* He-uniform initial weights from splitmix64(seed); biases zero. */
+BAMG_API bamg_status bamg_mlp_create(bamg_ctx* ctx, uint64_t seed, bamg_mlp** out);
+BAMG_API bamg_status bamg_mlp_destroy(bamg_mlp* mlp);
+BAMG_API bamg_status bamg_mlp_get_params(const bamg_mlp* mlp, float* params);
+/* Replaces the parameters and resets the optimiser state. */
+BAMG_API bamg_status bamg_mlp_set_params(bamg_mlp* mlp, const float* params);
+BAMG_API bamg_status bamg_mlp_forward(bamg_mlp* mlp, const float* X, int64_t n, float* w);
+/* Gradient of mean((w - t)^2) into grad (device, num_params floats; may be
+ * NULL) and the loss into *loss (device float, may be NULL); w_tmp is an n-float
+ * work array.  Grows the activation buffers on demand (allocates). */
+BAMG_API bamg_status bamg_mlp_gradient(bamg_mlp* mlp, const float* X, const float* t, int64_t n, float* w_tmp,
+                                       float* grad, float* loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on the
+ * batch (X, t); *loss (device, may be NULL) receives the batch loss before the step. */
+BAMG_API bamg_status bamg_mlp_train_step(bamg_mlp* mlp, const float* X, const float* t, int64_t n, float* w_tmp,
+                                         float lr, float* loss);
+/* Features of the block rows of a non-coarsest level (n_l x 8, device):
+ * log||A_ii||, sum_{j!=i}||A_ij||/||A_ii||, log(max/min nonzero block norm),
+ * blocks/27, clamped-row flag, log sum_j||D_i^-1 A_ij||, level, 1. */
+BAMG_API bamg_status bamg_mg_block_features(bamg_mg* mg, int level, float* X);
+/* Training targets from the plain FP64 cycle: for the k right-hand sides B
+ * (device, k consecutive fine vectors) the residual r after pre-smoothing on
+ * every non-coarsest level gives, per block row, clip(sum <r_i, q_i> /
+ * sum ||q_i||^2, 0.5, 2) with q = A D^-1 r; written level after level into
+ * targets (device floats).  Allocates work arrays. */
+BAMG_API bamg_status bamg_mg_smoother_targets(bamg_mg* mg, const double* B, int k, float* targets);
+/* With an MLP attached, every bamg_mg_update predicts the weights of every
+ * non-coarsest level from its features and estimates the Chebyshev interval
+ * for W D^-1 A; a non-finite prediction falls back to weight 1.  NULL
+ * detaches (plain smoother).  bamg_mg_set_smoother_weights also takes effect
+ * at the next update. */
+BAMG_API bamg_status bamg_mg_attach_mlp(bamg_mg* mg, bamg_mlp* mlp);
+/* Stationary iteration x_{k+1} = x_k + M (b - A x_k) from x_0 = 0 for `its`
+ * steps; rnorms (host, its + 1 doubles) receives ||b - A x_k||. */
+BAMG_API bamg_status bamg_mg_stationary(bamg_mg* mg, const double* b, double* x, int its, double* rnorms);
 
 #ifdef __cplusplus
 }

@@ -82,6 +82,18 @@ _SIGS = {
     "bamg_mg_get_level_scalars": [_P, ctypes.c_int, _P, _P],
     "bamg_mg_get_dinv": [_P, ctypes.c_int, _P],
     "bamg_mg_destroy": [_P],
+    "bamg_mlp_num_params": [_P],
+    "bamg_mlp_create": [_P, ctypes.c_uint64, _PP],
+    "bamg_mlp_destroy": [_P],
+    "bamg_mlp_get_params": [_P, _P],
+    "bamg_mlp_set_params": [_P, _P],
+    "bamg_mlp_forward": [_P, _P, _I64, _P],
+    "bamg_mlp_gradient": [_P, _P, _P, _I64, _P, _P, _P],
+    "bamg_mlp_train_step": [_P, _P, _P, _I64, _P, ctypes.c_float, _P],
+    "bamg_mg_block_features": [_P, ctypes.c_int, _P],
+    "bamg_mg_smoother_targets": [_P, _P, ctypes.c_int, _P],
+    "bamg_mg_attach_mlp": [_P, _P],
+    "bamg_mg_stationary": [_P, _P, _P, ctypes.c_int, _P],
 }
 
 _lib = None
@@ -311,6 +323,62 @@ def bamg_mg_get_dinv(ctx, mg, level: int, out):
 
 def bamg_mg_destroy(mg):
     _check(lib().bamg_mg_destroy(mg), None)
+
+
+# ------------------------------------------------- learned smoother weights
+def bamg_mlp_num_params() -> int:
+    n = ctypes.c_int()
+    _check(lib().bamg_mlp_num_params(ctypes.byref(n)), None)
+    return n.value
+
+
+def bamg_mlp_create(ctx, seed: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().bamg_mlp_create(ctx, ctypes.c_uint64(seed), ctypes.byref(h)), ctx)
+    return h
+
+
+def bamg_mlp_destroy(mlp):
+    _check(lib().bamg_mlp_destroy(mlp), None)
+
+
+def bamg_mlp_get_params(ctx, mlp, out):
+    _check(lib().bamg_mlp_get_params(mlp, _ptr(out)), ctx)
+
+
+def bamg_mlp_set_params(ctx, mlp, params):
+    _check(lib().bamg_mlp_set_params(mlp, _ptr(params)), ctx)
+
+
+def bamg_mlp_forward(ctx, mlp, X, w):
+    _check(lib().bamg_mlp_forward(mlp, _ptr(X), int(X.shape[0]), _ptr(w)), ctx)
+
+
+def bamg_mlp_gradient(ctx, mlp, X, t, w_tmp, grad=None, loss=None):
+    _check(lib().bamg_mlp_gradient(mlp, _ptr(X), _ptr(t), int(X.shape[0]), _ptr(w_tmp), _ptr(grad), _ptr(loss)), ctx)
+
+
+def bamg_mlp_train_step(ctx, mlp, X, t, w_tmp, lr: float, loss=None):
+    _check(lib().bamg_mlp_train_step(mlp, _ptr(X), _ptr(t), int(X.shape[0]), _ptr(w_tmp), ctypes.c_float(lr),
+                                     _ptr(loss)), ctx)
+
+
+def bamg_mg_block_features(ctx, mg, level: int, X):
+    _check(lib().bamg_mg_block_features(mg, int(level), _ptr(X)), ctx)
+
+
+def bamg_mg_smoother_targets(ctx, mg, B, k: int, targets):
+    _check(lib().bamg_mg_smoother_targets(mg, _ptr(B), int(k), _ptr(targets)), ctx)
+
+
+def bamg_mg_attach_mlp(ctx, mg, mlp):
+    _check(lib().bamg_mg_attach_mlp(mg, mlp), ctx)
+
+
+def bamg_mg_stationary(ctx, mg, b, x, its: int) -> list:
+    out = (ctypes.c_double * (its + 1))()
+    _check(lib().bamg_mg_stationary(mg, _ptr(b), _ptr(x), int(its), ctypes.byref(out)), ctx)
+    return list(out)
 
 
 def exported_symbols() -> list[str]:

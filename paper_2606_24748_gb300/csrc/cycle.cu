@@ -270,6 +270,16 @@ Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
 }
 
 template Status vcycle_on<double>(bamg_mg*, const int*, cudaStream_t);
+
+Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st) {
+  return mg->levels[l].bs == 3 ? smooth_down<3, double>(mg, l, nullptr, st) : smooth_down<6, double>(mg, l, nullptr, st);
+}
+
+Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st) {
+  Level& L = mg->levels[l];
+  if (L.bs == 3) return transfer<6, 3, double>(L.R, L.R->vals, L.r, mg->levels[l + 1].b, 0, nullptr, st);
+  return transfer<6, 6, double>(L.R, L.R->vals, L.r, mg->levels[l + 1].b, 0, nullptr, st);
+}
 template Status vcycle_on<float>(bamg_mg*, const int*, cudaStream_t);
 
 // z = M r for FP64 vectors r (read) and z (written); in the mixed form the
@@ -290,6 +300,8 @@ static Status precond(bamg_mg* mg, const double* r, double* z, const int* done, 
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
+
+Status mg_precond(bamg_mg* mg, const double* r, double* z, cudaStream_t st) { return precond(mg, r, z, nullptr, st); }
 
 // ------------------------------------------------------------------ CG
 

@@ -181,7 +181,9 @@ struct Level {
   double omega = 0.0;        // prolongator damping used at setup
   double* dinv = nullptr;    // block-diagonal inverse, slice-interleaved
   float* dinv32 = nullptr;
-  float* weights = nullptr;  // per-block-row smoother weights (borrowed), or null
+  float* weights = nullptr;  // per-block-row smoother weights (borrowed or learned_w), or null
+  float* feat = nullptr;     // block features (learned weights)
+  float* learned_w = nullptr;
   // vectors (FP64 and FP32 forms): right-hand side, iterate, residual, directions
   double *b = nullptr, *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d032 = nullptr, *d132 = nullptr;
@@ -194,8 +196,11 @@ struct CgState {
 
 }  // namespace bamg
 
+struct bamg_mlp;
+
 struct bamg_mg {
   bamg_ctx* ctx = nullptr;
+  bamg_mlp* mlp = nullptr;           // attached weight predictor (borrowed), or null
   bamg_mg_opts opts{};
   std::vector<bamg::Level> levels;
   double* scal = nullptr;            // levels x kScalarsPerLevel device scalars
@@ -295,6 +300,10 @@ template <typename T>
 Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
 void mg_release_graphs(bamg_mg* mg);
+Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st);  // features -> MLP -> level weights
+Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st);  // FP64 pre-smoothing of level l (b -> x, r)
+Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st);     // levels[l+1].b = R_l r_l
+Status mg_precond(bamg_mg* mg, const double* r, double* z, cudaStream_t st);  // one V-cycle
 
 // ------------------------------------------------------------ kernel launchers
 // y = A x (row-block product) in precision T (double or float); x, y device.

@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restric
                                                             const int* __restrict__ col, const TM* __restrict__ vals,
                                                             const int* __restrict__ diag_slot,
                                                             const double* __restrict__ dinv, int scalar_diag,
+                                                            const float* __restrict__ wts,
                                                             const double* __restrict__ w_in,
                                                             double* __restrict__ w_out, const double* norm_in,
                                                             double* norm_out, int64_t n, int64_t nthreads,
@@ -261,12 +262,13 @@ __global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restric
         for (int r = 0; r < BS; ++r) z[r] = acc[r] * s / (double)vals[vidx<B>(ds, r * BS + r)];
       } else {
         const int64_t base = (row >> 5) * (32LL * B) + (row & 31);
+        const double wr = wts ? (double)wts[row] : 1.0;
 #pragma unroll
         for (int r = 0; r < BS; ++r) {
           double t = 0.0;
 #pragma unroll
           for (int c = 0; c < BS; ++c) t = fma(dinv[base + 32 * (r * BS + c)], acc[c] * s, t);
-          z[r] = t;
+          z[r] = wr * t;
         }
       }
 #pragma unroll
@@ -286,6 +288,7 @@ template <int BS, int V, typename TM>
 __global__ void __launch_bounds__(kRowThreads) k_rayleigh(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const TM* __restrict__ vals,
                                                           const int* __restrict__ diag_slot, int scalar_diag,
+                                                          const float* __restrict__ wts,
                                                           const double* __restrict__ w, int64_t n, int64_t nthreads,
                                                           double* partials, unsigned* counter, double* out_scal,
                                                           double lower, double upper, int degree) {
@@ -312,7 +315,8 @@ __global__ void __launch_bounds__(kRowThreads) k_rayleigh(const int* __restrict_
           double t = 0.0;
 #pragma unroll
           for (int c = 0; c < BS; ++c) t = fma((double)vals[vidx<B>(ds, r * BS + c)], wi[c], t);
-          local[1] = fma(wi[r], t, local[1]);
+          // M = D W^-1: the quotient of A v = lam M v for the preconditioner W D^-1
+          local[1] = fma(wi[r], wts ? t / (double)wts[row] : t, local[1]);
         }
       }
     }
@@ -341,8 +345,8 @@ static unsigned red_grid(int64_t rows) {
 }
 
 template <int BS, typename TM>
-static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const double* dinv, bool scalar_diag,
-                         double* out_scal) {
+static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const double* dinv, const float* wts,
+                         bool scalar_diag, double* out_scal) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
   const int64_t n = A->nbr, rows = row_threads_for<TM>(A);
@@ -353,11 +357,11 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
   for (int it = 0; it < mg->opts.power_its; ++it) {
     const double* nin = it == 0 ? nullptr : norms + ((it + 1) & 1);
     BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
-                                                    scalar_diag ? 1 : 0, w[it & 1], w[(it + 1) & 1], nin,
+                                                    scalar_diag ? 1 : 0, scalar_diag ? nullptr : wts, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
   BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
-                                                w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
+                                                scalar_diag ? nullptr : wts, w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
                                                 mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
@@ -371,12 +375,13 @@ Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal) {
   // (the FP32 copy), in FP64 arithmetic.
   const bool f32 = A->vals64_stale || (mg->opts.precision == BAMG_FP32 && !scalar_diag);
   if (f32) BAMG_TRY(bsr_ensure_fp32(A));
+  const float* wts = L.weights;
   if (L.bs == 3)
-    return f32 ? power_impl<3, float>(mg, A, A->vals32, L.dinv, scalar_diag, out_scal)
-               : power_impl<3, double>(mg, A, A->vals, L.dinv, scalar_diag, out_scal);
+    return f32 ? power_impl<3, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal)
+               : power_impl<3, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal);
   if (L.bs == 6)
-    return f32 ? power_impl<6, float>(mg, A, A->vals32, L.dinv, scalar_diag, out_scal)
-               : power_impl<6, double>(mg, A, A->vals, L.dinv, scalar_diag, out_scal);
+    return f32 ? power_impl<6, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal)
+               : power_impl<6, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal);
   return make_status(BAMG_ERR_INVALID, "block size %d", L.bs);
 }
 
@@ -401,6 +406,7 @@ Status mg_refresh_level(bamg_mg* mg, int l) {
     }
     BAMG_CUDA(cudaGetLastError());
   }
+  BAMG_TRY(mg_learned_weights(mg, l, st));
   return power_lambda(mg, l, false, mg->scal + (int64_t)l * kScalarsPerLevel);
 }
 
@@ -488,6 +494,8 @@ static void mg_release(bamg_mg* mg) {
     if (L.R) bamg_bsr_destroy(L.R);
     dfree(L.rmap, st);
     for (double** p : {&L.b, &L.x, &L.r, &L.d0, &L.d1, &L.dinv}) dfree(*p, st);
+    dfree(L.feat, st);
+    dfree(L.learned_w, st);
     for (float** p : {&L.b32, &L.x32, &L.r32, &L.d032, &L.d132, &L.dinv32}) dfree(*p, st);
   }
   for (double** p : {&mg->cx, &mg->cr, &mg->cp, &mg->cq, &mg->cz, &mg->czold, &mg->scal, &mg->power_w[0],

@@ -1,0 +1,169 @@
+"""Training and evaluation driver for the learned smoother weights.
+
+Builds inclusion-mesh instances (3D elasticity with a heterogeneous Young's
+modulus), generates (features, target) pairs with the plain V-cycle, trains
+the MLP on the GPU with the library's own forward/backward/Adam kernels, and
+compares the learned and the plain smoother on held-out instances: V-cycle
+convergence factor of the stationary iteration and CG iterations / time to
+rtol 1e-8.  Every numerical step runs in libbamg; this module only moves
+tensors and calls the C ABI.
+
+    python -m paper_2606_24748_gb300.learned --ne 48 --train 200 --test 50
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import bamg as B
+
+K_RHS = 4
+
+
+class Instance:
+    """One inclusion mesh assembled through blocked COO with its hierarchy."""
+
+    def __init__(self, ctx, ne: int, seed: int, nu: float = 0.3, precision: int = B.BAMG_FP64):
+        from workloads.elasticity import (Mesh, coo_indices, coo_values, element_scale, gaussian_rhs,
+                                          inclusion_moduli, body_force)
+        self.ctx = ctx
+        self.mesh = Mesh(ne)
+        m = self.mesh
+        bi, bj = coo_indices(m, "cuda")
+        self.A = B.bamg_bsr_create(ctx, 3, 3, m.n_nodes, m.n_nodes)
+        B.bamg_bsr_coo_preallocate(ctx, self.A, bi, bj)
+        vals = coo_values(m, nu, element_scale(m, E_el=inclusion_moduli(m, seed)), "cuda")
+        B.bamg_bsr_coo_set_values(ctx, self.A, vals, 0)
+        del vals, bi, bj
+        o = B.bamg_mg_opts_default()
+        o.grid[0] = o.grid[1] = o.grid[2] = m.m
+        o.precision = precision
+        self.mg = B.bamg_mg_setup(ctx, self.A, m.coords(), m.dirichlet(), o)
+        self.nl = B.bamg_mg_num_levels(self.mg)
+        self.rows = [B.bamg_bsr_info(B.bamg_mg_get_level(self.mg, l)[0])["nbr"] for l in range(self.nl - 1)]
+        self.rhs = torch.from_numpy(np.stack([gaussian_rhs(m, 10_000 + 31 * seed + k) for k in range(K_RHS)])).cuda()
+        self.b = torch.from_numpy(body_force(m)).cuda()
+
+    def data(self):
+        """(features, targets) of every non-coarsest level, stacked."""
+        n = sum(self.rows)
+        X = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+        t = torch.empty(n, dtype=torch.float32, device="cuda")
+        off = 0
+        for l, nr in enumerate(self.rows):
+            B.bamg_mg_block_features(self.ctx, self.mg, l, X[off:off + nr])
+            off += nr
+        B.bamg_mg_smoother_targets(self.ctx, self.mg, self.rhs, K_RHS, t)
+        return X, t
+
+    def measure(self, its: int = 10):
+        """Convergence factor of 10 stationary V-cycles and CG to 1e-8 (iterations, ms)."""
+        x = torch.zeros_like(self.b)
+        rn = B.bamg_mg_stationary(self.ctx, self.mg, self.b, x, its)
+        rho = (rn[-1] / rn[0]) ** (1.0 / its)
+        B.bamg_cg_solve(self.ctx, self.mg, self.b, x, 1e-8, 500, check=False)   # warm the graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = B.bamg_cg_solve(self.ctx, self.mg, self.b, x, 1e-8, 500, check=False)
+        ms = (time.perf_counter() - t0) * 1e3
+        return {"rho": rho, "cg_its": out["iterations"], "cg_ms": ms, "converged": out["converged"]}
+
+    def close(self):
+        B.bamg_mg_destroy(self.mg)
+        B.bamg_bsr_destroy(self.A)
+
+
+def train(ctx, mlp, X, t, epochs: int = 30, batch: int = 32768, lr: float = 1e-3, seed: int = 0):
+    """Mini-batch Adam on (X, t); returns the loss after every epoch."""
+    n = X.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    w_tmp = torch.empty(min(batch, n), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).cuda()
+        tot, cnt = 0.0, 0
+        for s in range(0, n, batch):
+            idx = perm[s:s + batch]
+            Xb, tb = X[idx].contiguous(), t[idx].contiguous()
+            B.bamg_mlp_train_step(ctx, mlp, Xb, tb, w_tmp, lr, loss)
+            tot += float(loss.item()) * idx.numel()
+            cnt += idx.numel()
+        hist.append(tot / cnt)
+    return hist
+
+
+def mse(ctx, mlp, X, t) -> float:
+    w = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    B.bamg_mlp_forward(ctx, mlp, X, w)
+    return float(torch.mean((w - t) ** 2).item())
+
+
+def run(ne: int = 48, n_train: int = 200, n_test: int = 50, epochs: int = 30, seed0_train: int = 0,
+        seed0_test: int = 1000, log=print) -> dict:
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    mlp = B.bamg_mlp_create(ctx, 12345)
+    Xs, ts = [], []
+    t0 = time.perf_counter()
+    for k in range(n_train):
+        inst = Instance(ctx, ne, seed0_train + k)
+        X, t = inst.data()
+        Xs.append(X)
+        ts.append(t)
+        inst.close()
+    X, t = torch.cat(Xs), torch.cat(ts)
+    t_data = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = train(ctx, mlp, X, t, epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    log(f"training set {X.shape[0]} rows from {n_train} instances in {t_data:.1f} s; "
+        f"{epochs} epochs in {t_train:.2f} s, loss {hist[0]:.4f} -> {hist[-1]:.4f}")
+    const = float(torch.mean((t - t.mean()) ** 2).item())
+    res = []
+    for k in range(n_test):
+        inst = Instance(ctx, ne, seed0_test + k)
+        Xt, tt = inst.data()
+        plain = inst.measure()
+        B.bamg_mg_attach_mlp(ctx, inst.mg, mlp)
+        B.bamg_mg_update(ctx, inst.mg)
+        learned = inst.measure()
+        test_mse = mse(ctx, mlp, Xt, tt)
+        res.append({"plain": plain, "learned": learned, "mse": test_mse})
+        inst.close()
+    B.bamg_mlp_destroy(mlp)
+    B.bamg_ctx_destroy(ctx)
+
+    def agg(key, f):
+        return float(np.mean([r[key][f] for r in res]))
+    out = {
+        "ne": ne, "train_instances": n_train, "test_instances": n_test, "train_rows": int(X.shape[0]),
+        "epochs": epochs, "train_seconds": round(t_train, 3), "data_seconds": round(t_data, 1),
+        "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "target_variance": const,
+        "test_mse": float(np.mean([r["mse"] for r in res])),
+        "rho_plain": agg("plain", "rho"), "rho_learned": agg("learned", "rho"),
+        "cg_its_plain": agg("plain", "cg_its"), "cg_its_learned": agg("learned", "cg_its"),
+        "cg_ms_plain": agg("plain", "cg_ms"), "cg_ms_learned": agg("learned", "cg_ms"),
+        "learned_better_fraction": float(np.mean([r["learned"]["rho"] < r["plain"]["rho"] for r in res])),
+    }
+    out["use_learned"] = out["rho_learned"] < out["rho_plain"]
+    return out
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--ne", type=int, default=48)
+    p.add_argument("--train", type=int, default=200)
+    p.add_argument("--test", type=int, default=50)
+    p.add_argument("--epochs", type=int, default=30)
+    a = p.parse_args()
+    print(json.dumps(run(a.ne, a.train, a.test, a.epochs)))
+
+
+if __name__ == "__main__":
+    main()
