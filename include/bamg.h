@@ -236,6 +236,12 @@ BAMG_API void bamg_mg_opts_default(bamg_mg_opts* opts);
  * must outlive the hierarchy. */
 BAMG_API bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords,
                           const uint8_t* dirichlet, const bamg_mg_opts* opts, bamg_mg** out);
+/* Numeric re-setup for a new operator with the same pattern (same mesh):
+ * reuses aggregates, tentative prolongators and every symbolic plan, and
+ * recomputes the prolongator damping, the smoothed prolongators and the
+ * Galerkin products from the current values of A, then runs the update.
+ * Equivalent to a fresh bamg_mg_setup of the same operator. */
+BAMG_API bamg_status bamg_mg_resetup(bamg_mg* mg);
 /* Hot reuse step (Sec. 3.1): with the prolongators fixed, recompute every
  * Galerkin product from the current values of A, then the smoother data
  * (block-diagonal inverses, eigen-estimates) and the coarsest factor. */

@@ -74,6 +74,7 @@ _SIGS = {
     "bamg_ptap_destroy": [_P],
     "bamg_mg_setup": [_P, _P, _P, _P, ctypes.POINTER(bamg_mg_opts), _PP],
     "bamg_mg_update": [_P],
+    "bamg_mg_resetup": [_P],
     "bamg_vcycle": [_P, _P, _P],
     "bamg_cg_solve": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
     "bamg_mg_set_smoother_weights": [_P, ctypes.c_int, _P],
@@ -279,6 +280,10 @@ def bamg_mg_setup(ctx, A, coords: np.ndarray, dirichlet: np.ndarray, opts: bamg_
 
 def bamg_mg_update(ctx, mg):
     _check(lib().bamg_mg_update(mg), ctx)
+
+
+def bamg_mg_resetup(ctx, mg):
+    _check(lib().bamg_mg_resetup(mg), ctx)
 
 
 def bamg_vcycle(ctx, mg, b, x):

@@ -184,6 +184,12 @@ struct Level {
   float* weights = nullptr;  // per-block-row smoother weights (borrowed or learned_w), or null
   float* feat = nullptr;     // block features (learned weights)
   float* learned_w = nullptr;
+  // prolongator smoothing data, kept for bamg_mg_resetup
+  bamg_bsr* Pt = nullptr;    // tentative prolongator (geometry only)
+  bamg_ptap* ap = nullptr;   // plan of A P~ (stage 1 only)
+  int* zrow = nullptr;       // block row of each block of A P~
+  int* agg = nullptr;        // aggregate of each node
+  double* q = nullptr;       // P~ blocks, node-major
   // vectors (FP64 and FP32 forms): right-hand side, iterate, residual, directions
   double *b = nullptr, *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d032 = nullptr, *d132 = nullptr;
@@ -204,6 +210,7 @@ struct bamg_mg {
   bamg_mg_opts opts{};
   std::vector<bamg::Level> levels;
   double* scal = nullptr;            // levels x kScalarsPerLevel device scalars
+  int scal_blocks_minus1 = 0;        // index of the spare block of scalars
   bamg::CoarseDense coarse;
   // CG work vectors (fine level, FP64) and state
   double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr, *czold = nullptr;

@@ -477,6 +477,7 @@ static Status alloc_vectors(bamg_mg* mg) {
   BAMG_CUDA(cudaMallocHost(&mg->cg_host, sizeof(CgState)));
   const int64_t ns = ((int64_t)mg->levels.size() + 1) * kScalarsPerLevel;
   BAMG_TRY(dalloc(&mg->scal, ns, st));
+  mg->scal_blocks_minus1 = (int)mg->levels.size();
   BAMG_CUDA(cudaMemsetAsync(mg->scal, 0, sizeof(double) * ns, st));
   return Status{};
 }
@@ -489,6 +490,11 @@ static void mg_release(bamg_mg* mg) {
       ptap_release(L.plan);
       delete L.plan;
     }
+    if (L.ap) bamg_ptap_destroy(L.ap);
+    if (L.Pt) bamg_bsr_destroy(L.Pt);
+    dfree(L.zrow, st);
+    dfree(L.agg, st);
+    dfree(L.q, st);
     if (L.own_A && L.A) bamg_bsr_destroy(L.A);
     if (L.P) bamg_bsr_destroy(L.P);
     if (L.R) bamg_bsr_destroy(L.R);
@@ -508,6 +514,40 @@ static void mg_release(bamg_mg* mg) {
   cudaStreamSynchronize(st);
 }
 
+// Prolongator smoothing of level l from the current values of its operator
+// (Sec. 2.2): omega = 4 / (3 lambda_max(D_s^-1 A)), P = P~ - omega D_s^-1 A P~.
+static Status smooth_level(bamg_mg* mg, int l) {
+  bamg_ctx* ctx = mg->ctx;
+  cudaStream_t st = ctx->stream;
+  Level& L = mg->levels[l];
+  const int bs = L.bs;
+  // scratch slot in the last (spare) block of scalars
+  double* lam_slot = mg->scal + (int64_t)mg->scal_blocks_minus1 * kScalarsPerLevel + 4;
+  BAMG_TRY(power_lambda(mg, l, true, lam_slot));
+  double lam_s = 0.0;
+  BAMG_CUDA(cudaMemcpyAsync(&lam_s, lam_slot + kLam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BAMG_CUDA(cudaStreamSynchronize(st));
+  if (!(lam_s > 0.0) || !std::isfinite(lam_s))
+    return make_status(BAMG_ERR_BREAKDOWN, "level %d: eigen-estimate %g is not positive", l, lam_s);
+  L.omega = 4.0 / (3.0 * lam_s);
+  BAMG_TRY(ptap_run(L.ap, L.A, L.Pt, nullptr, BAMG_FP64, false));
+  bamg_bsr* P = L.P;
+  const int64_t nt = P->nnzb * bs * 6;
+  if (nt > 0) {
+    const unsigned b = (unsigned)((nt + 255) / 256);
+    if (bs == 3)
+      { k_smooth_prolongator<3><<<b, 256, 0, st>>>(P->nnzb, L.zrow, P->colidx, L.ap->Z, L.agg, L.q, L.A->diag_slot,
+                                                 L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
+    else
+      { k_smooth_prolongator<6><<<b, 256, 0, st>>>(P->nnzb, L.zrow, P->colidx, L.ap->Z, L.agg, L.q, L.A->diag_slot,
+                                                 L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
+    BAMG_CUDA(cudaGetLastError());
+  }
+  P->version++;
+  P->vals64_stale = false;
+  return Status{};
+}
+
 static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, const uint8_t* dir) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
@@ -524,6 +564,7 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
   BAMG_TRY(dalloc(&mg->power_w[0], A->nbr * 6, st));
   BAMG_TRY(dalloc(&mg->power_w[1], A->nbr * 6, st));
   BAMG_TRY(dalloc(&mg->scal, (int64_t)(o.max_levels + 1) * kScalarsPerLevel, st));
+  mg->scal_blocks_minus1 = o.max_levels;
   while (mg->levels.back().n * mg->levels.back().bs > o.max_coarse_dofs && (int)mg->levels.size() < o.max_levels) {
     const int l = (int)mg->levels.size() - 1;
     Level& L = mg->levels[l];
@@ -574,20 +615,12 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       BAMG_TRY(bsr_set_pattern(Pt, std::move(rp), std::move(ci)));
       BAMG_TRY(bsr_upload_values(Pt, Q));
     }
-    // damping omega = 4 / (3 lambda_max(D_s^-1 A))
-    double* lam_slot = mg->scal + (int64_t)o.max_levels * kScalarsPerLevel + 4;
-    BAMG_TRY(power_lambda(mg, l, true, lam_slot));
-    double lam_s = 0.0;
-    BAMG_CUDA(cudaMemcpyAsync(&lam_s, lam_slot + kLam, sizeof(double), cudaMemcpyDeviceToHost, st));
-    BAMG_CUDA(cudaStreamSynchronize(st));
-    if (!(lam_s > 0.0) || !std::isfinite(lam_s))
-      return make_status(BAMG_ERR_BREAKDOWN, "level %d: eigen-estimate %g is not positive", l, lam_s);
-    L.omega = 4.0 / (3.0 * lam_s);
-    // P = P~ - omega D_s^-1 A P~ on the pattern of A P~
+    // P = P~ - omega D_s^-1 A P~ on the pattern of A P~ (values by smooth_level)
     bamg_ptap* ap = nullptr;
     BAMG_TRY(ptap_build(L.A, Pt, false, &ap, nullptr));
-    std::unique_ptr<bamg_ptap, bamg_status (*)(bamg_ptap*)> ap_guard(ap, bamg_ptap_destroy);
-    BAMG_TRY(ptap_run(ap, L.A, Pt, nullptr, BAMG_FP64, false));
+    L.ap = ap;
+    L.Pt = Pt;
+    Pt_guard.release();
     bamg_bsr* P = nullptr;
     if (bamg_bsr_create(ctx, bs, 6, L.n, nagg, &P) != BAMG_OK) return make_status(BAMG_ERR_OOM, "P");
     L.P = P;
@@ -597,29 +630,12 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       for (int64_t i = 0; i < L.n; ++i)
         for (int z = zr[i]; z < zr[i + 1]; ++z) zrow[z] = (int)i;
       BAMG_TRY(bsr_set_pattern(P, std::move(zr), std::move(zc)));
-      int *d_zrow = nullptr, *d_agg = nullptr;
-      double* d_q = nullptr;
-      BAMG_TRY(upload(&d_zrow, zrow, st));
-      BAMG_TRY(upload(&d_agg, agg, st));
-      BAMG_TRY(upload(&d_q, Q, st));
-      const int64_t nt = P->nnzb * bs * 6;
-      if (nt > 0) {
-        const unsigned b = (unsigned)((nt + 255) / 256);
-        if (bs == 3)
-          { k_smooth_prolongator<3><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
-                                                     L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
-        else
-          { k_smooth_prolongator<6><<<b, 256, 0, st>>>(P->nnzb, d_zrow, P->colidx, ap->Z, d_agg, d_q, L.A->diag_slot,
-                                                     L.A->vals, L.omega, P->slot_of, P->vals); BAMG_COUNT_LAUNCH; }
-      }
-      cudaError_t e = cudaGetLastError();
-      cudaStreamSynchronize(st);
-      dfree(d_zrow, st);
-      dfree(d_agg, st);
-      dfree(d_q, st);
-      if (e != cudaSuccess) return cuda_status(e, "smooth prolongator");
-      P->version++;
+      BAMG_TRY(upload(&L.zrow, zrow, st));
+      BAMG_TRY(upload(&L.agg, agg, st));
+      BAMG_TRY(upload(&L.q, Q, st));
+      BAMG_CUDA(cudaStreamSynchronize(st));
     }
+    BAMG_TRY(smooth_level(mg, l));
     // R = P^T pattern and block map (values filled by the state-gated refresh)
     {
       const auto &pr = P->h_rowptr, &pc = P->h_colidx;
@@ -648,8 +664,6 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       plan->prof_stage1 = BAMG_PROF_PTAP_STAGE1_L0;
       plan->prof_stage2 = BAMG_PROF_PTAP_STAGE2_L0;
     }
-    ap_guard.reset();
-    Pt_guard.reset();
     Level C;
     C.A = Ac;
     C.own_A = true;
@@ -749,6 +763,21 @@ bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, cons
   }
   *out = mg;
   return BAMG_OK;
+}
+
+bamg_status bamg_mg_resetup(bamg_mg* mg) {
+  if (!mg) return BAMG_ERR_INVALID;
+  auto body = [&]() -> Status {
+    const int nl = (int)mg->levels.size();
+    for (int l = 0; l + 1 < nl; ++l) {
+      BAMG_TRY(smooth_level(mg, l));
+      BAMG_TRY(ptap_run(mg->levels[l].plan, mg->levels[l].A, mg->levels[l].P, mg->levels[l + 1].A, BAMG_FP64, true));
+    }
+    BAMG_TRY(mg_update_impl(mg));
+    return check_device_error(mg->ctx);
+  };
+  Status s = body();
+  return s.ok() ? BAMG_OK : fail(mg->ctx, s);
 }
 
 bamg_status bamg_mg_update(bamg_mg* mg) {

@@ -167,12 +167,12 @@ def test_training_reduces_the_loss():
     mlp = B.bamg_mlp_create(ctx, 3)
     try:
         Xs, ts = [], []
+        probs = learned.InclusionProblems(ctx, 12)
         for s in range(2):
-            inst = learned.Instance(ctx, 12, s)
-            X, t = inst.data()
+            X, t = probs.load(s).data()
             Xs.append(X)
             ts.append(t)
-            inst.close()
+        probs.close()
         X, t = torch.cat(Xs), torch.cat(ts)
         before = learned.mse(ctx, mlp, X, t)
         hist = learned.train(ctx, mlp, X, t, epochs=40, batch=2048, lr=3e-3)
@@ -181,3 +181,27 @@ def test_training_reduces_the_loss():
     finally:
         B.bamg_mlp_destroy(mlp)
         B.bamg_ctx_destroy(ctx)
+
+
+def test_numeric_resetup_equals_a_fresh_setup():
+    from gpu_helpers import read_bsr, same_pattern
+    ne = 13
+    fresh = GpuProblem(ne, seed=21)
+    reuse = GpuProblem(ne, seed=5)
+    try:
+        reuse.reassemble(21)
+        B.bamg_mg_resetup(reuse.ctx, reuse.mg)
+        for l in range(B.bamg_mg_num_levels(fresh.mg)):
+            Af, Pf = B.bamg_mg_get_level(fresh.mg, l)
+            Ar, Pr = B.bamg_mg_get_level(reuse.mg, l)
+            a, b = read_bsr(fresh.ctx, Af), read_bsr(reuse.ctx, Ar)
+            assert same_pattern(a, b) and rel(b.vals, a.vals) <= 1e-13
+            if Pf is not None:
+                pa, pb = read_bsr(fresh.ctx, Pf), read_bsr(reuse.ctx, Pr)
+                assert rel(pb.vals, pa.vals) <= 1e-13
+        h = hierarchy(ne)   # the unperturbed problem differs: resetup really recomputed P
+        pr = read_bsr(reuse.ctx, B.bamg_mg_get_level(reuse.mg, 0)[1])
+        assert rel(pr.vals, h.levels[0].P.vals) > 1e-8
+    finally:
+        fresh.close()
+        reuse.close()
