@@ -234,7 +234,9 @@ def run_ours(args):
         tdist.init_process_group("nccl")
         dist = tdist
     K, W = args.steps, args.warmup
-    wl = Workload(B, torch, args.ne, 0.3, args.precision, n_inputs=min(K + W, 8))
+    stream_bytes = 72 * 64 * args.ne ** 3
+    wl = Workload(B, torch, args.ne, 0.3, args.precision,
+                  n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))))
     for k in range(W):
         wl.step(k)
     clocks = Clocks(local)
@@ -283,9 +285,13 @@ def run_ours(args):
     if not args.no_e2e:
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
     if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
+        out0 = wl.step(0)
+        x64 = wl.x.clone()
+        result["fp64_input0"] = {"cg_iterations": out0["iterations"],
+                                 "true_residual_rel": out0["true_rnorm"] / out0["bnorm"]}
         wl.close()
         wl = None
-        result["mixed"] = compare_mixed(args, torch, B)
+        result["mixed"] = compare_mixed(args, torch, B, x64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(samples=1)
     if wl is not None:
@@ -369,7 +375,7 @@ def phases(wl, torch, B):
 def e2e(wl, torch, B, dist, K, W, world, per_step):
     """Same step through the C ABI with host buffers: the value stream and b
     copied from pinned host memory, the solution read back, every step."""
-    n_host = min(2, len(wl.inputs))
+    n_host = min(2 if wl.n_coo * 72 < 4e9 else 1, len(wl.inputs))
     host_in = [t.cpu().pin_memory() for t in wl.inputs[:n_host]]
     host_b = wl.b.cpu().pin_memory()
     host_x = torch.empty_like(host_b).pin_memory()
@@ -400,20 +406,26 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
             "d2h_bytes_per_step": int(host_x.numel() * 8)}
 
 
-def compare_mixed(args, torch, B):
-    """Time to rtol 1e-8 of the mixed-precision form on the same workload."""
-    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=2)
+def compare_mixed(args, torch, B, x64=None):
+    """Time to rtol 1e-8 of the mixed-precision form on the same workload, and
+    its solution against the FP64 form's for the same input."""
+    K = max(3, min(args.steps, 10))
+    stream_bytes = 72 * 64 * args.ne ** 3
+    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))))
     for k in range(2):
         wl.step(k)
-    K = max(3, min(args.steps, 10))
     ms, outs = timed(torch, None, lambda k: wl.step(k), K)
     ph = phases(wl, torch, B)
-    x = wl.x.clone()
     its = [o["iterations"] for o in outs]
     res = {"ms_per_step": round(ms / K, 4), "cg_iterations": its, "phases_ms": ph,
            "true_residual_rel": outs[-1]["true_rnorm"] / outs[-1]["bnorm"]}
+    if x64 is not None:
+        out0 = wl.step(0)
+        d = torch.linalg.norm(wl.x - x64) / torch.linalg.norm(x64)
+        res["input0"] = {"cg_iterations": out0["iterations"],
+                         "true_residual_rel": out0["true_rnorm"] / out0["bnorm"],
+                         "solution_rel_diff_vs_fp64": float(d.item())}
     wl.close()
-    del x
     return res
 
 
