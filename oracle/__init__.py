@@ -17,4 +17,6 @@ Modules
   multigrid    hierarchy setup / reuse update / V-cycle (Sec. 2.1, Sec. 3.1)
   krylov       preconditioned CG (Sec. 4.1)
   splitmix     the splitmix64 counter-based generator (start vectors)
+  learned      features, targets, MLP and Adam of the learned smoother weights
+  multi_rhs    many right-hand sides: the cycle and CG column by column
 """
