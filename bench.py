@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-multi", action="store_true", help="skip the 16-right-hand-side measurement")
     return p.parse_args()
 
 
@@ -284,6 +285,8 @@ def run_ours(args):
     result["phases_ms"] = phases(wl, torch, B)
     if not args.no_e2e:
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
+    if not args.no_multi and args.precision == "fp64" and rank == 0 and world == 1:
+        result["multi_rhs"] = multi_rhs(wl, torch, B)
     if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
         out0 = wl.step(0)
         x64 = wl.x.clone()
@@ -404,6 +407,82 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
             "ms_per_step": round(ms_step, 4),
             "h2d_bytes_per_step": int(host_in[0].numel() * 8 + host_b.numel() * 8),
             "d2h_bytes_per_step": int(host_x.numel() * 8)}
+
+
+def event_ms(torch, fn, reps):
+    """Device time of fn() per call (CUDA events on the current stream)."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def multi_rhs(wl, torch, B, k=16):
+    """k seeded N(0,1) right-hand sides (clamped dofs zeroed) on the workload's
+    operator: blocked SpMM against k SpMVs, and the k-column PCG against k
+    single-vector solves, in the FP64 form and the mixed form."""
+    from workloads.elasticity import gaussian_rhs
+    m = wl.mesh
+    n = m.n_dofs
+    a = wl.levels[0]["A"]
+    Bh = np.stack([gaussian_rhs(m, s) for s in range(k)], axis=1)
+    Bd = torch.from_numpy(Bh).cuda()
+    X = torch.zeros_like(Bd)
+    out = {"k": k, "rhs": "N(0,1) seeds 0..%d, clamped dofs zeroed" % (k - 1)}
+    # SpMM vs k SpMVs on the fine operator (operator 0.55 GB FP64: larger than L2)
+    cols = [Bd[:, j].contiguous() for j in range(k)]
+    ys = [torch.empty_like(c) for c in cols]
+    for prec, s, name in ((B.BAMG_FP64, 8, "fp64"), (B.BAMG_FP32, 4, "fp32")):
+        if prec == B.BAMG_FP32:
+            Xs, Ys = Bd.float(), torch.empty(n, k, dtype=torch.float32, device="cuda")
+            cs = [c.float() for c in cols]
+            yss = [y.float() for y in ys]
+        else:
+            Xs, Ys, cs, yss = Bd, X, cols, ys
+        f_mm = lambda: B.bamg_bsr_spmm(wl.ctx, wl.A, Xs, Ys, k, prec)  # noqa: E731
+        f_mv = lambda: [B.bamg_bsr_spmv(wl.ctx, wl.A, c, y, prec) for c, y in zip(cs, yss)]  # noqa: E731
+        for _ in range(3):
+            f_mm()
+            f_mv()
+        t_mm = event_ms(torch, f_mm, 10)
+        t_mv = event_ms(torch, f_mv, 3)
+        byts = bm.spmm_bytes(a["nnzb"], a["nbr"], a["nbc"], 3, 3, k, s)
+        flops = bm.spmv_flops(a["nnzb"], 3, 3) * k
+        out[f"spmm_{name}"] = {"ms": round(t_mm, 4), "gbs": round(byts / t_mm / 1e6, 1),
+                               "tflops": round(flops / t_mm / 1e9, 4),
+                               "k_spmv_ms": round(t_mv, 4), "speedup_vs_k_spmv": round(t_mv / t_mm, 2)}
+        if prec == B.BAMG_FP64:
+            out[f"spmm_{name}"]["frac_fp64_peak"] = round(flops / t_mm / 1e9 / FP64_PEAK_TFLOPS, 3)
+    # k-column PCG vs k single solves: FP64 hierarchy (the workload's) and a mixed one
+    ctx, A = wl.ctx, wl.A
+    o = B.bamg_mg_opts_default()
+    o.grid[0] = o.grid[1] = o.grid[2] = m.m
+    o.precision = B.BAMG_FP32
+    mg32 = B.bamg_mg_setup(ctx, A, m.coords(), m.dirichlet(), o)
+    for name, mg in (("fp64", wl.mg), ("mixed", mg32)):
+        B.bamg_mg_update(ctx, mg)
+        B.bamg_cg_solve_multi(ctx, mg, Bd, X, k, RTOL, MAXIT)   # warm-up (allocates, captures)
+        B.bamg_cg_solve(ctx, mg, cols[0], ys[0], RTOL, MAXIT)
+        res = {}
+        t_blk = event_ms(torch, lambda: res.__setitem__("i", B.bamg_cg_solve_multi(ctx, mg, Bd, X, k, RTOL, MAXIT)), 2)
+        infos = res["i"]
+        seq = []
+        t_seq = event_ms(torch, lambda: seq.append([B.bamg_cg_solve(ctx, mg, c, y, RTOL, MAXIT) for c, y in zip(cols, ys)]), 1)
+        its_b = [i["iterations"] for i in infos]
+        its_s = [o["iterations"] for o in seq[-1]]
+        worst = max(i["true_rnorm"] / i["bnorm"] for i in infos)
+        diff = max(float(torch.linalg.norm(X[:, j] - ys[j]) / torch.linalg.norm(ys[j])) for j in range(k))
+        out[f"cg_{name}"] = {"block_ms": round(t_blk, 3), "sequential_ms": round(t_seq, 3),
+                             "speedup": round(t_seq / t_blk, 2), "iterations_block": its_b,
+                             "iterations_sequential": its_s, "max_true_residual_rel": worst,
+                             "max_solution_rel_diff_block_vs_single": diff}
+    B.bamg_mg_destroy(mg32)
+    return out
 
 
 def compare_mixed(args, torch, B, x64=None):

@@ -256,12 +256,40 @@ BAMG_API bamg_status bamg_vcycle(bamg_mg* mg, const double* b, double* x);
  * p^T A p <= 0. */
 BAMG_API bamg_status bamg_cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit,
                           bamg_cg_info* info);
+/* Many right-hand sides at once (blocked SpMM form of the cycle and of CG).
+ * B and X are device FP64 arrays of k fine vectors stored RHS-minor: entry
+ * (dof d, vector j) at B[d * k + j], 1 <= k <= 32.  Internally the columns are
+ * padded to a power of two >= 4; the work arrays (about 6 fine vectors per
+ * column plus each level's cycle vectors) are allocated on the first call
+ * for a column count and kept with the hierarchy.
+ *
+ * bamg_mg_vcycle_multi: X = M B, one V-cycle per column from x = 0.  Per
+ * column the arithmetic and its order are those of bamg_vcycle with one lane
+ * per block row on every operator (bamg_bsr_set_lanes(.., 1)), so the
+ * results then agree bit for bit; with other lane counts they differ only by
+ * summation order.
+ *
+ * bamg_cg_solve_multi: k independent preconditioned CG recurrences (the
+ * iterates of bamg_cg_solve on each column, up to the summation order of the
+ * dot products) that share every pass over the operators: own step lengths,
+ * stopping test ||b_j - A x_j|| <= rtol ||b_j|| and iteration count per
+ * column; a column that stops is frozen while the others continue.  info
+ * (host, k entries, may be NULL) receives each column's result.  Returns
+ * BAMG_ERR_BREAKDOWN or BAMG_ERR_NOT_CONVERGED if any column did so (the
+ * message names the first). */
+BAMG_API bamg_status bamg_mg_vcycle_multi(bamg_mg* mg, const double* B, double* X, int k);
+BAMG_API bamg_status bamg_cg_solve_multi(bamg_mg* mg, const double* B, double* X, int k, double rtol, int maxit,
+                                         bamg_cg_info* info);
 /* Per-block-row smoother weights of a level (device float array of the
  * level's block-row count, borrowed) scaling each row of the Chebyshev
  * update, i.e. the smoother is preconditioned by W D^-1; w = NULL restores
  * the plain smoother.  The eigen-estimate of W D^-1 A is refreshed by the
  * next bamg_mg_update. */
 BAMG_API bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w);
+/* Lanes per block row (power of two, 1..32) for every operator of the
+ * hierarchy (A, P and R = P^T of each level, both precisions), replacing the
+ * autotuner's choices; results then no longer depend on timing. */
+BAMG_API bamg_status bamg_mg_set_lanes(bamg_mg* mg, int lanes);
 /* Inspection: number of levels; a level's operator and prolongator (P is
  * NULL on the coarsest level); its eigen-estimate and prolongator damping
  * factor; its block-diagonal inverse (device, nbr row-major bs x bs blocks). */

@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libbamg.so")
 BAMG_OK = 0
 STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG_ERR_CUDA", 4: "BAMG_ERR_STATE",
                 5: "BAMG_ERR_NAN", 6: "BAMG_ERR_BREAKDOWN", 7: "BAMG_ERR_NOT_CONVERGED", 8: "BAMG_ERR_TIMEOUT"}
+(BAMG_ERR_INVALID, BAMG_ERR_OOM, BAMG_ERR_CUDA, BAMG_ERR_STATE, BAMG_ERR_NAN, BAMG_ERR_BREAKDOWN,
+ BAMG_ERR_NOT_CONVERGED, BAMG_ERR_TIMEOUT) = range(1, 9)
 BAMG_FP64 = 0
 BAMG_FP32 = 1
 PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
@@ -77,7 +79,10 @@ _SIGS = {
     "bamg_mg_resetup": [_P],
     "bamg_vcycle": [_P, _P, _P],
     "bamg_cg_solve": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
+    "bamg_mg_vcycle_multi": [_P, _P, _P, ctypes.c_int],
+    "bamg_cg_solve_multi": [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
     "bamg_mg_set_smoother_weights": [_P, ctypes.c_int, _P],
+    "bamg_mg_set_lanes": [_P, ctypes.c_int],
     "bamg_mg_num_levels": [_P, ctypes.POINTER(ctypes.c_int)],
     "bamg_mg_get_level": [_P, ctypes.c_int, _PP, _PP],
     "bamg_mg_get_level_scalars": [_P, ctypes.c_int, _P, _P],
@@ -300,8 +305,28 @@ def bamg_cg_solve(ctx, mg, b, x, rtol: float, maxit: int, check: bool = True) ->
     return out
 
 
+def bamg_mg_vcycle_multi(ctx, mg, B, X, k: int):
+    """X = M B for k fine vectors stored RHS-minor (B[d * k + j])."""
+    _check(lib().bamg_mg_vcycle_multi(mg, _ptr(B), _ptr(X), int(k)), ctx)
+
+
+def bamg_cg_solve_multi(ctx, mg, B, X, k: int, rtol: float, maxit: int, check: bool = True) -> list:
+    """k simultaneous PCG solves; returns one info dict per column."""
+    info = (bamg_cg_info * max(1, int(k)))()
+    st = lib().bamg_cg_solve_multi(mg, _ptr(B), _ptr(X), int(k), float(rtol), int(maxit), info)
+    out = [{"status": st, "iterations": i.iterations, "converged": bool(i.converged), "rnorm": i.rnorm,
+            "bnorm": i.bnorm, "true_rnorm": i.true_rnorm} for i in info[:int(k)]]
+    if check:
+        _check(st, ctx)
+    return out
+
+
 def bamg_mg_set_smoother_weights(ctx, mg, level: int, w):
     _check(lib().bamg_mg_set_smoother_weights(mg, int(level), _ptr(w)), ctx)
+
+
+def bamg_mg_set_lanes(ctx, mg, lanes: int):
+    _check(lib().bamg_mg_set_lanes(mg, int(lanes)), ctx)
 
 
 def bamg_mg_num_levels(mg) -> int:

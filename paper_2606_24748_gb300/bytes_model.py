@@ -39,6 +39,11 @@ def spmv_flops(nnzb: int, bs_r: int, bs_c: int) -> int:
     return 2 * nnzb * bs_r * bs_c
 
 
+def spmm_bytes(nnzb: int, nbr: int, nbc: int, bs_r: int, bs_c: int, k: int, s: int = 8) -> int:
+    """Y = A X for k vectors: the matrix once, X once, Y written once."""
+    return matrix_bytes(nnzb, nbr, bs_r, bs_c, s) + s * k * (bs_c * nbc + bs_r * nbr)
+
+
 def ptap_bytes(A: dict, P: dict, Ac: dict, s: int = 8) -> int:
     """A_c = P^T A P: A and P read once (values, indices, row pointers), A_c values written."""
     return (matrix_bytes(A["nnzb"], A["nbr"], A["bs_r"], A["bs_c"], s)

@@ -135,6 +135,117 @@ __device__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials,
   return true;
 }
 
+// Four consecutive values (the right-hand sides one thread of a multi-vector
+// kernel owns); p must be aligned to 4 elements.  ld4 reads through the
+// read-only path (arrays the kernel does not write), ld4w plainly.
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4w(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4w(const float* p, float (&v)[4]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// Block-row product for four right-hand sides at once: X holds kp vectors
+// RHS-minor (entry (dof d, vector j) at X[d * kp + j]) and the thread takes
+// vectors c0..c0+3 of block row `row`.  Each block value is loaded once and
+// used for the four vectors; the kp / 4 threads of a row read the same value
+// (one broadcast).  Per vector, the summation order is that of row_product
+// with one lane per row.
+template <int BR, int BC, typename T>
+__device__ __forceinline__ void row_product4(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                             const T* __restrict__ vals, const T* __restrict__ X, int kp,
+                                             int64_t row, int c0, T (&acc)[BR][4]) {
+  const int64_t s = row >> 5;
+  const int lane = (int)(row & 31);
+  const int a0 = __ldg(slice_ptr + s), a1 = __ldg(slice_ptr + s + 1);
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[r][e] = T(0);
+  for (int c = a0; c < a1; ++c) {
+    const int j = __ldg(col + (int64_t)c * 32 + lane);
+    const T* v = vals + (int64_t)c * (32 * BR * BC) + lane;
+    T xv[BC][4];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) ld4(X + ((int64_t)j * BC + q) * kp + c0, xv[q]);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) {
+        const T a = __ldg(v + 32 * (r * BC + q));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[r][e] = fma(a, xv[q][e], acc[r][e]);
+      }
+  }
+}
+
+// Deterministic grid reduction of ns = G * NV sums at once: thread t adds
+// v[e] to sum (t mod G) * NV + e.  G is a power of two <= 32, ns <= 64 and
+// blockDim.x = 256 (a multiple of ns); the grid-stride loops that feed it keep
+// a thread on one residue mod G.  Fixed shuffle trees inside each warp, warps
+// summed in order, per-CTA partials summed by the last CTA to arrive (atomic
+// ticket) in a fixed order.  Returns true in the last CTA, where out_sm
+// (shared, ns doubles) then holds the sums for every thread of the CTA.
+template <int NV>
+__device__ bool grid_reduce_groups(const double (&v)[NV], int G, double* __restrict__ partials,
+                                   unsigned* __restrict__ counter, double* out_sm) {
+  __shared__ double sm[512];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ns = G * NV;
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    double x = v[e];
+    for (int o = 16; o >= G; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane < G) sm[warp * ns + lane * NV + e] = x;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < ns) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += sm[w * ns + threadIdx.x];
+    partials[(int64_t)blockIdx.x * ns + threadIdx.x] = a;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const int step = blockDim.x / ns;
+  double a = 0.0;
+  for (int b = threadIdx.x / ns; b < (int)gridDim.x; b += step)
+    a += __ldcg(partials + (int64_t)b * ns + threadIdx.x % ns);
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  if ((int)threadIdx.x < ns) {
+    double t = 0.0;
+    for (int k = 0; k < step; ++k) t += sm[k * ns + threadIdx.x];
+    out_sm[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
 __device__ __forceinline__ void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }

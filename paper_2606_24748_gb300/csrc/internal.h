@@ -200,6 +200,39 @@ struct CgState {
   int its, maxit, done, converged, breakdown, pad2[3];
 };
 
+// Many right-hand sides at once: at most kMaxRhs vectors, stored RHS-minor
+// and padded to kp = a power of two >= 4 columns.
+constexpr int kMaxRhs = 32;
+
+// Per-column state of k simultaneous PCG recurrences.
+struct CgMultiState {
+  double bnorm2[kMaxRhs], rnorm2[kMaxRhs], rz[kMaxRhs], alpha[kMaxRhs], beta[kMaxRhs], pq[kMaxRhs];
+  double true_r2[kMaxRhs];
+  double rtol2;
+  int its[kMaxRhs], done[kMaxRhs], converged[kMaxRhs], breakdown[kMaxRhs];
+  int maxit, k, kp, all_done;
+};
+
+// Work area of the multi-right-hand-side V-cycle and CG (allocated on first
+// use for a column count, grown on demand).
+struct MultiLevel {
+  void *b = nullptr, *x = nullptr, *r = nullptr, *d0 = nullptr, *d1 = nullptr;
+};
+struct MultiWork {
+  int kp = 0;
+  std::vector<MultiLevel> lv;
+  double* coarse_y = nullptr;  // npad x kp, FP64
+  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *czold = nullptr;
+  bool own_rz = false;         // cr / cz allocated (mixed form) or aliased to level 0 (FP64)
+  CgMultiState* st = nullptr;
+  CgMultiState* host = nullptr;  // pinned
+  double* partials = nullptr;    // grid x 64
+  unsigned* counters = nullptr;  // 8
+  cudaGraphExec_t graph = nullptr;  // one CG iteration for graph_kp columns
+  uint64_t graph_kernels = 0;
+  int graph_kp = 0;
+};
+
 }  // namespace bamg
 
 struct bamg_mlp;
@@ -222,6 +255,7 @@ struct bamg_mg {
   uint64_t cg_graph_epoch = ~0ull;
   uint64_t cg_graph_kernels = 0;
   double* power_w[2] = {nullptr, nullptr};
+  bamg::MultiWork* multi = nullptr;  // multi-right-hand-side work area
 };
 
 namespace bamg {
@@ -307,6 +341,7 @@ template <typename T>
 Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
 void mg_release_graphs(bamg_mg* mg);
+void mg_release_multi(bamg_mg* mg);               // multi-right-hand-side work area
 Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st);  // features -> MLP -> level weights
 Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st);  // FP64 pre-smoothing of level l (b -> x, r)
 Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st);     // levels[l+1].b = R_l r_l

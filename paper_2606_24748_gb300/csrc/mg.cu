@@ -485,6 +485,7 @@ static Status alloc_vectors(bamg_mg* mg) {
 static void mg_release(bamg_mg* mg) {
   cudaStream_t st = mg->ctx->stream;
   mg_release_graphs(mg);
+  mg_release_multi(mg);
   for (auto& L : mg->levels) {
     if (L.plan) {
       ptap_release(L.plan);
@@ -790,6 +791,17 @@ bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w)
   if (!mg || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
   mg->levels[level].weights = const_cast<float*>(w);
   mg_release_graphs(mg);  // the captured iteration holds the old pointer
+  return BAMG_OK;
+}
+
+bamg_status bamg_mg_set_lanes(bamg_mg* mg, int lanes) {
+  if (!mg) return BAMG_ERR_INVALID;
+  if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
+    return fail(mg->ctx, make_status(BAMG_ERR_INVALID, "lanes must be a power of two in [1, 32]"));
+  for (auto& L : mg->levels)
+    for (bamg_bsr* M : {L.A, L.P, L.R})
+      if (M) M->vec = M->vec32 = lanes;
+  mg_release_graphs(mg);  // captured iterations hold the old launch shapes
   return BAMG_OK;
 }
 

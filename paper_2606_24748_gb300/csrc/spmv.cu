@@ -89,6 +89,24 @@ __global__ void __launch_bounds__(256) k_spmm(const int* __restrict__ slice_ptr,
   for (int r = 0; r < BR; ++r) Y[(row * BR + r) * k + j] = acc[r];
 }
 
+// The same product with four right-hand sides per thread (k a multiple of 4,
+// X and Y aligned to four elements): each block value is loaded once for four
+// vectors.
+template <int BR, int BC, typename T>
+__global__ void __launch_bounds__(256) k_spmm4(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                               const T* __restrict__ vals, const T* __restrict__ X,
+                                               T* __restrict__ Y, int64_t nbr, int k) {
+  const int G = k >> 2;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = t / G;
+  if (row >= nbr) return;
+  const int c0 = (int)(t - row * G) * 4;
+  T acc[BR][4];
+  row_product4<BR, BC, T>(slice_ptr, col, vals, X, k, row, c0, acc);
+#pragma unroll
+  for (int r = 0; r < BR; ++r) st4(Y + (row * BR + r) * k + c0, acc[r]);
+}
+
 template <typename T>
 static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* x, T* y, cudaStream_t st) {
   const int64_t nt = A->nslices * kSlice * (int64_t)vec;
@@ -201,10 +219,14 @@ template <typename T>
 Status launch_spmm(const bamg_bsr* A, const T* vals, const T* X, T* Y, int k, cudaStream_t st) {
   const int64_t nt = A->nbr * (int64_t)k;
   if (nt == 0) return Status{};
-  const unsigned blocks = (unsigned)((nt + 255) / 256);
+  const bool four = k % 4 == 0 && ((uintptr_t)X % (4 * sizeof(T))) == 0 && ((uintptr_t)Y % (4 * sizeof(T))) == 0;
+  const unsigned blocks = (unsigned)(((four ? nt / 4 : nt) + 255) / 256);
 #define BAMG_SPMM_CASE(R, C)                                                                   \
   if (A->br == R && A->bc == C) {                                                              \
-    { k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
+    if (four)                                                                                  \
+      { k_spmm4<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
+    else                                                                                       \
+      { k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
     BAMG_CUDA(cudaGetLastError());                                                             \
     return Status{};                                                                           \
   }
