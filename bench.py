@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-multi", action="store_true", help="skip the 16-right-hand-side measurement")
+    p.add_argument("--no-batch", action="store_true", help="skip the 32-problem batch measurement")
+    p.add_argument("--only", default="", choices=["", "multi", "batch"],
+                   help="run only that measurement (its own JSON object; used for profiling)")
     return p.parse_args()
 
 
@@ -287,6 +290,8 @@ def run_ours(args):
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
     if not args.no_multi and args.precision == "fp64" and rank == 0 and world == 1:
         result["multi_rhs"] = multi_rhs(wl, torch, B)
+    if not args.no_batch and rank == 0 and world == 1:
+        result["batch"] = batch_solve(torch, B)
     if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
         out0 = wl.step(0)
         x64 = wl.x.clone()
@@ -485,6 +490,66 @@ def multi_rhs(wl, torch, B, k=16):
     return out
 
 
+def batch_solve(torch, B, seed=7, count=32):
+    """A batch of uneven problems (elements per direction U{16..40}, Poisson
+    ratio U[0.2, 0.45], each with its own hierarchy and context, unit body
+    force): one graph launch solving all of them to rtol 1e-8 (branch count
+    autotuned) against the same solves one after another."""
+    from workloads.elasticity import batch_problems
+    probs = []
+    for ne, nu in batch_problems(seed, count):
+        m = Mesh(ne)
+        ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+        bi, bj = coo_indices(m, "cuda")
+        A = B.bamg_bsr_create(ctx, 3, 3, m.n_nodes, m.n_nodes)
+        B.bamg_bsr_coo_preallocate(ctx, A, bi, bj)
+        B.bamg_bsr_coo_set_values(ctx, A, coo_values(m, nu, element_scale(m), "cuda"), 0)
+        o = B.bamg_mg_opts_default()
+        o.grid[0] = o.grid[1] = o.grid[2] = m.m
+        mg = B.bamg_mg_setup(ctx, A, m.coords(), m.dirichlet(), o)
+        b = torch.from_numpy(body_force(m)).cuda()
+        probs.append({"ne": ne, "nu": nu, "ctx": ctx, "A": A, "mg": mg, "b": b, "x": torch.zeros_like(b),
+                      "levels": level_sizes(B, mg), "n_coo": int(bi.numel())})
+    lctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    bt = B.bamg_batch_create(lctx, [p["mg"] for p in probs])
+    bs, xs = [p["b"] for p in probs], [p["x"] for p in probs]
+    tune_ms = B.bamg_batch_autotune(lctx, bt, bs, xs, RTOL, MAXIT)
+    res = {}
+    B.bamg_batch_cg_solve(lctx, bt, bs, xs, RTOL, MAXIT)
+    l0 = B.bamg_kernel_launches()
+    t_batch = event_ms(torch, lambda: res.__setitem__("r", B.bamg_batch_cg_solve(lctx, bt, bs, xs, RTOL, MAXIT)), 3)
+    kernels = (B.bamg_kernel_launches() - l0) // 3
+    infos, loops = res["r"]
+    seq = []
+    for p in probs:
+        B.bamg_cg_solve(p["ctx"], p["mg"], p["b"], p["x"], RTOL, MAXIT)
+    t_seq = event_ms(torch, lambda: seq.append([B.bamg_cg_solve(p["ctx"], p["mg"], p["b"], p["x"], RTOL, MAXIT)
+                                                for p in probs]), 3)
+    its = [i["iterations"] for i in infos]
+    same = all(i["iterations"] == o["iterations"] for i, o in zip(infos, seq[-1]))
+    nbytes = 0
+    for p, it in zip(probs, its):
+        _, parts, _ = step_bytes(p["levels"], p["n_coo"], it + 1, it, False)
+        nbytes += parts["vcycles"] + parts["cg"]
+    out = {"problems": count, "seed": seed,
+           "dofs_total": int(sum(p["b"].numel() for p in probs)),
+           "levels": [len(p["levels"]) for p in probs],
+           "branches": B.bamg_batch_get_branches(bt), "autotune_best_ms": round(tune_ms, 3),
+           "batch_ms": round(t_batch, 3), "sequential_ms": round(t_seq, 3),
+           "speedup": round(t_seq / t_batch, 2),
+           "gbs_batch": round(nbytes / t_batch / 1e6, 1), "gbs_sequential": round(nbytes / t_seq / 1e6, 1),
+           "graph_launches_per_solve": 1, "loop_iterations": loops, "kernels_per_solve": int(kernels),
+           "iterations": its, "iterations_equal_sequential": same,
+           "max_true_residual_rel": max(i["true_rnorm"] / i["bnorm"] for i in infos)}
+    B.bamg_batch_destroy(bt)
+    B.bamg_ctx_destroy(lctx)
+    for p in probs:
+        B.bamg_mg_destroy(p["mg"])
+        B.bamg_bsr_destroy(p["A"])
+        B.bamg_ctx_destroy(p["ctx"])
+    return out
+
+
 def compare_mixed(args, torch, B, x64=None):
     """Time to rtol 1e-8 of the mixed-precision form on the same workload, and
     its solution against the FP64 form's for the same input."""
@@ -574,8 +639,26 @@ def run_reference(args):
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_only(args):
+    """One of the extra measurements on its own (for profiling runs)."""
+    import torch
+    from paper_2606_24748_gb300 import bamg as B
+    if not os.path.exists(B.LIB_PATH):
+        from paper_2606_24748_gb300.build import build
+        build()
+    if args.only == "batch":
+        return {"only": "batch", "batch": batch_solve(torch, B)}
+    wl = Workload(B, torch, args.ne, 0.3, "fp64", n_inputs=1)
+    out = {"only": "multi", "multi_rhs": multi_rhs(wl, torch, B)}
+    wl.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.only and args.impl == "ours":
+        print(json.dumps(run_only(args)), flush=True)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

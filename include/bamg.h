@@ -300,6 +300,42 @@ BAMG_API bamg_status bamg_mg_get_level_scalars(const bamg_mg* mg, int level, dou
 BAMG_API bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* dinv);
 BAMG_API bamg_status bamg_mg_destroy(bamg_mg* mg);
 
+/* ------------------------------------------------- batch of problems */
+
+/* A batch of independent problems, each with its own hierarchy, solved by
+ * PCG in one graph launch (not in the paper: a serving-style extension).
+ * The graph runs every problem's solve start, then a device-controlled
+ * while loop whose body is one CG iteration of every problem still running
+ * (a kernel at the end of each iteration sets the loop condition, bounded
+ * at maxit iterations), then every problem's x and true residual; no
+ * host round trip happens inside a solve.  Problems run as concurrent
+ * branches of the graph, dealt largest-first to n_branches branches.  Each
+ * problem executes exactly the kernels of bamg_cg_solve, so its result and
+ * iteration count are those of a standalone solve.
+ *
+ * bamg_batch_create: mgs (host array of n hierarchies, borrowed; each set up
+ * and updated) must each have their own context, since a context's
+ * reduction buffers serve one solve at a time (BAMG_ERR_INVALID otherwise).
+ * The batch launches on ctx's stream.  Branches default to n.
+ * bamg_batch_cg_solve: b and x are host arrays of n device pointers (FP64
+ * fine vectors; x entries may be NULL, x itself may be NULL).  The graph is
+ * built on the first call and rebuilt when the pointers, rtol or maxit
+ * change.  info (host, n entries, may be NULL), loops (may be NULL): loop
+ * iterations run.  Returns BAMG_ERR_BREAKDOWN / BAMG_ERR_NOT_CONVERGED if
+ * any problem did so (the message names the first).
+ * bamg_batch_autotune: times one solve with 1, 2, 4, ... n branches (median
+ * of three after a warm-up) and keeps the fastest; *best_ms (may be NULL)
+ * receives its time.  Runs solves, so it overwrites the x vectors. */
+typedef struct bamg_batch bamg_batch;
+BAMG_API bamg_status bamg_batch_create(bamg_ctx* ctx, int n, bamg_mg* const* mgs, bamg_batch** out);
+BAMG_API bamg_status bamg_batch_destroy(bamg_batch* bt);
+BAMG_API bamg_status bamg_batch_set_branches(bamg_batch* bt, int n_branches);
+BAMG_API bamg_status bamg_batch_get_branches(const bamg_batch* bt, int* n_branches);
+BAMG_API bamg_status bamg_batch_cg_solve(bamg_batch* bt, const double* const* b, double* const* x, double rtol,
+                                         int maxit, bamg_cg_info* info, int* loops);
+BAMG_API bamg_status bamg_batch_autotune(bamg_batch* bt, const double* const* b, double* const* x, double rtol,
+                                         int maxit, float* best_ms);
+
 /* --------------------------------------------- learned smoother weights */
 
 /* Per-block-row smoother weights predicted by a small MLP (not in the paper;

@@ -81,6 +81,13 @@ _SIGS = {
     "bamg_cg_solve": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
     "bamg_mg_vcycle_multi": [_P, _P, _P, ctypes.c_int],
     "bamg_cg_solve_multi": [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info)],
+    "bamg_batch_create": [_P, ctypes.c_int, _P, _PP],
+    "bamg_batch_destroy": [_P],
+    "bamg_batch_set_branches": [_P, ctypes.c_int],
+    "bamg_batch_get_branches": [_P, ctypes.POINTER(ctypes.c_int)],
+    "bamg_batch_cg_solve": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(bamg_cg_info),
+                            ctypes.POINTER(ctypes.c_int)],
+    "bamg_batch_autotune": [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "bamg_mg_set_smoother_weights": [_P, ctypes.c_int, _P],
     "bamg_mg_set_lanes": [_P, ctypes.c_int],
     "bamg_mg_num_levels": [_P, ctypes.POINTER(ctypes.c_int)],
@@ -319,6 +326,52 @@ def bamg_cg_solve_multi(ctx, mg, B, X, k: int, rtol: float, maxit: int, check: b
     if check:
         _check(st, ctx)
     return out
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[(_ptr(t) if t is not None else None) for t in ts])
+
+
+def bamg_batch_create(ctx, mgs):
+    arr = (ctypes.c_void_p * len(mgs))(*mgs)
+    out = ctypes.c_void_p()
+    _check(lib().bamg_batch_create(ctx, len(mgs), arr, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def bamg_batch_destroy(bt):
+    lib().bamg_batch_destroy(bt)
+
+
+def bamg_batch_set_branches(ctx, bt, n: int):
+    _check(lib().bamg_batch_set_branches(bt, int(n)), ctx)
+
+
+def bamg_batch_get_branches(bt) -> int:
+    n = ctypes.c_int()
+    _check(lib().bamg_batch_get_branches(bt, ctypes.byref(n)), None)
+    return n.value
+
+
+def bamg_batch_cg_solve(ctx, bt, bs, xs, rtol: float, maxit: int, check: bool = True):
+    """One graph launch solving every problem; returns (infos, loop iterations)."""
+    n = len(bs)
+    info = (bamg_cg_info * n)()
+    loops = ctypes.c_int()
+    st = lib().bamg_batch_cg_solve(bt, _ptr_array(bs), _ptr_array(xs) if xs is not None else None,
+                                   float(rtol), int(maxit), info, ctypes.byref(loops))
+    out = [{"status": st, "iterations": i.iterations, "converged": bool(i.converged), "rnorm": i.rnorm,
+            "bnorm": i.bnorm, "true_rnorm": i.true_rnorm} for i in info]
+    if check:
+        _check(st, ctx)
+    return out, loops.value
+
+
+def bamg_batch_autotune(ctx, bt, bs, xs, rtol: float, maxit: int) -> float:
+    ms = ctypes.c_float()
+    _check(lib().bamg_batch_autotune(bt, _ptr_array(bs), _ptr_array(xs), float(rtol), int(maxit), ctypes.byref(ms)),
+           ctx)
+    return ms.value
 
 
 def bamg_mg_set_smoother_weights(ctx, mg, level: int, w):

@@ -577,21 +577,45 @@ static Status cg_graph(bamg_mg* mg, double* r, double* z) {
 
 void mg_release_graphs(bamg_mg* mg) { cg_graphs_release(mg); }
 
-static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit, bamg_cg_info* info) {
+// CG work vectors r and z: in the FP64 form the cycle reads its right-hand
+// side and writes its result in place (level 0's b and x).
+static double* cg_r(bamg_mg* mg) { return mg->opts.precision == BAMG_FP64 ? mg->levels[0].b : mg->cr; }
+static double* cg_z(bamg_mg* mg) { return mg->opts.precision == BAMG_FP64 ? mg->levels[0].x : mg->cz; }
+
+Status cg_prologue(bamg_mg* mg, const double* b, double rtol, int maxit, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
-  cudaStream_t st = ctx->stream;
-  Level& L0 = mg->levels[0];
-  const int64_t m = L0.n * 3;
-  const bool f64 = mg->opts.precision == BAMG_FP64;
-  double* r = f64 ? L0.b : mg->cr;  // the cycle reads its right-hand side in place
-  double* z = f64 ? L0.x : mg->cz;
+  const int64_t m = mg->levels[0].n * 3;
+  double *r = cg_r(mg), *z = cg_z(mg);
   CgState* s = mg->cg;
-  BAMG_TRY(cg_graph(mg, r, z));
   { k_cg_setup<<<1, 1, 0, st>>>(s, rtol, maxit); BAMG_COUNT_LAUNCH; }
   { k_cg_init<<<vec_grid(m), 256, 0, st>>>(m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5); BAMG_COUNT_LAUNCH; }
   BAMG_TRY(precond(mg, r, z, &s->done, st));
   { k_cg_first<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+Status cg_step(bamg_mg* mg, cudaStream_t st) { return cg_iteration(mg, cg_r(mg), cg_z(mg), st); }
+
+Status cg_epilogue(bamg_mg* mg, const double* b, double* x, double* true_r2, cudaStream_t st) {
+  bamg_ctx* ctx = mg->ctx;
+  Level& L0 = mg->levels[0];
+  const int64_t m = L0.n * 3;
+  if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  const bamg_bsr* A = L0.A;
+  const int64_t rows = row_threads(A);
+  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+                                                          true_r2, ctx->d_partials, ctx->d_counters + 7); BAMG_COUNT_LAUNCH; })
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int maxit, bamg_cg_info* info) {
+  bamg_ctx* ctx = mg->ctx;
+  cudaStream_t st = ctx->stream;
+  CgState* s = mg->cg;
+  BAMG_TRY(cg_graph(mg, cg_r(mg), cg_z(mg)));
+  BAMG_TRY(cg_prologue(mg, b, rtol, maxit, st));
   BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaStreamSynchronize(st));
   int launched = 0;
@@ -614,12 +638,8 @@ static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int
       its_before = its_now;
     }
   }
-  if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-  const bamg_bsr* A = L0.A;
-  const int64_t rows = row_threads(A);
   double* tr = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel + 8;
-  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
-                                                          tr, ctx->d_partials, ctx->d_counters + 7); BAMG_COUNT_LAUNCH; })
+  BAMG_TRY(cg_epilogue(mg, b, x, tr, st));
   double tr2 = 0.0;
   BAMG_CUDA(cudaMemcpyAsync(&tr2, tr, sizeof(double), cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
