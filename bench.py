@@ -167,6 +167,28 @@ def step_bytes(levels, n_coo, precond_applications, cg_its, mixed, power_its=15)
     return sum(parts.values()), parts, vc
 
 
+def level_count(ne, max_coarse_dofs=2100):
+    """Levels of the hierarchy: coarsen (3x3x3 node aggregates) while a level has more dofs."""
+    m, bs, n = ne + 1, 3, 1
+    while bs * m ** 3 > max_coarse_dofs:
+        m, bs, n = max(1, m // 3), 6, n + 1
+    return n
+
+
+def workload_config(ne, precision, world):
+    mesh = Mesh(ne)
+    nl = level_count(ne)
+    n_coo = 64 * ne ** 3 + (ne + 1) ** 2
+    nnzb = (3 * ne + 1) ** 3          # 27-point node adjacency: (3m - 2)^3 blocks, m = ne + 1
+    return {"workload": f"elasticity {ne}^3 Q1 elements, {mesh.n_dofs} dofs, {nl}-level SA-AMG, reuse step "
+                        f"(COO re-assembly, PtAP all levels, smoother refresh, PCG V(2,2) Chebyshev to rtol 1e-8), "
+                        f"{'mixed FP32/FP64' if precision == 'mixed' else 'FP64'}",
+            "elements": ne, "dofs": mesh.n_dofs, "levels": nl, "precision": precision,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (value stream %.2f GB, fine operator %.2f GB)" % (
+                n_coo * 72 / 1e9, nnzb * 76 / 1e9)}
+
+
 # ---------------------------------------------------------------- our arm
 class Workload:
     def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000):
@@ -269,14 +291,7 @@ def run_ours(args):
         "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if wl.mixed else "f64",
         "data": "synthetic: seeded Q1 elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
-        "config": {"workload": f"elasticity {args.ne}^3 Q1 elements, {wl.mesh.n_dofs} dofs, "
-                               f"{len(wl.levels)}-level SA-AMG, reuse step (COO re-assembly, PtAP all levels, "
-                               f"smoother refresh, PCG V(2,2) Chebyshev to rtol 1e-8), "
-                               f"{'mixed FP32/FP64' if wl.mixed else 'FP64'}",
-                   "elements": args.ne, "dofs": wl.mesh.n_dofs, "levels": len(wl.levels),
-                   "precision": args.precision, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (value stream %.2f GB, fine operator %.2f GB)" % (
-                       wl.n_coo * 72 / 1e9, wl.levels[0]["A"]["nnzb"] * 76 / 1e9)},
+        "config": workload_config(args.ne, args.precision, world),
         "cg_iterations": its, "bytes_per_step": int(bytes_step),
         "bytes_parts": {k: int(v) for k, v in parts.items()},
         "gpu_launches": int(launches),
@@ -574,68 +589,88 @@ def compare_mixed(args, torch, B, x64=None):
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
-def oracle_step_sample(ne=24, seed=1):
-    """One reuse step of the oracle on a smaller mesh of the same problem."""
-    from oracle import krylov
-    from oracle import multigrid as omg
-    from oracle.assembly import coo_assemble_blocks
-    m = Mesh(ne)
-    bi, bj = coo_indices(m)
-    bi, bj = bi.numpy(), bj.numpy()
-    v0 = coo_values(m, 0.3, element_scale(m)).numpy()
-    h = omg.setup(coo_assemble_blocks(m.n_nodes, m.n_nodes, 3, 3, bi, bj, v0), m.coords(), m.dirichlet(), m.grid)
-    v = coo_values(m, 0.3, element_scale(m, delta=perturbation(m.n_el, seed))).numpy()
-    b = body_force(m)
-    t0 = time.perf_counter()
-    A = coo_assemble_blocks(m.n_nodes, m.n_nodes, 3, 3, bi, bj, v)
-    h2 = omg.update(h, A)
-    x, its, info = krylov.pcg(h2.levels[0].As, b, lambda r: omg.vcycle(h2, r), RTOL, MAXIT)
-    dt = time.perf_counter() - t0
+def oracle_levels(h2):
     levels = []
-    for l, L in enumerate(h2.levels):
+    for L in h2.levels:
         a = {"nnzb": L.A.nnzb, "nbr": L.A.nbr, "nbc": L.A.nbc, "bs_r": L.A.bs_r, "bs_c": L.A.bs_c}
         p = r = None
         if L.P is not None:
             p = {"nnzb": L.P.nnzb, "nbr": L.P.nbr, "nbc": L.P.nbc, "bs_r": L.P.bs_r, "bs_c": L.P.bs_c}
             r = {"nnzb": L.P.nnzb, "nbr": L.P.nbc, "nbc": L.P.nbr, "bs_r": L.P.bs_c, "bs_c": L.P.bs_r}
         levels.append({"A": a, "P": p, "R": r})
-    nbytes = step_bytes(levels, int(bi.size), its + 1, its, False)[0]
-    return dt, nbytes, its
+    return levels
 
 
-def cpu_baseline(samples=1, ne=24):
+class OracleSample:
+    """The oracle's reuse step on a smaller mesh of the same problem: cold
+    setup once (untimed), then per step COO assembly of a perturbed operator,
+    the Galerkin products on every level, the smoother refresh and PCG."""
+
+    def __init__(self, ne):
+        from oracle import multigrid as omg
+        from oracle.assembly import coo_assemble_blocks
+        self.omg, self.coo = omg, coo_assemble_blocks
+        self.m = m = Mesh(ne)
+        bi, bj = coo_indices(m)
+        self.bi, self.bj = bi.numpy(), bj.numpy()
+        v0 = coo_values(m, 0.3, element_scale(m)).numpy()
+        self.h = omg.setup(coo_assemble_blocks(m.n_nodes, m.n_nodes, 3, 3, self.bi, self.bj, v0),
+                           m.coords(), m.dirichlet(), m.grid)
+        self.b = body_force(m)
+
+    def step(self, seed):
+        """Returns (seconds, algorithmic bytes, iterations)."""
+        from oracle import krylov
+        m, omg = self.m, self.omg
+        v = coo_values(m, 0.3, element_scale(m, delta=perturbation(m.n_el, seed))).numpy()
+        t0 = time.perf_counter()
+        A = self.coo(m.n_nodes, m.n_nodes, 3, 3, self.bi, self.bj, v)
+        h2 = omg.update(self.h, A)
+        x, its, info = krylov.pcg(h2.levels[0].As, self.b, lambda r: omg.vcycle(h2, r), RTOL, MAXIT)
+        dt = time.perf_counter() - t0
+        nbytes = step_bytes(oracle_levels(h2), int(self.bi.size), its + 1, its, False)[0]
+        return dt, nbytes, its
+
+
+def cpu_baseline(steps=8, ne=24):
+    s = OracleSample(ne)
     tot_t, tot_b = 0.0, 0.0
-    for k in range(samples):
-        dt, nb, _ = oracle_step_sample(ne, seed=k + 1)
+    for k in range(steps):
+        dt, nb, _ = s.step(seed=k + 1)
         tot_t += dt
         tot_b += nb
     return {"value": round(tot_b / tot_t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{samples} oracle reuse step(s) (COO assembly, Galerkin products, smoother refresh, "
+            "sample": f"{steps} oracle reuse steps (COO assembly, Galerkin products, smoother refresh, "
                       f"PCG to 1e-8) of the same elasticity problem at {ne}^3 elements "
                       f"({3 * (ne + 1) ** 3} dofs), single-threaded scipy/numpy on the host",
             "seconds": round(tot_t, 2)}
 
 
 def run_reference(args):
+    """The oracle on the host cores (one thread), each step one reuse step of
+    the same problem on a 24^3-element sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     K, W = args.steps, args.warmup
-    ne = 16
+    ne = 24
+    sample = OracleSample(ne)
     for k in range(W):
-        oracle_step_sample(ne, seed=100 + k)
+        sample.step(seed=100 + k)
     tt, tb = 0.0, 0.0
     for k in range(K):
-        dt, nb, _ = oracle_step_sample(ne, seed=k + 1)
+        dt, nb, _ = sample.step(seed=k + 1)
         tt += dt
         tb += nb
     value = tb / tt / 1e9
+    desc = (f"oracle reuse step (COO assembly, Galerkin products, smoother refresh, PCG to 1e-8) per step "
+            f"on a {ne}^3-element sample ({3 * (ne + 1) ** 3} dofs) of the same problem, single-threaded")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": round(tt / K * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic: seeded Q1 elasticity", "config": {"workload": f"oracle sample: {ne}^3 elements"},
-            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "kind": "oracle", "cores": 1,
-                             "sample": f"oracle reuse step on {ne}^3 elements per step"},
+            "data": "synthetic: seeded Q1 elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
+            "config": workload_config(args.ne, args.precision, args.gpus),
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "kind": "oracle", "cores": 1, "sample": desc},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
