@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                   help="0: lanes per row from the size heuristic instead of timing (for runs under a profiler)")
     p.add_argument("--no-multi", action="store_true", help="skip the 16-right-hand-side measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the 32-problem batch measurement")
     p.add_argument("--only", default="", choices=["", "multi", "batch"],
@@ -191,7 +193,7 @@ def workload_config(ne, precision, world):
 
 # ---------------------------------------------------------------- our arm
 class Workload:
-    def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000):
+    def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000, autotune=1):
         self.B, self.torch = B, torch
         self.mesh = Mesh(ne)
         m = self.mesh
@@ -205,6 +207,7 @@ class Workload:
         o = B.bamg_mg_opts_default()
         o.grid[0] = o.grid[1] = o.grid[2] = m.m
         o.precision = B.BAMG_FP32 if precision == "mixed" else B.BAMG_FP64
+        o.autotune = autotune
         self.mg = B.bamg_mg_setup(self.ctx, self.A, m.coords(), m.dirichlet(), o)
         del v0
         # per-step inputs (perturbed operators), resident in HBM
@@ -262,7 +265,7 @@ def run_ours(args):
     K, W = args.steps, args.warmup
     stream_bytes = 72 * 64 * args.ne ** 3
     wl = Workload(B, torch, args.ne, 0.3, args.precision,
-                  n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))))
+                  n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))), autotune=args.autotune)
     for k in range(W):
         wl.step(k)
     clocks = Clocks(local)

@@ -144,12 +144,18 @@ BAMG_API bamg_status bamg_bsr_spmv(bamg_bsr* A, const void* x, void* y, bamg_pre
  * (1 <= k <= 32), right-hand-side-minor layout: X[dof * k + j]. */
 BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, bamg_prec prec);
 
-/* Lanes per block row used by this matrix's row kernels (a power of two in
- * 1..32): 1 = one row per lane (long matrices), more lanes for few, long rows
- * (restrictions, coarse levels).  _autotune times the FP64 product for every
- * width on the context's stream and keeps the fastest (allocates two work
- * vectors; returns the choice and its time in ms, either may be NULL).
- * Results do not depend on the choice beyond summation order. */
+/* Thread mapping of this matrix's row kernels ("lanes"): a power of two in
+ * 1..32 = lanes per block row (1 = one row per lane for long matrices, more
+ * lanes for few, long rows); or, for 6x3 and 6x6 blocks only, the component
+ * split: -VS = VS warps (1, 2 or 4) per output component of a 32-row slice,
+ * each taking every VS-th block of the rows (no cross-lane sums, no idle
+ * lanes; the FP64 pipe's two FMA per clock per SM make those count); 0 in
+ * _set_lanes means -4.  _autotune times the product for every choice from a
+ * flushed L2 on the context's stream and keeps the fastest, for the FP64
+ * values and, when present, the FP32 copy (allocates work vectors; returns
+ * the FP64 choice and its time in ms, either may be NULL).  Results do not
+ * depend on the choice beyond summation order.  _set_lanes applies to both
+ * copies. */
 BAMG_API bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms);
 BAMG_API bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes);
 BAMG_API bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes);
@@ -213,6 +219,11 @@ typedef struct {
                                eigen-estimates and coarsest solve) */
   int autotune;             /* 1 (default): bamg_bsr_autotune every level's
                                operator, prolongator and restriction at setup */
+  int coarse_solver;        /* coarsest-level exact solve: 0 (default) = banded
+                               block-tridiagonal Cholesky when the level's
+                               half-bandwidth splits it into >= 3 chunks, else
+                               dense; 1 = always dense; 2 = banded whenever
+                               it splits into >= 2 chunks */
 } bamg_mg_opts;
 
 typedef struct {
@@ -286,9 +297,11 @@ BAMG_API bamg_status bamg_cg_solve_multi(bamg_mg* mg, const double* B, double* X
  * the plain smoother.  The eigen-estimate of W D^-1 A is refreshed by the
  * next bamg_mg_update. */
 BAMG_API bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w);
-/* Lanes per block row (power of two, 1..32) for every operator of the
- * hierarchy (A, P and R = P^T of each level, both precisions), replacing the
- * autotuner's choices; results then no longer depend on timing. */
+/* Thread mapping for every operator of the hierarchy (A, P and R = P^T of
+ * each level, both precisions), replacing the autotuner's choices, so that
+ * results no longer depend on timing: lanes = a power of two in 1..32 lanes
+ * per block row, or 0 = component split for the 6x3 / 6x6-block operators
+ * and one lane per row for the others (see bamg_bsr_set_lanes). */
 BAMG_API bamg_status bamg_mg_set_lanes(bamg_mg* mg, int lanes);
 /* Inspection: number of levels; a level's operator and prolongator (P is
  * NULL on the coarsest level); its eigen-estimate and prolongator damping

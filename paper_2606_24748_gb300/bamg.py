@@ -39,7 +39,8 @@ class bamg_mg_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int), ("max_coarse_dofs", ctypes.c_int64),
                 ("grid", ctypes.c_int * 3), ("cheb_degree", ctypes.c_int),
                 ("cheb_lower", ctypes.c_double), ("cheb_upper", ctypes.c_double),
-                ("power_its", ctypes.c_int), ("precision", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("power_its", ctypes.c_int), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("coarse_solver", ctypes.c_int)]
 
 
 class bamg_cg_info(ctypes.Structure):

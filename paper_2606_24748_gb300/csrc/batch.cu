@@ -279,7 +279,7 @@ Status create(bamg_ctx* ctx, int n, bamg_mg* const* mgs, bamg_batch* bt) {
   for (int p = 0; p < n; ++p) {
     bamg_mg* mg = mgs[p];
     if (!mg) return make_status(BAMG_ERR_INVALID, "hierarchy %d is null", p);
-    if (mg->levels.empty() || mg->levels[0].bs != 3 || !mg->coarse.M)
+    if (mg->levels.empty() || mg->levels[0].bs != 3 || !mg->coarse.factored)
       return make_status(BAMG_ERR_STATE, "hierarchy %d is not set up", p);
     for (int q = 0; q < p; ++q)
       if (mgs[q] == mg || mgs[q]->ctx == mg->ctx)

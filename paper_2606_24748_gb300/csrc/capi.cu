@@ -406,21 +406,31 @@ bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms) {
   if (!A) return BAMG_ERR_INVALID;
   Status s = bsr_autotune(A, ms);
   if (!s.ok()) return fail(A->ctx, s);
-  if (lanes) *lanes = A->vec;
+  if (lanes) *lanes = A->split ? -A->split : A->vec;
   return BAMG_OK;
 }
 
 bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
   if (!A) return BAMG_ERR_INVALID;
-  if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
-    return fail(A->ctx, make_status(BAMG_ERR_INVALID, "lanes must be a power of two in [1, 32]"));
+  if (lanes <= 0) {
+    const int vs = lanes == 0 ? 4 : -lanes;
+    if (vs != 1 && vs != 2 && vs != 4)
+      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "component split takes 1, 2 or 4 warps per component"));
+    if (A->br != 6 || (A->bc != 3 && A->bc != 6))
+      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "the component-split form needs 6x3 or 6x6 blocks"));
+    A->split = A->split32 = vs;
+    return BAMG_OK;
+  }
+  if (lanes > 32 || (lanes & (lanes - 1)))
+    return fail(A->ctx, make_status(BAMG_ERR_INVALID, "lanes must be -4, -2, -1, 0 or a power of two in [1, 32]"));
   A->vec = A->vec32 = lanes;
+  A->split = A->split32 = 0;
   return BAMG_OK;
 }
 
 bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes) {
   if (!A || !lanes) return BAMG_ERR_INVALID;
-  *lanes = A->vec;
+  *lanes = A->split ? -A->split : A->vec;
   return BAMG_OK;
 }
 

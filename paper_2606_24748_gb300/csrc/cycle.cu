@@ -120,6 +120,87 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restric
   for (int a = 0; a < BS; ++a) d[i * BS + a] = f * z[a];
 }
 
+// Component-split forms of the three row kernels above (6-row blocks): CTA =
+// one slice, BS * VS warps (see row_component).  The block-diagonal inverse
+// needs every component of the new residual, exchanged through shared memory.
+template <int BS, int VS, typename T>
+__global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__ sp, const int* __restrict__ col,
+                                                         const T* __restrict__ vals, int64_t n,
+                                                         const T* __restrict__ d_in, T* __restrict__ d_out,
+                                                         T* __restrict__ x, T* __restrict__ r,
+                                                         const T* __restrict__ dinv, const float* __restrict__ w,
+                                                         const double* __restrict__ scal, int k, int has_next,
+                                                         const int* done) {
+  BAMG_DONE_RETURN
+  __shared__ T rs[BS][32];
+  const int64_t s = blockIdx.x;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BS, sub = wp / BS;
+  const int64_t i = s * 32 + lane;
+  const T acc = row_component<BS, BS, VS, T, T, T>(sp, col, vals, d_in, s, lane, a, sub);
+  const bool lead = sub == 0 && i < n;
+  T ri = T(0), di = T(0);
+  if (lead) {
+    di = d_in[i * BS + a];
+    ri = r[i * BS + a] - acc;
+    r[i * BS + a] = ri;
+    x[i * BS + a] += di;
+  }
+  if (!has_next) return;
+  if (sub == 0) rs[a][lane] = ri;
+  __syncthreads();
+  if (!lead) return;
+  const int64_t base = s * (32LL * BS * BS) + lane;
+  T z = T(0);
+#pragma unroll
+  for (int c = 0; c < BS; ++c) z = fma(__ldg(dinv + base + 32 * (a * BS + c)), rs[c][lane], z);
+  const T c1 = (T)scal[kCheb + 2 * k];
+  const T c2 = (T)(scal[kCheb + 2 * k + 1] * (w ? (double)w[i] : 1.0));
+  d_out[i * BS + a] = fma(c1, di, c2 * z);
+}
+
+template <int BS, int VS, typename T>
+__global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict__ sp, const int* __restrict__ col,
+                                                          const T* __restrict__ vals, int64_t n,
+                                                          const T* __restrict__ x, const T* __restrict__ b,
+                                                          T* __restrict__ r, T* __restrict__ d,
+                                                          const T* __restrict__ dinv, const float* __restrict__ w,
+                                                          const double* __restrict__ scal, const int* done) {
+  BAMG_DONE_RETURN
+  __shared__ T rs[BS][32];
+  const int64_t s = blockIdx.x;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BS, sub = wp / BS;
+  const int64_t i = s * 32 + lane;
+  const T acc = row_component<BS, BS, VS, T, T, T>(sp, col, vals, x, s, lane, a, sub);
+  const bool lead = sub == 0 && i < n;
+  T ri = T(0);
+  if (lead) {
+    ri = b[i * BS + a] - acc;
+    r[i * BS + a] = ri;
+  }
+  if (sub == 0) rs[a][lane] = ri;
+  __syncthreads();
+  if (!lead) return;
+  const int64_t base = s * (32LL * BS * BS) + lane;
+  T z = T(0);
+#pragma unroll
+  for (int c = 0; c < BS; ++c) z = fma(__ldg(dinv + base + 32 * (a * BS + c)), rs[c][lane], z);
+  const T f = (T)(scal[kInvTheta] * (w ? (double)w[i] : 1.0));
+  d[i * BS + a] = f * z;
+}
+
+template <int BR, int BC, int VS, typename T>
+__global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ sp, const int* __restrict__ col,
+                                                        const T* __restrict__ vals, int64_t n,
+                                                        const T* __restrict__ v, T* __restrict__ y, int accumulate,
+                                                        const int* done) {
+  BAMG_DONE_RETURN
+  const int64_t s = blockIdx.x;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BR, sub = wp / BR;
+  const int64_t i = s * 32 + lane;
+  const T acc = row_component<BR, BC, VS, T, T, T>(sp, col, vals, v, s, lane, a, sub);
+  if (sub == 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
+}
+
 template <typename T>
 __global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ x, const int* done) {
   BAMG_DONE_RETURN
@@ -188,9 +269,17 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
-    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
-                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                   k + 1 < m ? 1 : 0, done); BAMG_COUNT_LAUNCH; })
+    if (BS == 6 && split_for<T>(A)) {
+      BAMG_DISPATCH_VS(split_for<T>(A), {
+        k_cheb_step_split<BS, VS, T><<<(unsigned)A->nslices, 32 * BS * VS, 0, st>>>(
+            A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
+            k + 1 < m ? 1 : 0, done);
+        BAMG_COUNT_LAUNCH; })
+    } else {
+      BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                     d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
+                                                     k + 1 < m ? 1 : 0, done); BAMG_COUNT_LAUNCH; })
+    }
     prof_end(mg->ctx, pm, st);
   }
   BAMG_CUDA(cudaGetLastError());
@@ -206,15 +295,32 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
+  const int split = BS == 6 ? split_for<T>(A) : 0;
+  const unsigned gs = (unsigned)A->nslices;
   const int pr = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_RINIT_L0 : -1, st);
-  BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
-                                                  p.d0, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; })
+  if (split) {
+    BAMG_DISPATCH_VS(split, {
+      k_cheb_rinit_split<BS, VS, T><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, p.x, p.b,
+                                                                 p.r, p.d0, p.dinv, L.weights, sc, done);
+      BAMG_COUNT_LAUNCH; })
+  } else {
+    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+                                                    p.d0, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; })
+  }
   prof_end(mg->ctx, pr, st);
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k + 1 < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
-    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
-                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done); BAMG_COUNT_LAUNCH; })
+    if (split) {
+      BAMG_DISPATCH_VS(split, {
+        k_cheb_step_split<BS, VS, T><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
+                                                                  d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
+                                                                  1, done);
+        BAMG_COUNT_LAUNCH; })
+    } else {
+      BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                     d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done); BAMG_COUNT_LAUNCH; })
+    }
     prof_end(mg->ctx, pm, st);
   }
   const int64_t mm = L.n * BS;
@@ -228,6 +334,14 @@ static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int a
                        cudaStream_t st) {
   const int64_t rows = row_threads_for<T>(M);
   if (rows == 0) return Status{};
+  if (BR == 6 && split_for<T>(M)) {
+    BAMG_DISPATCH_VS(split_for<T>(M), {
+      k_transfer_split<BR, BC, VS, T><<<(unsigned)M->nslices, 32 * BR * VS, 0, st>>>(M->slice_ptr, M->sell_col, vals,
+                                                                                     M->nbr, v, y, accumulate, done);
+      BAMG_COUNT_LAUNCH; })
+    BAMG_CUDA(cudaGetLastError());
+    return Status{};
+  }
   BAMG_DISPATCH_V(lanes_for<T>(M), { k_transfer<BR, BC, V, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
       M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
@@ -353,7 +467,7 @@ __global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double
 
 // q = A p, alpha = rz / (p.q)
 template <int V>
-__global__ void __launch_bounds__(kRowThreads) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
+__global__ void __launch_bounds__(256) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
                                                        const double* __restrict__ vals, int64_t n, int64_t nthreads,
                                                        const double* __restrict__ p, double* __restrict__ q,
                                                        CgState* s, double* partials, unsigned* counter) {
@@ -446,7 +560,7 @@ __global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restri
 
 // ||b - A x||^2 into s->pq (final true residual)
 template <int V>
-__global__ void __launch_bounds__(kRowThreads) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
+__global__ void __launch_bounds__(256) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
                                                                const double* __restrict__ vals, int64_t n,
                                                                int64_t nthreads, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* out_norm2,
@@ -472,8 +586,11 @@ __global__ void __launch_bounds__(kRowThreads) k_true_residual(const int* __rest
 }
 
 static unsigned vec_grid(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 1216)); }
+// Reducing row kernels: 256 threads per CTA, so that one thread per row
+// (the fine operator has 274,625 rows at 64^3 elements) fits in the 1,216 CTAs
+// of the reduction partials.
 static unsigned row_grid(int64_t rows) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kRowThreads - 1) / kRowThreads, 1216));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 1216));
 }
 
 // One CG iteration after the first preconditioner application.
@@ -485,7 +602,7 @@ static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   CgState* s = mg->cg;
   const int* done = &s->done;
   const int pa = prof_begin(ctx, BAMG_PROF_CG_AP, st);
-  BAMG_DISPATCH_V(A->vec, { k_cg_Ap<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+  BAMG_DISPATCH_V(A->vec, { k_cg_Ap<V><<<row_grid(rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
                                                   ctx->d_partials, ctx->d_counters + 2); BAMG_COUNT_LAUNCH; })
   prof_end(ctx, pa, st);
   { k_cg_xr<<<vec_grid(m), 256, 0, st>>>(m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3); BAMG_COUNT_LAUNCH; }
@@ -604,7 +721,7 @@ Status cg_epilogue(bamg_mg* mg, const double* b, double* x, double* true_r2, cud
   if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   const bamg_bsr* A = L0.A;
   const int64_t rows = row_threads(A);
-  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
                                                           true_r2, ctx->d_partials, ctx->d_counters + 7); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};

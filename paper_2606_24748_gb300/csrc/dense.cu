@@ -1,8 +1,10 @@
-// Exact coarsest-level solve: dense FP64 Cholesky A = L L^T, then the explicit
-// inverse factor W = L^-1, so every V-cycle applies x = W^T (W b) as two
-// dense triangular matrix-vector products spread over the whole GPU instead of
-// two sequential substitutions.  The matrix is padded to a multiple of the
-// 32-wide tiles with an identity block (which factors to itself).
+// Exact coarsest-level solve.  Dense form: FP64 Cholesky A = L L^T, then the
+// explicit inverse factor W = L^-1, so every V-cycle applies x = W^T (W b) as
+// two dense triangular matrix-vector products spread over the whole GPU
+// instead of two sequential substitutions.  The matrix is padded to a
+// multiple of the 32-wide tiles with an identity block (which factors to
+// itself).  Banded form (below): block-tridiagonal Cholesky over chunks of
+// the band, used when the level's half-bandwidth is small against its size.
 //
 // Tiled right-looking algorithms, one kernel per tile step:
 //   Cholesky   for k: factor tile (k,k); L(i,k) = A(i,k) L(k,k)^-T; A(i,j) -= L(i,k) L(j,k)^T
@@ -67,10 +69,29 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
   }
 }
 
+// 1 / sqrt(d) by Newton's method for the reciprocal square root,
+// y <- y + y (1 - d y^2) / 2, from the single-precision estimate; each step
+// doubles the correct bits (about 22 -> 44 -> full double precision).  FP64
+// division and square root are long instruction sequences on the FP64 pipe,
+// and the pivots of a factorisation are one long serial chain of them.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  const float f = (float)d;
+  double y = (f > 1e-30f && f < 1e30f) ? (double)rsqrtf(f) : 1.0 / sqrt(d);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+
 // Cholesky of the diagonal tile (k, k) in shared memory and the inverse of
-// the factor (one CTA); L is written back, L^-1 to Linv.
+// the factor (one CTA); L is written back, L^-1 to Linv.  Pivot j stores
+// L_jj = d / sqrt(d) and 1 / L_jj, so the column scaling and the rows of the
+// inverse multiply instead of dividing.
 __device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __restrict__ Linv, int* err,
                           double (*a)[kT + 1], double (*w)[kT + 1]) {
+  __shared__ double inv[kT];
   const int tid = threadIdx.x;
   double* base = M + (int64_t)k * kT * ld + (int64_t)k * kT;
   __syncthreads();
@@ -83,10 +104,12 @@ __device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __r
         set_err(err, kDevBreakdown);
         d = 1.0;
       }
-      a[j][j] = sqrt(d);
+      const double r = rsqrt_newton(d);
+      a[j][j] = d * r;
+      inv[j] = r;
     }
     __syncthreads();
-    if (tid > j && tid < kT) a[tid][j] /= a[j][j];
+    if (tid > j && tid < kT) a[tid][j] *= inv[j];
     __syncthreads();
     for (int e = tid; e < kT * kT; e += blockDim.x) {
       const int i = e / kT, l = e % kT;
@@ -102,7 +125,7 @@ __device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __r
       for (int l = c + part; l < r; l += 8) t = fma(a[r][l], w[l][c], t);
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (part == 0) w[r][c] = (c <= r) ? (((r == c) ? 1.0 : 0.0) - t) / a[r][r] : 0.0;
+    if (part == 0) w[r][c] = (c <= r) ? (((r == c) ? 1.0 : 0.0) - t) * inv[r] : 0.0;
     __syncthreads();
   }
   for (int e = tid; e < kT * kT; e += blockDim.x) {
@@ -238,19 +261,278 @@ __global__ void k_tri_mv(const double* __restrict__ Wm, int64_t ld, int64_t n, c
   if (lane == 0) out[row] = (TO)acc;
 }
 
-Status coarse_factor(bamg_mg* mg) {
+// The same for KP vectors stored RHS-minor (v[j * KP + c]).
+template <int KP, typename TI, typename TO>
+__global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, const TI* __restrict__ v,
+                         TO* __restrict__ out, int lower, const int* done) {
+  if (done && *done) return;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int64_t j0 = lower ? 0 : row, j1 = lower ? row + 1 : n;
+  const double* wr = Wm + row * ld;
+  double acc[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
+  for (int64_t j = j0 + lane; j < j1; j += 32) {
+    const double wv = wr[j];
+    const TI* vj = v + j * KP;
+#pragma unroll
+    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, (double)vj[c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
+#pragma unroll
+  for (int c = 0; c < KP; ++c)
+    if (lane == c) out[row * KP + c] = (TO)acc[c];
+}
+
+// ------------------------------------------------------------ banded form
+//
+// With nodes numbered lexicographically the coarsest operator is banded: a
+// half-bandwidth of b dofs (27-point block stencil on an m^3 node grid:
+// b = 6 (m^2 + m + 2) - 1).  Split into chunks of s >= b rows (a multiple of
+// 32) it is block tridiagonal, and its Cholesky factor is block bidiagonal
+// with no fill outside the band:
+//   S_0 = A_00;  S_k = A_kk - L_{k,k-1} L_{k,k-1}^T
+//   L_kk = chol(S_k);  L_{k+1,k} = A_{k+1,k} L_kk^-T
+// which costs about nc (s^3 / 6 + 2 s^3) multiply-adds instead of n^3 / 3 for
+// the dense factor and its inverse.  The solve with L then L^T is a chain
+// over the chunks; with W_k = L_kk^-1, M_k = W_k L_{k,k-1} and
+// N_k = W_k^T L_{k+1,k}^T formed here:
+//   y_k = W_k b_k - M_k y_{k-1};   x_k = W_k^T y_k - N_k x_{k+1}
+// i.e. two block-diagonal products and 2 (nc - 1) chained products.
+
+// C = beta C + alpha A op(B) for s x s row-major matrices, op(B) = B or B^T;
+// one 32 x 32 output tile per CTA (256 threads, 4 outputs each); with
+// lower_only, tiles above the diagonal are skipped.
+template <bool kTransB>
+__global__ void __launch_bounds__(256) k_chunk_gemm(double* __restrict__ C, const double* __restrict__ A,
+                                                    const double* __restrict__ B, int s, double alpha, double beta,
+                                                    int lower_only) {
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (lower_only && tj > ti) return;
+  __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
+  const int tid = threadIdx.x, c = tid % kT, r0 = tid / kT;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int kt = 0; kt < s / kT; ++kt) {
+    __syncthreads();
+    for (int e = tid; e < kT * kT; e += blockDim.x) {
+      const int i = e / kT, j = e % kT;
+      As[i][j] = A[(int64_t)(ti * kT + i) * s + kt * kT + j];
+      Bs[i][j] = kTransB ? B[(int64_t)(tj * kT + i) * s + kt * kT + j] : B[(int64_t)(kt * kT + i) * s + tj * kT + j];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int l = 0; l < kT; ++l) {
+      const double bv = kTransB ? Bs[c][l] : Bs[l][c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fma(As[r0 + 8 * q][l], bv, acc[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double* p = C + (int64_t)(ti * kT + r0 + 8 * q) * s + tj * kT + c;
+    *p = (beta == 0.0 ? 0.0 : beta * *p) + alpha * acc[q];
+  }
+}
+
+// Diagonal and subdiagonal chunks from the stored blocks (upper chunks are
+// the transposes, not stored); rows past n get an identity diagonal.
+template <typename TM, int BS>
+__global__ void k_band_fill(int64_t nnzb, const int* __restrict__ rows, const int* __restrict__ colidx,
+                            const int* __restrict__ slot_of, const TM* __restrict__ vals, double* __restrict__ D,
+                            double* __restrict__ Sub, int s, int* err) {
+  constexpr int B = BS * BS;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb * B) return;
+  const int64_t k = t / B;
+  const int e = (int)(t - k * B);
+  const int64_t i = (int64_t)rows[k] * BS + e / BS, j = (int64_t)colidx[k] * BS + e % BS;
+  const int64_t ci = i / s, cj = j / s, ri = i - ci * s, rj = j - cj * s;
+  const double v = (double)vals[vidx<B>(slot_of[k], e)];
+  if (ci == cj)
+    D[(ci * s + ri) * s + rj] = v;
+  else if (ci == cj + 1)
+    Sub[(cj * s + ri) * s + rj] = v;
+  else if (ci + 1 != cj && v != 0.0)
+    set_err(err, kDevIndex);  // outside the band the chunks were sized for
+}
+
+__global__ void k_band_pad(double* __restrict__ D, int64_t n, int64_t npad, int s) {
+  const int64_t i = n + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  const int64_t c = i / s, r = i - c * s;
+  D[(c * s + r) * s + r] = 1.0;
+}
+
+// out[k s + r] = sum_j M_k[r][j] v[k s + j] for every chunk k (rows of v at
+// or past nvalid read as 0); warp per row, KP vectors.
+template <int KP, typename TI>
+__global__ void k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows, const TI* __restrict__ v,
+                           int64_t nvalid, double* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const int64_t k = row / s, r = row - k * s;
+  const double* mr = Mats + (k * s + r) * s;
+  const int64_t g0 = k * s;
+  double acc[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
+  for (int j = lane; j < s; j += 32) {
+    if (g0 + j >= nvalid) break;
+    const double wv = mr[j];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, (double)v[(g0 + j) * KP + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
+#pragma unroll
+  for (int c = 0; c < KP; ++c)
+    if (lane == c) out[row * KP + c] = acc[c];
+}
+
+// y[r] -= sum_j M[r][j] z[j] for one chunk (s rows), KP vectors.
+template <int KP>
+__global__ void k_chunk_chain(const double* __restrict__ M, int s, const double* __restrict__ z,
+                              double* __restrict__ y, const int* done) {
+  if (done && *done) return;
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= s) return;
+  const double* mr = M + r * s;
+  double acc[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
+  for (int j = lane; j < s; j += 32) {
+    const double wv = mr[j];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, z[(int64_t)j * KP + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
+#pragma unroll
+  for (int c = 0; c < KP; ++c)
+    if (lane == c) y[r * KP + c] -= acc[c];
+}
+
+template <typename TO>
+__global__ void k_band_out(int64_t m, const double* __restrict__ x, TO* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < m) out[t] = (TO)x[t];
+}
+
+static unsigned warps_grid(int64_t rows) { return (unsigned)std::max<int64_t>(1, (rows * 32 + 255) / 256); }
+
+// Half-bandwidth of the coarsest operator in dofs.
+static int64_t half_bandwidth(const bamg_bsr* A) {
+  int64_t b = 0;
+  for (int64_t I = 0; I < A->nbr; ++I)
+    for (int k = A->h_rowptr[I]; k < A->h_rowptr[I + 1]; ++k) b = std::max<int64_t>(b, std::llabs(A->h_colidx[k] - I));
+  return (b + 1) * A->br - 1;
+}
+
+static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld, int ntl, double* dt) {
+  int per_sm = 0;
+  BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
+  if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
+  const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
+  int* err = ctx->d_err;
+  void* args[] = {&F, &W, &ld, &ntl, &dt, &err};
+  BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, ctx->stream));
+  BAMG_COUNT_LAUNCH;
+  return Status{};
+}
+
+static Status band_factor(bamg_mg* mg) {
+  bamg_ctx* ctx = mg->ctx;
+  cudaStream_t st = ctx->stream;
+  Level& C = mg->levels.back();
+  CoarseDense& D = mg->coarse;
+  const bamg_bsr* A = C.A;
+  const int bs = C.bs, s = D.s, nc = D.nc;
+  const int64_t n = D.n, npad = D.npad, ss = (int64_t)s * s;
+  if (!D.D) {
+    for (double** p : {&D.D, &D.Wb, &D.Wtb, &D.Mb}) BAMG_TRY(dalloc(p, nc * ss, st));
+    for (double** p : {&D.Sub, &D.Bb, &D.Nb}) BAMG_TRY(dalloc(p, std::max(1, nc - 1) * ss, st));
+    BAMG_TRY(dalloc(&D.b64, npad, st));
+    BAMG_TRY(dalloc(&D.x64, npad, st));
+    BAMG_TRY(dalloc(&D.dinv_tiles, (int64_t)(s / kT) * kT * kT, st));
+  }
+  const int pm = prof_begin(ctx, BAMG_PROF_COARSE_FACTOR, st);
+  BAMG_CUDA(cudaMemsetAsync(D.D, 0, sizeof(double) * nc * ss, st));
+  BAMG_CUDA(cudaMemsetAsync(D.Sub, 0, sizeof(double) * std::max(1, nc - 1) * ss, st));
+  if (npad > n) { k_band_pad<<<(unsigned)((npad - n + 255) / 256), 256, 0, st>>>(D.D, n, npad, s); BAMG_COUNT_LAUNCH; }
+  const int64_t nt_fill = A->nnzb * bs * bs;
+  if (nt_fill > 0) {
+    const unsigned b = (unsigned)((nt_fill + 255) / 256);
+    const bool f32 = A->vals64_stale;
+    if (bs == 6) {
+      if (f32) { k_band_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      else { k_band_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+    } else {
+      if (f32) { k_band_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      else { k_band_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+    }
+  }
+  const int t = s / kT;
+  const dim3 g((unsigned)t, (unsigned)t);
+  for (int k = 0; k < nc; ++k) {
+    double* Dk = D.D + k * ss;
+    double* Wk = D.Wb + k * ss;
+    if (k > 0) { k_chunk_gemm<true><<<g, 256, 0, st>>>(Dk, D.Bb + (k - 1) * ss, D.Bb + (k - 1) * ss, s, -1.0, 1.0, 1); BAMG_COUNT_LAUNCH; }
+    BAMG_CUDA(cudaMemsetAsync(Wk, 0, sizeof(double) * ss, st));
+    BAMG_TRY(cooperative_factor(ctx, Dk, Wk, s, t, D.dinv_tiles));
+    { k_transpose_dense<<<g, 256, 0, st>>>(Wk, D.Wtb + k * ss, s); BAMG_COUNT_LAUNCH; }
+    if (k + 1 < nc) {
+      double* Bk = D.Bb + k * ss;
+      { k_chunk_gemm<true><<<g, 256, 0, st>>>(Bk, D.Sub + k * ss, Wk, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
+      { k_chunk_gemm<true><<<g, 256, 0, st>>>(D.Nb + k * ss, D.Wtb + k * ss, Bk, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
+    }
+    if (k > 0) { k_chunk_gemm<false><<<g, 256, 0, st>>>(D.Mb + k * ss, Wk, D.Bb + (k - 1) * ss, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
+  }
+  prof_end(ctx, pm, st);
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+template <int KP, typename T>
+static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, const int* done, cudaStream_t st) {
+  CoarseDense& D = mg->coarse;
+  const int s = D.s, nc = D.nc;
+  const int64_t ss = (int64_t)s * s, npad = D.npad;
+  // forward: y = blockdiag(W) b, then y_k -= M_k y_{k-1}
+  { k_chunk_mv<KP, T><<<warps_grid(npad), 256, 0, st>>>(D.Wb, s, npad, b, D.n, y, done); BAMG_COUNT_LAUNCH; }
+  for (int k = 1; k < nc; ++k) {
+    k_chunk_chain<KP><<<warps_grid(s), 256, 0, st>>>(D.Mb + k * ss, s, y + (int64_t)(k - 1) * s * KP,
+                                                     y + (int64_t)k * s * KP, done);
+    BAMG_COUNT_LAUNCH;
+  }
+  // backward: z = blockdiag(W^T) y, then z_k -= N_k z_{k+1}
+  { k_chunk_mv<KP, double><<<warps_grid(npad), 256, 0, st>>>(D.Wtb, s, npad, y, npad, z, done); BAMG_COUNT_LAUNCH; }
+  for (int k = nc - 2; k >= 0; --k) {
+    k_chunk_chain<KP><<<warps_grid(s), 256, 0, st>>>(D.Nb + k * ss, s, z + (int64_t)(k + 1) * s * KP,
+                                                     z + (int64_t)k * s * KP, done);
+    BAMG_COUNT_LAUNCH;
+  }
+  const int64_t m = D.n * KP;
+  { k_band_out<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, z, x, done); BAMG_COUNT_LAUNCH; }
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+static Status dense_factor(bamg_mg* mg) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
   Level& C = mg->levels.back();
   CoarseDense& D = mg->coarse;
   const int bs = C.bs;
-  const int64_t n = C.n * bs;
-  const int64_t npad = ((n + kT - 1) / kT) * kT;
+  const int64_t n = D.n, npad = D.npad;
   const int nt = (int)(npad / kT);
-  if (npad > 16384) return make_status(BAMG_ERR_INVALID, "coarsest level too large for a dense solve (%lld)", (long long)n);
   if (!D.M) {
-    D.n = n;
-    D.npad = npad;
     BAMG_TRY(dalloc(&D.M, npad * npad, st));
     BAMG_TRY(dalloc(&D.Wt, npad * npad, st));
     BAMG_TRY(dalloc(&D.b64, npad, st));
@@ -263,44 +545,24 @@ Status coarse_factor(bamg_mg* mg) {
   const int pm = prof_begin(ctx, BAMG_PROF_COARSE_FACTOR, st);
   { k_dense_init<<<(unsigned)((npad * npad + 255) / 256), 256, 0, st>>>(F, n, npad); BAMG_COUNT_LAUNCH; }
   const bamg_bsr* A = C.A;
-  if (!D.rows) {
-    std::vector<int> rows(A->nnzb);
-    for (int64_t I = 0; I < A->nbr; ++I)
-      for (int k = A->h_rowptr[I]; k < A->h_rowptr[I + 1]; ++k) rows[k] = (int)I;
-    BAMG_TRY(upload(&D.rows, rows, st));
-    BAMG_CUDA(cudaStreamSynchronize(st));
-  }
-  const int* d_rows = D.rows;
   const int64_t nt_fill = A->nnzb * bs * bs;
   if (nt_fill > 0) {
     const unsigned b = (unsigned)((nt_fill + 255) / 256);
     if (bs == 6) {
       if (A->vals64_stale)
-        { k_dense_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
+        { k_dense_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
       else
-        { k_dense_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
+        { k_dense_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
     } else {
       if (A->vals64_stale)
-        { k_dense_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
+        { k_dense_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, F, npad); BAMG_COUNT_LAUNCH; }
       else
-        { k_dense_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, d_rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
+        { k_dense_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, F, npad); BAMG_COUNT_LAUNCH; }
     }
   }
   BAMG_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * npad * npad, st));
   if (!D.dinv_tiles) BAMG_TRY(dalloc(&D.dinv_tiles, (int64_t)nt * kT * kT, st));
-  {
-    int per_sm = 0;
-    BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
-    const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
-    int64_t ld = npad;
-    int ntl = nt;
-    double* dt = D.dinv_tiles;
-    int* err = ctx->d_err;
-    void* args[] = {&F, &W, &ld, &ntl, &dt, &err};
-    if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
-    BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, st));
-    BAMG_COUNT_LAUNCH;
-  }
+  BAMG_TRY(cooperative_factor(ctx, F, W, npad, nt, D.dinv_tiles));
   // Wt = W^T (the factor in F is no longer needed)
   dim3 tg((unsigned)nt, (unsigned)nt);
   { k_transpose_dense<<<tg, 256, 0, st>>>(W, F, npad); BAMG_COUNT_LAUNCH; }
@@ -309,9 +571,43 @@ Status coarse_factor(bamg_mg* mg) {
   return Status{};
 }
 
+Status coarse_factor(bamg_mg* mg) {
+  cudaStream_t st = mg->ctx->stream;
+  Level& C = mg->levels.back();
+  CoarseDense& D = mg->coarse;
+  const bamg_bsr* A = C.A;
+  const int64_t n = C.n * C.bs;
+  if (D.n == 0) {  // first factorisation: choose the form
+    D.n = n;
+    const int64_t b = half_bandwidth(A);
+    const int64_t s = ((b + 1 + kT - 1) / kT) * kT;
+    const int64_t nc = (n + s - 1) / s;
+    const int mode = mg->opts.coarse_solver;
+    const bool band = mode != 1 && nc >= (mode == 2 ? 2 : 3);
+    if (band) {
+      D.s = (int)s;
+      D.nc = (int)nc;
+      D.npad = nc * s;
+    } else {
+      D.npad = ((n + kT - 1) / kT) * kT;
+      if (D.npad > 16384)
+        return make_status(BAMG_ERR_INVALID, "coarsest level too large for a dense solve (%lld)", (long long)n);
+    }
+    std::vector<int> rows(A->nnzb);
+    for (int64_t I = 0; I < A->nbr; ++I)
+      for (int k = A->h_rowptr[I]; k < A->h_rowptr[I + 1]; ++k) rows[k] = (int)I;
+    BAMG_TRY(upload(&D.rows, rows, st));
+    BAMG_CUDA(cudaStreamSynchronize(st));
+  }
+  BAMG_TRY(D.nc > 0 ? band_factor(mg) : dense_factor(mg));
+  D.factored = true;
+  return Status{};
+}
+
 template <typename T>
 Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t st) {
   CoarseDense& D = mg->coarse;
+  if (D.nc > 0) return band_apply<1, T>(mg, b, x, D.b64, D.x64, done, st);
   const int64_t n = D.n;
   const unsigned g = (unsigned)((n * 32 + 255) / 256);
   { k_tri_mv<T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, D.x64, 1, done); BAMG_COUNT_LAUNCH; }
@@ -320,7 +616,32 @@ Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t
   return Status{};
 }
 
+template <typename T>
+Status coarse_apply_multi(bamg_mg* mg, int kp, const T* b, T* x, double* work, const int* done, cudaStream_t st) {
+  CoarseDense& D = mg->coarse;
+  const int64_t n = D.n;
+  double* y = work;
+  double* z = work + D.npad * kp;
+#define BAMG_KP_CASE(KP)                                                                                   \
+  if (kp == KP) {                                                                                          \
+    if (D.nc > 0) return band_apply<KP, T>(mg, b, x, y, z, done, st);                                     \
+    const unsigned g = (unsigned)((n * 32 + 255) / 256);                                                   \
+    { k_tri_mm<KP, T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, y, 1, done); BAMG_COUNT_LAUNCH; }      \
+    { k_tri_mm<KP, double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, y, x, 0, done); BAMG_COUNT_LAUNCH; }     \
+    BAMG_CUDA(cudaGetLastError());                                                                         \
+    return Status{};                                                                                       \
+  }
+  BAMG_KP_CASE(4)
+  BAMG_KP_CASE(8)
+  BAMG_KP_CASE(16)
+  BAMG_KP_CASE(32)
+#undef BAMG_KP_CASE
+  return make_status(BAMG_ERR_INVALID, "unsupported column count %d", kp);
+}
+
 template Status coarse_apply<double>(bamg_mg*, const double*, double*, const int*, cudaStream_t);
 template Status coarse_apply<float>(bamg_mg*, const float*, float*, const int*, cudaStream_t);
+template Status coarse_apply_multi<double>(bamg_mg*, int, const double*, double*, double*, const int*, cudaStream_t);
+template Status coarse_apply_multi<float>(bamg_mg*, int, const float*, float*, double*, const int*, cudaStream_t);
 
 }  // namespace bamg

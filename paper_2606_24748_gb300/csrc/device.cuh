@@ -61,6 +61,45 @@ __device__ __forceinline__ void row_product(const int* __restrict__ slice_ptr,
   }
 }
 
+// Component-split block-row product for matrices with 6-row blocks (the
+// restriction, coarse operators).  A CTA of BR * VS warps takes one 32-row
+// slice: warp (a, sub) adds the products for output component a (lane = row
+// within the slice) over every VS-th chunk of the slice, starting at sub.
+// Each block adds BC products to one accumulator, so no lane is idle and no
+// partial sums are combined across lanes: with FP64 at two FMA per clock per
+// SM, the lanes-per-row form spends as many instructions on its reduction
+// and its one-lane epilogue as on the products of a short row.  The VS
+// partial sums of a component are added in shared memory in sub order
+// (one barrier); the result is valid in the sub = 0 warps.  Every thread of
+// the CTA must call this.  The warps read the same column indices and x
+// entries (cached); every value is read once, coalesced.
+template <int BR, int BC, int VS, typename TM, typename TA, typename TX>
+__device__ __forceinline__ TA row_component(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                            const TM* __restrict__ vals, const TX* __restrict__ x, int64_t s,
+                                            int lane, int a, int sub) {
+  const int c0 = __ldg(slice_ptr + s), c1 = __ldg(slice_ptr + s + 1);
+  TA acc = TA(0);
+  for (int c = c0 + sub; c < c1; c += VS) {
+    const int j = __ldg(col + (int64_t)c * 32 + lane);
+    const TM* v = vals + (int64_t)c * (32 * BR * BC) + 32 * (a * BC) + lane;
+    TA xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = (TA)__ldg(x + (int64_t)j * BC + q);
+#pragma unroll
+    for (int q = 0; q < BC; ++q) acc = fma((TA)__ldcs(v + 32 * q), xv[q], acc);
+  }
+  if (VS > 1) {
+    __shared__ TA part[VS][BR][32];
+    part[sub][a][lane] = acc;
+    __syncthreads();
+    if (sub == 0) {
+#pragma unroll
+      for (int t = 1; t < VS; ++t) acc += part[t][a][lane];
+    }
+  }
+  return acc;
+}
+
 // Thread -> (row, sub-lane) for V lanes per row.
 template <int V>
 __device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub) {

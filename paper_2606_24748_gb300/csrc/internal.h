@@ -97,6 +97,8 @@ struct bamg_bsr {
   bool all_diag = false;     // every block row has its diagonal block
   int vec = 1;               // lanes per block row of the FP64 row kernels (1..32, power of 2)
   int vec32 = 1;             // the same for kernels reading the FP32 copy
+  int split = 0;             // 6-row blocks: 0 = lanes per row; 1, 2 or 4 = component split with
+  int split32 = 0;           //   that many warps per component of a slice (FP64 / FP32 kernels)
   bool vec_tuned = false;
   std::vector<int> h_slice_ptr, h_slot_of;
   double* vals = nullptr;    // 32 * nchunks * B
@@ -166,6 +168,16 @@ struct CoarseDense {
   double* x64 = nullptr;
   int* rows = nullptr;   // block row of every stored block of the coarsest operator
   double* dinv_tiles = nullptr;  // inverses of the 32x32 diagonal tiles of L
+  bool factored = false;
+  // Banded form (nc > 0): the padded matrix (npad = nc * s) split into chunks
+  // of s rows is block tridiagonal; per chunk k, s x s row-major:
+  //   D[k]  A_kk, then the Schur complement, then its Cholesky factor L_kk
+  //   Sub[k] A_{k+1,k};  Bb[k] = L_{k+1,k} = A_{k+1,k} L_kk^-T
+  //   Wb[k] = L_kk^-1,  Wtb[k] = its transpose
+  //   Mb[k] = W_k L_{k,k-1} (k >= 1),  Nb[k] = W_k^T L_{k+1,k}^T (k <= nc - 2)
+  int nc = 0, s = 0;
+  double *D = nullptr, *Sub = nullptr, *Wb = nullptr, *Wtb = nullptr, *Bb = nullptr, *Mb = nullptr,
+         *Nb = nullptr;
 };
 
 struct Level {
@@ -221,7 +233,7 @@ struct MultiLevel {
 struct MultiWork {
   int kp = 0;
   std::vector<MultiLevel> lv;
-  double* coarse_y = nullptr;  // npad x kp, FP64
+  double* coarse_y = nullptr;  // 2 x npad x kp, FP64 (coarsest-solve work)
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr, *czold = nullptr;
   bool own_rz = false;         // cr / cz allocated (mixed form) or aliased to level 0 (FP64)
   CgMultiState* st = nullptr;
@@ -337,6 +349,10 @@ Status mg_refresh_restriction(bamg_mg* mg, int l);      // state-gated R = P^T
 Status coarse_factor(bamg_mg* mg);                      // dense Cholesky + inverse of the coarsest level
 template <typename T>
 Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t st);
+// The same solve for kp vectors stored RHS-minor (b, x: n x kp); work holds
+// 2 * npad * kp doubles.
+template <typename T>
+Status coarse_apply_multi(bamg_mg* mg, int kp, const T* b, T* x, double* work, const int* done, cudaStream_t st);
 template <typename T>
 Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
@@ -370,6 +386,17 @@ template <typename T>
 inline int lanes_for(const bamg_bsr* A) {
   return sizeof(T) == 4 ? A->vec32 : A->vec;
 }
+template <typename T>
+inline int split_for(const bamg_bsr* A) {
+  return sizeof(T) == 4 ? A->split32 : A->split;
+}
+// Run `body` with the compile-time warps per component VS matching s (1, 2 or 4).
+#define BAMG_DISPATCH_VS(s, ...)                            \
+  switch (s) {                                             \
+    case 4: { constexpr int VS = 4; __VA_ARGS__; } break;   \
+    case 2: { constexpr int VS = 2; __VA_ARGS__; } break;   \
+    default: { constexpr int VS = 1; __VA_ARGS__; } break;  \
+  }
 template <typename T>
 inline int64_t row_threads_for(const bamg_bsr* A) {
   return A->nslices * kSlice * (int64_t)lanes_for<T>(A);

@@ -506,7 +506,9 @@ static void mg_release(bamg_mg* mg) {
     for (float** p : {&L.b32, &L.x32, &L.r32, &L.d032, &L.d132, &L.dinv32}) dfree(*p, st);
   }
   for (double** p : {&mg->cx, &mg->cr, &mg->cp, &mg->cq, &mg->cz, &mg->czold, &mg->scal, &mg->power_w[0],
-                     &mg->power_w[1], &mg->coarse.M, &mg->coarse.Wt, &mg->coarse.b64, &mg->coarse.x64})
+                     &mg->power_w[1], &mg->coarse.M, &mg->coarse.Wt, &mg->coarse.b64, &mg->coarse.x64,
+                     &mg->coarse.D, &mg->coarse.Sub, &mg->coarse.Wb, &mg->coarse.Wtb, &mg->coarse.Bb,
+                     &mg->coarse.Mb, &mg->coarse.Nb})
     dfree(*p, st);
   dfree(mg->coarse.rows, st);
   dfree(mg->coarse.dinv_tiles, st);
@@ -722,6 +724,7 @@ void bamg_mg_opts_default(bamg_mg_opts* o) {
   o->power_its = 15;
   o->precision = BAMG_FP64;
   o->autotune = 1;
+  o->coarse_solver = 0;
 }
 
 bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, const uint8_t* dirichlet,
@@ -796,11 +799,15 @@ bamg_status bamg_mg_set_smoother_weights(bamg_mg* mg, int level, const float* w)
 
 bamg_status bamg_mg_set_lanes(bamg_mg* mg, int lanes) {
   if (!mg) return BAMG_ERR_INVALID;
-  if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
-    return fail(mg->ctx, make_status(BAMG_ERR_INVALID, "lanes must be a power of two in [1, 32]"));
+  if (lanes < 0 || lanes > 32 || (lanes & (lanes - 1)))
+    return fail(mg->ctx, make_status(BAMG_ERR_INVALID, "lanes must be 0 or a power of two in [1, 32]"));
   for (auto& L : mg->levels)
     for (bamg_bsr* M : {L.A, L.P, L.R})
-      if (M) M->vec = M->vec32 = lanes;
+      if (M) {
+        const bool split = lanes == 0 && M->br == 6 && (M->bc == 3 || M->bc == 6);
+        M->vec = M->vec32 = lanes == 0 ? 1 : lanes;
+        M->split = M->split32 = split ? 4 : 0;
+      }
   mg_release_graphs(mg);  // captured iterations hold the old launch shapes
   return BAMG_OK;
 }

@@ -214,34 +214,6 @@ __global__ void k_munpack(int64_t m, int k, int kp, const TS* __restrict__ src, 
   dst[t] = (double)src[d * kp + j];
 }
 
-// Coarsest level, KP columns: y_i = sum_{j<=i} W[i][j] v_j (lower) or
-// x_j = sum_{i>=j} Wt[j][i] y_i (upper); warp per row, the single-vector
-// kernel's summation order per column.
-template <int KP, typename TI, typename TO>
-__global__ void k_mtri(const double* __restrict__ Wm, int64_t ld, int64_t n, const TI* __restrict__ v,
-                       TO* __restrict__ out, int lower, const int* done) {
-  BAMG_DONE_RETURN
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const int64_t j0 = lower ? 0 : row, j1 = lower ? row + 1 : n;
-  const double* wr = Wm + row * ld;
-  double acc[KP];
-#pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
-  for (int64_t j = j0 + lane; j < j1; j += 32) {
-    const double wv = wr[j];
-    const TI* vj = v + j * KP;
-#pragma unroll
-    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, (double)vj[c], acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
-#pragma unroll
-  for (int c = 0; c < KP; ++c)
-    if (lane == c) out[row * KP + c] = (TO)acc[c];
-}
-
 // ----------------------------------------------------------------- CG kernels
 
 __global__ void k_mcg_setup(CgMultiState* s, int k, int kp, double rtol, int maxit) {
@@ -547,23 +519,7 @@ Status mtransfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int kp, int
 
 template <typename T>
 Status mcoarse(bamg_mg* mg, int kp, const T* b, T* x, const int* done, cudaStream_t st) {
-  CoarseDense& D = mg->coarse;
-  const int64_t n = D.n;
-  const unsigned g = grid_for(n * 32);
-  double* y = mg->multi->coarse_y;
-#define BAMG_MTRI(KP)                                                                                         \
-  if (kp == KP) {                                                                                             \
-    { k_mtri<KP, T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, y, 1, done); BAMG_COUNT_LAUNCH; }           \
-    { k_mtri<KP, double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, y, x, 0, done); BAMG_COUNT_LAUNCH; }          \
-    BAMG_CUDA(cudaGetLastError());                                                                            \
-    return Status{};                                                                                          \
-  }
-  BAMG_MTRI(4)
-  BAMG_MTRI(8)
-  BAMG_MTRI(16)
-  BAMG_MTRI(32)
-#undef BAMG_MTRI
-  return make_status(BAMG_ERR_INVALID, "unsupported column count %d", kp);
+  return coarse_apply_multi<T>(mg, kp, b, x, mg->multi->coarse_y, done, st);
 }
 
 // level 0 block right-hand side -> level 0 block iterate
@@ -684,7 +640,7 @@ Status prepare(bamg_mg* mg, int kp) {
     }
   }
   const int64_t m = mg->levels[0].n * 3 * (int64_t)kp;
-  BAMG_TRY(dalloc(&W.coarse_y, mg->coarse.npad * kp, st));
+  BAMG_TRY(dalloc(&W.coarse_y, 2 * mg->coarse.npad * kp, st));
   for (double** p : {&W.cx, &W.cp, &W.cq, &W.czold}) BAMG_TRY(dalloc(p, m, st));
   if (f32) {
     BAMG_TRY(dalloc(&W.cr, m, st));
@@ -720,7 +676,7 @@ Status check_multi(bamg_mg* mg, int k) {
   if (k < 1 || k > kMaxRhs) return make_status(BAMG_ERR_INVALID, "column count %d outside 1..%d", k, kMaxRhs);
   if (mg->levels.empty() || mg->levels[0].bs != 3)
     return make_status(BAMG_ERR_STATE, "the hierarchy has no 3x3-block fine level");
-  if (!mg->coarse.M) return make_status(BAMG_ERR_STATE, "the hierarchy has not been updated");
+  if (!mg->coarse.factored) return make_status(BAMG_ERR_STATE, "the hierarchy has not been updated");
   return Status{};
 }
 

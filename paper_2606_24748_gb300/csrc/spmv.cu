@@ -25,6 +25,18 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv(const int* __restrict__ sl
   }
 }
 
+// Component-split form for 6-row blocks (CTA = one slice, BR * VS warps).
+template <int BR, int BC, int VS, typename T>
+__global__ void __launch_bounds__(768) k_spmv_split(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                                    const T* __restrict__ vals, const T* __restrict__ x,
+                                                    T* __restrict__ y, int64_t nbr) {
+  const int64_t s = blockIdx.x;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BR, sub = wp / BR;
+  const T acc = row_component<BR, BC, VS, T, T, T>(slice_ptr, col, vals, x, s, lane, a, sub);
+  const int64_t i = s * 32 + lane;
+  if (sub == 0 && i < nbr) y[i * BR + a] = acc;
+}
+
 // Any block shape up to 8x8 (shapes without a specialisation).
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) k_spmv_any(const int* __restrict__ slice_ptr,
@@ -107,8 +119,25 @@ __global__ void __launch_bounds__(256) k_spmm4(const int* __restrict__ slice_ptr
   for (int r = 0; r < BR; ++r) st4(Y + (row * BR + r) * k + c0, acc[r]);
 }
 
+static bool can_split(const bamg_bsr* A) { return A->br == 6 && (A->bc == 3 || A->bc == 6); }
+
+// vec = lanes per row (1..32), or -VS for the component-split form with VS
+// warps per component.
 template <typename T>
 static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* x, T* y, cudaStream_t st) {
+  if (vec < 0) {
+    if (A->nslices == 0) return Status{};
+    BAMG_DISPATCH_VS(-vec, {
+      if (A->bc == 6)
+        k_spmv_split<6, 6, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y,
+                                                                            A->nbr);
+      else
+        k_spmv_split<6, 3, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y,
+                                                                            A->nbr);
+      BAMG_COUNT_LAUNCH; })
+    BAMG_CUDA(cudaGetLastError());
+    return Status{};
+  }
   const int64_t nt = A->nslices * kSlice * (int64_t)vec;
   if (nt == 0) return Status{};
   const unsigned blocks = (unsigned)((nt + kRowThreads - 1) / kRowThreads);
@@ -132,7 +161,7 @@ static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* 
 
 template <typename T>
 Status launch_spmv(const bamg_bsr* A, const T* vals, const T* x, T* y, cudaStream_t st) {
-  return launch_spmv_v<T>(A, lanes_for<T>(A), vals, x, y, st);
+  return launch_spmv_v<T>(A, split_for<T>(A) && can_split(A) ? -split_for<T>(A) : lanes_for<T>(A), vals, x, y, st);
 }
 
 int default_vec(const bamg_bsr* A) {
@@ -154,7 +183,7 @@ int default_vec(const bamg_bsr* A) {
 // first, untimed); timing warm-cache repeats would favour one lane per row
 // for matrices that fit in L2.  Cold path (setup); allocates work buffers.
 template <typename T>
-static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, float* out_ms) {
+static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, int* out_split, float* out_ms) {
   cudaStream_t st = A->ctx->stream;
   T *x = nullptr, *y = nullptr;
   const int64_t nx = std::max<int64_t>(1, A->nbc * A->bc), ny = std::max<int64_t>(1, A->nbr * A->br);
@@ -169,15 +198,21 @@ static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, float* out_ms
   BAMG_TRY(dalloc((char**)&flush, (int64_t)flush_bytes, st));
   float best = 1e30f;
   int bestv = *out_vec;
+  int best_split = 0;
   Status s;
-  for (int v = 1; v <= 32; v *= 2) {
-    for (int w = 0; w < 2 && s.ok(); ++w) s = launch_spmv_v<T>(A, v, vals, x, y, st);
+  // widths 1, 2, ..., 32, then (6-row blocks) the component-split form with
+  // 1, 2 and 4 warps per component, coded as -1, -2, -4
+  static const int kChoices[] = {1, 2, 4, 8, 16, 32, -1, -2, -4};
+  const int n_choices = can_split(A) ? 9 : 6;
+  for (int ci = 0; ci < n_choices; ++ci) {
+    const int lv = kChoices[ci];
+    for (int w = 0; w < 2 && s.ok(); ++w) s = launch_spmv_v<T>(A, lv, vals, x, y, st);
     if (!s.ok()) break;
     float t[5];
     for (int rep = 0; rep < 5; ++rep) {
       cudaMemsetAsync(flush, rep, flush_bytes, st);
       cudaEventRecord(e0, st);
-      s = launch_spmv_v<T>(A, v, vals, x, y, st);
+      s = launch_spmv_v<T>(A, lv, vals, x, y, st);
       cudaEventRecord(e1, st);
       if (!s.ok()) break;
       cudaEventSynchronize(e1);
@@ -190,7 +225,12 @@ static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, float* out_ms
     std::sort(t, t + 5);
     if (t[2] < best * 0.97f) {
       best = t[2];
-      bestv = v;
+      if (lv < 0) {
+        best_split = -lv;
+      } else {
+        best_split = 0;
+        bestv = lv;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -201,6 +241,7 @@ static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, float* out_ms
   dfree(flush, st);
   if (!s.ok()) return s;
   *out_vec = bestv;
+  *out_split = best_split;
   if (out_ms) *out_ms = best;
   return Status{};
 }
@@ -209,8 +250,8 @@ Status bsr_autotune(bamg_bsr* A, float* best_ms) {
   if (!A->has_pattern) return make_status(BAMG_ERR_STATE, "autotune needs a pattern");
   const bool special = (A->br == 3 || A->br == 6) && (A->bc == 3 || A->bc == 6);
   if (!special) return Status{};
-  if (!A->vals64_stale) BAMG_TRY(tune_lanes<double>(A, A->vals, &A->vec, best_ms));
-  if (A->vals32) BAMG_TRY(tune_lanes<float>(A, A->vals32, &A->vec32, A->vals64_stale ? best_ms : nullptr));
+  if (!A->vals64_stale) BAMG_TRY(tune_lanes<double>(A, A->vals, &A->vec, &A->split, best_ms));
+  if (A->vals32) BAMG_TRY(tune_lanes<float>(A, A->vals32, &A->vec32, &A->split32, A->vals64_stale ? best_ms : nullptr));
   A->vec_tuned = true;
   return Status{};
 }

@@ -43,7 +43,7 @@ class GpuProblem:
     optional hierarchy."""
 
     def __init__(self, ne, nu=0.3, seed=None, precision=B.BAMG_FP64, max_coarse_dofs=2100, setup=True,
-                 E_el=None):
+                 E_el=None, coarse_solver=0):
         self.mesh = Mesh(ne)
         self.nu = nu
         self.ctx = B.bamg_ctx_create(torch.cuda.current_stream())
@@ -61,6 +61,7 @@ class GpuProblem:
             o.grid[0] = o.grid[1] = o.grid[2] = self.mesh.m
             o.precision = precision
             o.max_coarse_dofs = max_coarse_dofs
+            o.coarse_solver = coarse_solver
             self.mg = B.bamg_mg_setup(self.ctx, self.A, self.mesh.coords(), self.mesh.dirichlet(), o)
 
     def reassemble(self, seed):

@@ -166,6 +166,57 @@ def test_vcycle_matches_oracle(ne):
         gp.close()
 
 
+@pytest.mark.parametrize("ne", [13, 16, 20])
+@pytest.mark.parametrize("form", [1, 2])
+def test_coarsest_solve_forms_match_oracle(ne, form):
+    """Dense and banded (block-tridiagonal) coarsest factorisations give the
+    oracle's cycle; 20^3 elements has the 7^3-node coarsest level of the
+    64^3-element workload (2,058 dofs, six 352-row chunks)."""
+    h = hierarchy(ne)
+    gp = GpuProblem(ne, coarse_solver=form)
+    try:
+        rng = np.random.default_rng(100 + ne)
+        b = rng.standard_normal(gp.mesh.n_dofs)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x)
+        assert rel(x.cpu().numpy(), omg.vcycle(h, b)) <= TOL64
+        # the coarsest operator itself
+        nl = B.bamg_mg_num_levels(gp.mg)
+        Ac, _ = B.bamg_mg_get_level(gp.mg, nl - 1)
+        C = read_bsr(gp.ctx, Ac)
+        L = h.levels[-1]
+        assert rel(C.vals, L.A.vals) <= TOL64
+        # FP32 precision form on the same structure
+        if form == 2:
+            g32 = GpuProblem(ne, precision=B.BAMG_FP32, coarse_solver=form)
+            try:
+                y = torch.zeros_like(x)
+                B.bamg_vcycle(g32.ctx, g32.mg, torch.from_numpy(b).cuda(), y)
+                assert rel(y.cpu().numpy(), omg.vcycle(h, b)) < 1e-3   # FP32 cycle
+            finally:
+                g32.close()
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("ne,form", [(6, 1), (6, 2), (9, 0), (9, 1)])
+def test_one_level_cycle_is_the_exact_solve(ne, form):
+    """With a single level the cycle is the coarsest solve of the fine 3x3-block
+    operator: compare with a sparse direct solve (banded: 6 or 9 chunks)."""
+    import scipy.sparse.linalg as spla
+    _, _, A = problem(ne)
+    gp = GpuProblem(ne, max_coarse_dofs=10 ** 6, coarse_solver=form)
+    try:
+        assert B.bamg_mg_num_levels(gp.mg) == 1
+        b = np.random.default_rng(ne).standard_normal(gp.mesh.n_dofs)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), x)
+        ref = spla.spsolve(A.scalar().tocsc(), b)
+        assert rel(x.cpu().numpy(), ref) <= 1e-11
+    finally:
+        gp.close()
+
+
 @pytest.mark.parametrize("ne", [8, 24])
 def test_cg_matches_oracle(ne):
     h = hierarchy(ne)
@@ -260,18 +311,52 @@ def test_lane_choice_invariance(br, bc):
         B.bamg_bsr_coo_set_values(ctx, A, torch.from_numpy(v).cuda(), 0)
         x = rng.standard_normal(nbc * bc)
         yref = ref.scalar() @ x
-        for lanes in (1, 2, 4, 8, 16, 32):
+        choices = (1, 2, 4, 8, 16, 32) + ((-1, -2, -4) if br == 6 else ())   # < 0: component split
+        for lanes in choices:
             B.bamg_bsr_set_lanes(ctx, A, lanes)
+            assert B.bamg_bsr_get_lanes(A) == lanes
             y = torch.zeros(nbr * br, dtype=torch.float64, device="cuda")
             B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).cuda(), y)
             assert rel(y.cpu().numpy(), yref) <= 1e-14, lanes
+            y32 = torch.zeros(nbr * br, dtype=torch.float32, device="cuda")
+            B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).float().cuda(), y32, B.BAMG_FP32)
+            assert rel(y32.double().cpu().numpy(), yref) <= 1e-5, lanes
         lanes, ms = B.bamg_bsr_autotune(ctx, A)
-        assert lanes in (1, 2, 4, 8, 16, 32) and ms > 0
+        assert lanes in choices and ms > 0
         with pytest.raises(B.BamgError):
             B.bamg_bsr_set_lanes(ctx, A, 3)
+        if br == 3:
+            with pytest.raises(B.BamgError):
+                B.bamg_bsr_set_lanes(ctx, A, 0)
     finally:
         B.bamg_bsr_destroy(A)
         B.bamg_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [B.BAMG_FP64, B.BAMG_FP32])
+def test_component_split_hierarchy_gives_same_cycle(precision):
+    """The component-split kernels (6-row blocks: R, coarse A and P) change
+    only the summation order of the cycle."""
+    ne = 16
+    h = hierarchy(ne)
+    gp = GpuProblem(ne, precision=precision)
+    try:
+        b = np.random.default_rng(6).standard_normal(gp.mesh.n_dofs)
+        ys = []
+        for lanes in (1, 0):
+            B.bamg_mg_set_lanes(gp.ctx, gp.mg, lanes)
+            y = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+            B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), y)
+            ys.append(y.cpu().numpy())
+        ref = omg.vcycle(h, b)
+        tol = TOL64 if precision == B.BAMG_FP64 else 1e-3
+        assert rel(ys[1], ref) <= tol and rel(ys[0], ref) <= tol
+        assert rel(ys[1], ys[0]) <= (1e-13 if precision == B.BAMG_FP64 else 1e-5)
+        x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, torch.from_numpy(body_force(gp.mesh)).cuda(), x, 1e-8, 200)
+        assert out["converged"]
+    finally:
+        gp.close()
 
 
 def test_autotuned_hierarchy_gives_same_cycle():
