@@ -90,7 +90,14 @@ typedef enum {
   BAMG_PROF_CG_AP = 4,          /* CG product q = A p */
   BAMG_PROF_COO = 5,            /* blocked COO numeric assembly */
   BAMG_PROF_COARSE_FACTOR = 6,  /* whole coarsest-level factorisation */
-  BAMG_PROF_COUNT = 7
+  BAMG_PROF_SMOOTH_COARSE = 7,  /* pre- or post-smoothing of a level below the finest */
+  BAMG_PROF_TRANSFER = 8,       /* one restriction or prolongation */
+  BAMG_PROF_COARSE_SOLVE = 9,   /* coarsest-level solve inside a cycle */
+  BAMG_PROF_L0_VECTOR = 10,     /* finest-level smoother start, final update, precision casts */
+  BAMG_PROF_CG_XR = 11,         /* CG x, r update and residual norm */
+  BAMG_PROF_CG_VECTOR = 12,     /* CG step-length dots and direction update */
+  BAMG_PROF_REFRESH = 13,       /* smoother refresh of a level (inverses, eigen-estimate) */
+  BAMG_PROF_COUNT = 14
 } bamg_prof_slot;
 BAMG_API bamg_status bamg_ctx_profile(bamg_ctx* ctx, int enable);
 BAMG_API bamg_status bamg_ctx_profile_read(bamg_ctx* ctx, int slot, double* total_ms, int64_t* launches);
@@ -308,6 +315,9 @@ BAMG_API bamg_status bamg_mg_set_lanes(bamg_mg* mg, int lanes);
  * factor; its block-diagonal inverse (device, nbr row-major bs x bs blocks). */
 BAMG_API bamg_status bamg_mg_num_levels(const bamg_mg* mg, int* n);
 BAMG_API bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** A, bamg_bsr** P);
+/* The cached restriction R = P^T of a level (NULL on the coarsest level);
+ * owned by the hierarchy, refreshed when P changes. */
+BAMG_API bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R);
 BAMG_API bamg_status bamg_mg_get_level_scalars(const bamg_mg* mg, int level, double* lambda_max,
                                       double* omega);
 BAMG_API bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* dinv);

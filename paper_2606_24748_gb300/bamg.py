@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG
 BAMG_FP64 = 0
 BAMG_FP32 = 1
 PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
-              "coo": 5, "coarse_factor": 6}
+              "coo": 5, "coarse_factor": 6, "smooth_coarse": 7, "transfer": 8, "coarse_solve": 9,
+              "l0_vector": 10, "cg_xr": 11, "cg_vector": 12, "refresh": 13}
 
 
 class BamgError(RuntimeError):
@@ -93,6 +94,7 @@ _SIGS = {
     "bamg_mg_set_lanes": [_P, ctypes.c_int],
     "bamg_mg_num_levels": [_P, ctypes.POINTER(ctypes.c_int)],
     "bamg_mg_get_level": [_P, ctypes.c_int, _PP, _PP],
+    "bamg_mg_get_restriction": [_P, ctypes.c_int, _PP],
     "bamg_mg_get_level_scalars": [_P, ctypes.c_int, _P, _P],
     "bamg_mg_get_dinv": [_P, ctypes.c_int, _P],
     "bamg_mg_destroy": [_P],
@@ -393,6 +395,12 @@ def bamg_mg_get_level(mg, level: int):
     A, P = ctypes.c_void_p(), ctypes.c_void_p()
     _check(lib().bamg_mg_get_level(mg, int(level), ctypes.byref(A), ctypes.byref(P)), None)
     return A, (P if P.value else None)
+
+
+def bamg_mg_get_restriction(mg, level: int):
+    R = ctypes.c_void_p()
+    _check(lib().bamg_mg_get_restriction(mg, int(level), ctypes.byref(R)), None)
+    return R if R.value else None
 
 
 def bamg_mg_get_level_scalars(ctx, mg, level: int) -> tuple[float, float]:

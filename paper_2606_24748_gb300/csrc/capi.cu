@@ -63,7 +63,7 @@ void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int
   for (size_t i = 0; i < count && i < pairs.size(); ++i) {
     const ProfPair& q = pairs[i];
     if (active_ap >= 0) {
-      const int lim = q.slot == BAMG_PROF_CG_AP ? active_ap : active_vc;
+      const int lim = (q.slot == BAMG_PROF_CG_AP || q.slot == BAMG_PROF_CG_XR) ? active_ap : active_vc;
       if (q.pos >= lim) continue;
     }
     float ms = 0.f;

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* _
                                                            T* __restrict__ d, T* __restrict__ x,
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
                                                            const double* __restrict__ scal, const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
                                                            const double* __restrict__ scal, int k, int has_next,
                                                            const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restric
                                                             T* __restrict__ r, T* __restrict__ d,
                                                             const T* __restrict__ dinv, const float* __restrict__ w,
                                                             const double* __restrict__ scal, const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
                                                          const T* __restrict__ dinv, const float* __restrict__ w,
                                                          const double* __restrict__ scal, int k, int has_next,
                                                          const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   __shared__ T rs[BS][32];
   const int64_t s = blockIdx.x;
@@ -165,6 +169,7 @@ __global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict_
                                                           T* __restrict__ r, T* __restrict__ d,
                                                           const T* __restrict__ dinv, const float* __restrict__ w,
                                                           const double* __restrict__ scal, const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   __shared__ T rs[BS][32];
   const int64_t s = blockIdx.x;
@@ -193,6 +198,7 @@ __global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ 
                                                         const T* __restrict__ vals, int64_t n,
                                                         const T* __restrict__ v, T* __restrict__ y, int accumulate,
                                                         const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t s = blockIdx.x;
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BR, sub = wp / BR;
@@ -203,6 +209,7 @@ __global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ 
 
 template <typename T>
 __global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ x, const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m) x[t] += d[t];
@@ -214,6 +221,7 @@ __global__ void __launch_bounds__(kRowThreads) k_transfer(const int* __restrict_
                                                           const T* __restrict__ vals, int64_t n, int64_t nthreads,
                                                           const T* __restrict__ v, T* __restrict__ y, int accumulate,
                                                           const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
@@ -229,6 +237,7 @@ __global__ void __launch_bounds__(kRowThreads) k_transfer(const int* __restrict_
 
 template <typename TS, typename TD>
 __global__ void k_cast_done(int64_t m, const TS* __restrict__ s, TD* __restrict__ d, const int* done) {
+  pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m) d[t] = (TD)s[t];
@@ -265,23 +274,27 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   const unsigned gn = (unsigned)((L.n + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
-  { k_cheb_init<BS, T><<<gn, kRowThreads, 0, st>>>(L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; }
+  const int pw = prof_begin(mg->ctx, l == 0 ? -1 : BAMG_PROF_SMOOTH_COARSE, st);
+  const int pi = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_L0_VECTOR : -1, st);
+  { BAMG_CUDA(launch_k(k_cheb_init<BS, T>, dim3(gn), dim3(kRowThreads), st, L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; }
+  prof_end(mg->ctx, pi, st);
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
     if (BS == 6 && split_for<T>(A)) {
       BAMG_DISPATCH_VS(split_for<T>(A), {
-        k_cheb_step_split<BS, VS, T><<<(unsigned)A->nslices, 32 * BS * VS, 0, st>>>(
+        BAMG_CUDA(launch_k(k_cheb_step_split<BS, VS, T>, dim3((unsigned)A->nslices), dim3(32 * BS * VS), st, 
             A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-            k + 1 < m ? 1 : 0, done);
+            k + 1 < m ? 1 : 0, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                     k + 1 < m ? 1 : 0, done); BAMG_COUNT_LAUNCH; })
+                                                     k + 1 < m ? 1 : 0, done)); BAMG_COUNT_LAUNCH; })
     }
     prof_end(mg->ctx, pm, st);
   }
+  prof_end(mg->ctx, pw, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -297,15 +310,16 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   const int m = mg->opts.cheb_degree;
   const int split = BS == 6 ? split_for<T>(A) : 0;
   const unsigned gs = (unsigned)A->nslices;
+  const int pw = prof_begin(mg->ctx, l == 0 ? -1 : BAMG_PROF_SMOOTH_COARSE, st);
   const int pr = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_RINIT_L0 : -1, st);
   if (split) {
     BAMG_DISPATCH_VS(split, {
-      k_cheb_rinit_split<BS, VS, T><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, p.x, p.b,
-                                                                 p.r, p.d0, p.dinv, L.weights, sc, done);
+      BAMG_CUDA(launch_k(k_cheb_rinit_split<BS, VS, T>, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, p.x, p.b,
+                                                                 p.r, p.d0, p.dinv, L.weights, sc, done));
       BAMG_COUNT_LAUNCH; })
   } else {
-    BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_rinit<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
-                                                    p.d0, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; })
+    BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_rinit<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+                                                    p.d0, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; })
   }
   prof_end(mg->ctx, pr, st);
   T* d[2] = {p.d0, p.d1};
@@ -313,18 +327,21 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
     if (split) {
       BAMG_DISPATCH_VS(split, {
-        k_cheb_step_split<BS, VS, T><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
+        BAMG_CUDA(launch_k(k_cheb_step_split<BS, VS, T>, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
                                                                   d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                                  1, done);
+                                                                  1, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { k_cheb_step<BS, V, T><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
-                                                     d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done); BAMG_COUNT_LAUNCH; })
+      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+                                                     d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done)); BAMG_COUNT_LAUNCH; })
     }
     prof_end(mg->ctx, pm, st);
   }
   const int64_t mm = L.n * BS;
-  { k_axpy_done<T><<<(unsigned)((mm + 255) / 256), 256, 0, st>>>(mm, d[(m - 1) & 1], p.x, done); BAMG_COUNT_LAUNCH; }
+  const int pa = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_L0_VECTOR : -1, st);
+  { BAMG_CUDA(launch_k(k_axpy_done<T>, dim3((unsigned)((mm + 255) / 256)), dim3(256), st, mm, d[(m - 1) & 1], p.x, done)); BAMG_COUNT_LAUNCH; }
+  prof_end(mg->ctx, pa, st);
+  prof_end(mg->ctx, pw, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -336,16 +353,26 @@ static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int a
   if (rows == 0) return Status{};
   if (BR == 6 && split_for<T>(M)) {
     BAMG_DISPATCH_VS(split_for<T>(M), {
-      k_transfer_split<BR, BC, VS, T><<<(unsigned)M->nslices, 32 * BR * VS, 0, st>>>(M->slice_ptr, M->sell_col, vals,
-                                                                                     M->nbr, v, y, accumulate, done);
+      BAMG_CUDA(launch_k(k_transfer_split<BR, BC, VS, T>, dim3((unsigned)M->nslices), dim3(32 * BR * VS), st, M->slice_ptr, M->sell_col, vals,
+                                                                                     M->nbr, v, y, accumulate, done));
       BAMG_COUNT_LAUNCH; })
     BAMG_CUDA(cudaGetLastError());
     return Status{};
   }
-  BAMG_DISPATCH_V(lanes_for<T>(M), { k_transfer<BR, BC, V, T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(
-      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done); BAMG_COUNT_LAUNCH; })
+  BAMG_DISPATCH_V(lanes_for<T>(M), { BAMG_CUDA(launch_k(k_transfer<BR, BC, V, T>, dim3((unsigned)((rows + kRowThreads - 1) / kRowThreads)), dim3(kRowThreads), st, 
+      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done)); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};
+}
+
+// Restriction (accumulate = 0) or prolongation (1) inside a profiling region.
+template <int BR, int BC, typename T>
+static Status transfer_prof(bamg_mg* mg, const bamg_bsr* M, const T* vals, const T* v, T* y, int accumulate,
+                            const int* done, cudaStream_t st) {
+  const int pt = prof_begin(mg->ctx, BAMG_PROF_TRANSFER, st);
+  Status s = transfer<BR, BC, T>(M, vals, v, y, accumulate, done, st);
+  prof_end(mg->ctx, pt, st);
+  return s;
 }
 
 template <typename T>
@@ -358,25 +385,27 @@ Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
     auto pc = level_ptrs<T>(C);
     if (L.bs == 3) {
       BAMG_TRY((smooth_down<3, T>(mg, l, done, st)));
-      BAMG_TRY((transfer<6, 3, T>(L.R, p.Rvals, p.r, pc.b, 0, done, st)));
+      BAMG_TRY((transfer_prof<6, 3, T>(mg, L.R, p.Rvals, p.r, pc.b, 0, done, st)));
     } else {
       BAMG_TRY((smooth_down<6, T>(mg, l, done, st)));
-      BAMG_TRY((transfer<6, 6, T>(L.R, p.Rvals, p.r, pc.b, 0, done, st)));
+      BAMG_TRY((transfer_prof<6, 6, T>(mg, L.R, p.Rvals, p.r, pc.b, 0, done, st)));
     }
   }
   {
     auto p = level_ptrs<T>(mg->levels[nl - 1]);
+    const int pc = prof_begin(mg->ctx, BAMG_PROF_COARSE_SOLVE, st);
     BAMG_TRY(coarse_apply<T>(mg, p.b, p.x, done, st));
+    prof_end(mg->ctx, pc, st);
   }
   for (int l = nl - 2; l >= 0; --l) {
     Level& L = mg->levels[l];
     auto p = level_ptrs<T>(L);
     auto pc = level_ptrs<T>(mg->levels[l + 1]);
     if (L.bs == 3) {
-      BAMG_TRY((transfer<3, 6, T>(L.P, p.Pvals, pc.x, p.x, 1, done, st)));
+      BAMG_TRY((transfer_prof<3, 6, T>(mg, L.P, p.Pvals, pc.x, p.x, 1, done, st)));
       BAMG_TRY((smooth_up<3, T>(mg, l, done, st)));
     } else {
-      BAMG_TRY((transfer<6, 6, T>(L.P, p.Pvals, pc.x, p.x, 1, done, st)));
+      BAMG_TRY((transfer_prof<6, 6, T>(mg, L.P, p.Pvals, pc.x, p.x, 1, done, st)));
       BAMG_TRY((smooth_up<6, T>(mg, l, done, st)));
     }
   }
@@ -403,13 +432,17 @@ static Status precond(bamg_mg* mg, const double* r, double* z, const int* done, 
   const int64_t m = L0.n * L0.bs;
   const unsigned g = (unsigned)((m + 255) / 256);
   if (mg->opts.precision == BAMG_FP32) {
-    { k_cast_done<double, float><<<g, 256, 0, st>>>(m, r, L0.b32, done); BAMG_COUNT_LAUNCH; }
+    int pc = prof_begin(mg->ctx, BAMG_PROF_L0_VECTOR, st);
+    { BAMG_CUDA(launch_k(k_cast_done<double, float>, dim3(g), dim3(256), st, m, r, L0.b32, done)); BAMG_COUNT_LAUNCH; }
+    prof_end(mg->ctx, pc, st);
     BAMG_TRY(vcycle_on<float>(mg, done, st));
-    { k_cast_done<float, double><<<g, 256, 0, st>>>(m, L0.x32, z, done); BAMG_COUNT_LAUNCH; }
+    pc = prof_begin(mg->ctx, BAMG_PROF_L0_VECTOR, st);
+    { BAMG_CUDA(launch_k(k_cast_done<float, double>, dim3(g), dim3(256), st, m, L0.x32, z, done)); BAMG_COUNT_LAUNCH; }
+    prof_end(mg->ctx, pc, st);
   } else {
-    if (r != L0.b) { k_cast_done<double, double><<<g, 256, 0, st>>>(m, r, L0.b, done); BAMG_COUNT_LAUNCH; }
+    if (r != L0.b) { BAMG_CUDA(launch_k(k_cast_done<double, double>, dim3(g), dim3(256), st, m, r, L0.b, done)); BAMG_COUNT_LAUNCH; }
     BAMG_TRY(vcycle_on<double>(mg, done, st));
-    if (z != L0.x) { k_cast_done<double, double><<<g, 256, 0, st>>>(m, L0.x, z, done); BAMG_COUNT_LAUNCH; }
+    if (z != L0.x) { BAMG_CUDA(launch_k(k_cast_done<double, double>, dim3(g), dim3(256), st, m, L0.x, z, done)); BAMG_COUNT_LAUNCH; }
   }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
@@ -420,6 +453,7 @@ Status mg_precond(bamg_mg* mg, const double* r, double* z, cudaStream_t st) { re
 // ------------------------------------------------------------------ CG
 
 __global__ void k_cg_setup(CgState* s, double rtol, int maxit) {
+  pdl_enter();
   s->bnorm2 = 0.0;
   s->rtol2 = rtol * rtol;
   s->rz = s->pq = s->alpha = s->beta = s->rnorm2 = 0.0;
@@ -431,6 +465,7 @@ __global__ void k_cg_setup(CgState* s, double rtol, int maxit) {
 // r = b, x = 0, ||b||^2
 __global__ void k_cg_init(int64_t m, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ x,
                           CgState* s, double* partials, unsigned* counter) {
+  pdl_enter();
   double local[1] = {0.0};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
     const double v = b[t];
@@ -453,6 +488,7 @@ __global__ void k_cg_init(int64_t m, const double* __restrict__ b, double* __res
 __global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double* __restrict__ z,
                            double* __restrict__ p, double* __restrict__ zold, CgState* s, double* partials,
                            unsigned* counter) {
+  pdl_enter();
   if (s->done) return;
   double local[1] = {0.0};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
@@ -471,6 +507,7 @@ __global__ void __launch_bounds__(256) k_cg_Ap(const int* __restrict__ sp, const
                                                        const double* __restrict__ vals, int64_t n, int64_t nthreads,
                                                        const double* __restrict__ p, double* __restrict__ q,
                                                        CgState* s, double* partials, unsigned* counter) {
+  pdl_enter();
   if (s->done) return;
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -504,6 +541,7 @@ __global__ void __launch_bounds__(256) k_cg_Ap(const int* __restrict__ sp, const
 __global__ void k_cg_xr(int64_t m, const double* __restrict__ p, const double* __restrict__ q,
                         double* __restrict__ x, double* __restrict__ r, CgState* s, double* partials,
                         unsigned* counter) {
+  pdl_enter();
   if (s->done) return;
   const double alpha = s->alpha;
   double local[1] = {0.0};
@@ -532,6 +570,7 @@ __global__ void k_cg_xr(int64_t m, const double* __restrict__ p, const double* _
 // beta = r.(z - z_old) / rz (Polak-Ribiere), rz = r.z
 __global__ void k_cg_dots(int64_t m, const double* __restrict__ r, const double* __restrict__ z,
                           const double* __restrict__ zold, CgState* s, double* partials, unsigned* counter) {
+  pdl_enter();
   if (s->done) return;
   double local[2] = {0.0, 0.0};
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
@@ -549,6 +588,7 @@ __global__ void k_cg_dots(int64_t m, const double* __restrict__ r, const double*
 // p = z + beta p, z_old = z
 __global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restrict__ p, double* __restrict__ zold,
                        const CgState* s) {
+  pdl_enter();
   if (s->done) return;
   const double beta = s->beta;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
@@ -565,6 +605,7 @@ __global__ void __launch_bounds__(256) k_true_residual(const int* __restrict__ s
                                                                int64_t nthreads, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* out_norm2,
                                                                double* partials, unsigned* counter) {
+  pdl_enter();
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
@@ -602,13 +643,17 @@ static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   CgState* s = mg->cg;
   const int* done = &s->done;
   const int pa = prof_begin(ctx, BAMG_PROF_CG_AP, st);
-  BAMG_DISPATCH_V(A->vec, { k_cg_Ap<V><<<row_grid(rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
-                                                  ctx->d_partials, ctx->d_counters + 2); BAMG_COUNT_LAUNCH; })
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_cg_Ap<V>, dim3(row_grid(rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+                                                  ctx->d_partials, ctx->d_counters + 2)); BAMG_COUNT_LAUNCH; })
   prof_end(ctx, pa, st);
-  { k_cg_xr<<<vec_grid(m), 256, 0, st>>>(m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3); BAMG_COUNT_LAUNCH; }
+  const int px = prof_begin(ctx, BAMG_PROF_CG_XR, st);
+  { BAMG_CUDA(launch_k(k_cg_xr, dim3(vec_grid(m)), dim3(256), st, m, mg->cp, mg->cq, mg->cx, r, s, ctx->d_partials, ctx->d_counters + 3)); BAMG_COUNT_LAUNCH; }
+  prof_end(ctx, px, st);
   BAMG_TRY(precond(mg, r, z, done, st));
-  { k_cg_dots<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->czold, s, ctx->d_partials, ctx->d_counters + 4); BAMG_COUNT_LAUNCH; }
-  { k_cg_p<<<vec_grid(m), 256, 0, st>>>(m, z, mg->cp, mg->czold, s); BAMG_COUNT_LAUNCH; }
+  const int pv = prof_begin(ctx, BAMG_PROF_CG_VECTOR, st);
+  { BAMG_CUDA(launch_k(k_cg_dots, dim3(vec_grid(m)), dim3(256), st, m, r, z, mg->czold, s, ctx->d_partials, ctx->d_counters + 4)); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_cg_p, dim3(vec_grid(m)), dim3(256), st, m, z, mg->cp, mg->czold, s)); BAMG_COUNT_LAUNCH; }
+  prof_end(ctx, pv, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -641,7 +686,7 @@ static Status cg_graph(bamg_mg* mg, double* r, double* z) {
   mg->cg_pairs_used.assign(ng, 0);
   if (ctx->prof.on)
     for (auto& v : mg->cg_pairs) {
-      v.resize(16);
+      v.resize(64);
       for (auto& q : v) {
         BAMG_CUDA(cudaEventCreate(&q.a));
         BAMG_CUDA(cudaEventCreate(&q.b));
@@ -704,10 +749,10 @@ Status cg_prologue(bamg_mg* mg, const double* b, double rtol, int maxit, cudaStr
   const int64_t m = mg->levels[0].n * 3;
   double *r = cg_r(mg), *z = cg_z(mg);
   CgState* s = mg->cg;
-  { k_cg_setup<<<1, 1, 0, st>>>(s, rtol, maxit); BAMG_COUNT_LAUNCH; }
-  { k_cg_init<<<vec_grid(m), 256, 0, st>>>(m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_cg_setup, dim3(1), dim3(1), st, s, rtol, maxit)); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_cg_init, dim3(vec_grid(m)), dim3(256), st, m, b, r, mg->cx, s, ctx->d_partials, ctx->d_counters + 5)); BAMG_COUNT_LAUNCH; }
   BAMG_TRY(precond(mg, r, z, &s->done, st));
-  { k_cg_first<<<vec_grid(m), 256, 0, st>>>(m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_cg_first, dim3(vec_grid(m)), dim3(256), st, m, r, z, mg->cp, mg->czold, s, ctx->d_partials, ctx->d_counters + 6)); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -721,8 +766,8 @@ Status cg_epilogue(bamg_mg* mg, const double* b, double* x, double* true_r2, cud
   if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   const bamg_bsr* A = L0.A;
   const int64_t rows = row_threads(A);
-  BAMG_DISPATCH_V(A->vec, { k_true_residual<V><<<row_grid(rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
-                                                          true_r2, ctx->d_partials, ctx->d_counters + 7); BAMG_COUNT_LAUNCH; })
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_true_residual<V>, dim3(row_grid(rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+                                                          true_r2, ctx->d_partials, ctx->d_counters + 7)); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }

@@ -117,21 +117,34 @@ __device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __r
     }
     __syncthreads();
   }
-  // rows of W = L^-1 one at a time; 8 threads per column split the dot product
-  const int c = tid >> 3, part = tid & 7;
-  for (int r = 0; r < kT; ++r) {
-    double t = 0.0;
-    if (c < r)
-      for (int l = c + part; l < r; l += 8) t = fma(a[r][l], w[l][c], t);
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (part == 0) w[r][c] = (c <= r) ? (((r == c) ? 1.0 : 0.0) - t) * inv[r] : 0.0;
+  // W = L^-1 by doubling the inverted diagonal blocks: with diagonal blocks
+  // W11, W22 of size h already inverted, the block below them is
+  // W21 = -W22 L21 W11, formed for every pair at once (two products, 2 h^3
+  // multiply-adds per pair) for h = 1, 2, 4, 8, 16.  T = L21 W11 is kept
+  // transposed in the (unused) upper triangle of the pair's block.
+  if (tid < kT) w[tid][tid] = inv[tid];
+  __syncthreads();
+  for (int h = 1; h < kT; h *= 2) {
+    const int hh = h * h;
+    for (int e = tid; e < (kT / 2) * h; e += blockDim.x) {  // (kT / 2h) pairs x h^2 entries
+      const int i0 = (e / hh) * 2 * h, m = (e % hh) / h, q = e % h;
+      double t = 0.0;
+      for (int n = q; n < h; ++n) t = fma(a[i0 + h + m][i0 + n], w[i0 + n][i0 + q], t);
+      w[i0 + q][i0 + h + m] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < (kT / 2) * h; e += blockDim.x) {
+      const int i0 = (e / hh) * 2 * h, p = (e % hh) / h, q = e % h;
+      double t = 0.0;
+      for (int m = 0; m <= p; ++m) t = fma(w[i0 + h + p][i0 + h + m], w[i0 + q][i0 + h + m], t);
+      w[i0 + h + p][i0 + q] = -t;
+    }
     __syncthreads();
   }
   for (int e = tid; e < kT * kT; e += blockDim.x) {
     const int i = e / kT, l = e % kT;
     base[(int64_t)i * ld + l] = l <= i ? a[i][l] : 0.0;
-    Linv[e] = w[i][l];
+    Linv[e] = l <= i ? w[i][l] : 0.0;
   }
 }
 
@@ -249,6 +262,7 @@ __global__ void k_transpose_dense(const double* __restrict__ S, double* __restri
 template <typename TI, typename TO>
 __global__ void k_tri_mv(const double* __restrict__ Wm, int64_t ld, int64_t n, const TI* __restrict__ v,
                          TO* __restrict__ out, int lower, const int* done) {
+  pdl_enter();
   if (done && *done) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -265,6 +279,7 @@ __global__ void k_tri_mv(const double* __restrict__ Wm, int64_t ld, int64_t n, c
 template <int KP, typename TI, typename TO>
 __global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, const TI* __restrict__ v,
                          TO* __restrict__ out, int lower, const int* done) {
+  pdl_enter();
   if (done && *done) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -371,6 +386,7 @@ __global__ void k_band_pad(double* __restrict__ D, int64_t n, int64_t npad, int 
 template <int KP, typename TI>
 __global__ void k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows, const TI* __restrict__ v,
                            int64_t nvalid, double* __restrict__ out, const int* done) {
+  pdl_enter();
   if (done && *done) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -398,6 +414,7 @@ __global__ void k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows,
 template <int KP>
 __global__ void k_chunk_chain(const double* __restrict__ M, int s, const double* __restrict__ z,
                               double* __restrict__ y, const int* done) {
+  pdl_enter();
   if (done && *done) return;
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -420,6 +437,7 @@ __global__ void k_chunk_chain(const double* __restrict__ M, int s, const double*
 
 template <typename TO>
 __global__ void k_band_out(int64_t m, const double* __restrict__ x, TO* __restrict__ out, const int* done) {
+  pdl_enter();
   if (done && *done) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < m) out[t] = (TO)x[t];
@@ -505,21 +523,21 @@ static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, co
   const int s = D.s, nc = D.nc;
   const int64_t ss = (int64_t)s * s, npad = D.npad;
   // forward: y = blockdiag(W) b, then y_k -= M_k y_{k-1}
-  { k_chunk_mv<KP, T><<<warps_grid(npad), 256, 0, st>>>(D.Wb, s, npad, b, D.n, y, done); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_chunk_mv<KP, T>, dim3(warps_grid(npad)), dim3(256), st, D.Wb, s, npad, b, D.n, y, done)); BAMG_COUNT_LAUNCH; }
   for (int k = 1; k < nc; ++k) {
-    k_chunk_chain<KP><<<warps_grid(s), 256, 0, st>>>(D.Mb + k * ss, s, y + (int64_t)(k - 1) * s * KP,
-                                                     y + (int64_t)k * s * KP, done);
+    BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s)), dim3(256), st, D.Mb + k * ss, s, y + (int64_t)(k - 1) * s * KP,
+                                                     y + (int64_t)k * s * KP, done));
     BAMG_COUNT_LAUNCH;
   }
   // backward: z = blockdiag(W^T) y, then z_k -= N_k z_{k+1}
-  { k_chunk_mv<KP, double><<<warps_grid(npad), 256, 0, st>>>(D.Wtb, s, npad, y, npad, z, done); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_chunk_mv<KP, double>, dim3(warps_grid(npad)), dim3(256), st, D.Wtb, s, npad, y, npad, z, done)); BAMG_COUNT_LAUNCH; }
   for (int k = nc - 2; k >= 0; --k) {
-    k_chunk_chain<KP><<<warps_grid(s), 256, 0, st>>>(D.Nb + k * ss, s, z + (int64_t)(k + 1) * s * KP,
-                                                     z + (int64_t)k * s * KP, done);
+    BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s)), dim3(256), st, D.Nb + k * ss, s, z + (int64_t)(k + 1) * s * KP,
+                                                     z + (int64_t)k * s * KP, done));
     BAMG_COUNT_LAUNCH;
   }
   const int64_t m = D.n * KP;
-  { k_band_out<T><<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, z, x, done); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_band_out<T>, dim3((unsigned)((m + 255) / 256)), dim3(256), st, m, z, x, done)); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -610,8 +628,8 @@ Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t
   if (D.nc > 0) return band_apply<1, T>(mg, b, x, D.b64, D.x64, done, st);
   const int64_t n = D.n;
   const unsigned g = (unsigned)((n * 32 + 255) / 256);
-  { k_tri_mv<T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, D.x64, 1, done); BAMG_COUNT_LAUNCH; }
-  { k_tri_mv<double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, D.x64, x, 0, done); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_tri_mv<T, double>, dim3(g), dim3(256), st, D.M, D.npad, n, b, D.x64, 1, done)); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_tri_mv<double, T>, dim3(g), dim3(256), st, D.Wt, D.npad, n, D.x64, x, 0, done)); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -626,8 +644,8 @@ Status coarse_apply_multi(bamg_mg* mg, int kp, const T* b, T* x, double* work, c
   if (kp == KP) {                                                                                          \
     if (D.nc > 0) return band_apply<KP, T>(mg, b, x, y, z, done, st);                                     \
     const unsigned g = (unsigned)((n * 32 + 255) / 256);                                                   \
-    { k_tri_mm<KP, T, double><<<g, 256, 0, st>>>(D.M, D.npad, n, b, y, 1, done); BAMG_COUNT_LAUNCH; }      \
-    { k_tri_mm<KP, double, T><<<g, 256, 0, st>>>(D.Wt, D.npad, n, y, x, 0, done); BAMG_COUNT_LAUNCH; }     \
+    { BAMG_CUDA(launch_k(k_tri_mm<KP, T, double>, dim3(g), dim3(256), st, D.M, D.npad, n, b, y, 1, done)); BAMG_COUNT_LAUNCH; }      \
+    { BAMG_CUDA(launch_k(k_tri_mm<KP, double, T>, dim3(g), dim3(256), st, D.Wt, D.npad, n, y, x, 0, done)); BAMG_COUNT_LAUNCH; }     \
     BAMG_CUDA(cudaGetLastError());                                                                         \
     return Status{};                                                                                       \
   }

@@ -695,7 +695,9 @@ Status mg_update_impl(bamg_mg* mg) {
   }
   for (int l = 0; l + 1 < nl; ++l) {
     BAMG_TRY(mg_refresh_restriction(mg, l));
+    const int pr = prof_begin(mg->ctx, BAMG_PROF_REFRESH, mg->ctx->stream);
     BAMG_TRY(mg_refresh_level(mg, l));
+    prof_end(mg->ctx, pr, mg->ctx->stream);
   }
   if (pp == BAMG_FP32) {
     BAMG_TRY(bsr_ensure_fp32(mg->levels[0].A));
@@ -822,6 +824,12 @@ bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** A, bamg_b
   if (!mg || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
   if (A) *A = mg->levels[level].A;
   if (P) *P = mg->levels[level].P;
+  return BAMG_OK;
+}
+
+bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R) {
+  if (!mg || !R || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
+  *R = mg->levels[level].R;
   return BAMG_OK;
 }
 
