@@ -122,6 +122,7 @@ void bsr_release(bamg_bsr* A) {
   dfree(A->sell_col, st);
   dfree(A->slot_of, st);
   dfree(A->diag_slot, st);
+  dfree(A->slot_row, st);
   dfree(A->vals, st);
   dfree(A->vals32, st);
   dfree(A->coo_perm, st);
@@ -136,17 +137,28 @@ void bsr_release(bamg_bsr* A) {
   A->h_slot_of.clear();
 }
 
-Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx) {
+Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, bool sort_rows) {
   cudaStream_t st = A->ctx->stream;
   const int64_t nbr = A->nbr;
   if ((int64_t)rowptr.size() != nbr + 1) return make_status(BAMG_ERR_INVALID, "rowptr size");
   A->nnzb = rowptr[nbr];
   A->nslices = (nbr + kSlice - 1) / kSlice;
+  // row of each row position (identity, or sorted by decreasing length within
+  // windows of 1,024 rows; padding positions past nbr stay at the end)
+  std::vector<int> order((size_t)A->nslices * kSlice);
+  for (size_t r = 0; r < order.size(); ++r) order[r] = (int64_t)r < nbr ? (int)r : -1;
+  auto len = [&](int i) { return i < 0 ? -1 : rowptr[i + 1] - rowptr[i]; };
+  if (sort_rows) {
+    constexpr size_t kWindow = 1024;
+    for (size_t w0 = 0; w0 < order.size(); w0 += kWindow) {
+      const size_t w1 = std::min(order.size(), w0 + kWindow);
+      std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) { return len(a) > len(b); });
+    }
+  }
   std::vector<int> sp(A->nslices + 1, 0);
   for (int64_t s = 0; s < A->nslices; ++s) {
     int w = 0;
-    for (int64_t i = s * kSlice; i < std::min<int64_t>(nbr, (s + 1) * kSlice); ++i)
-      w = std::max(w, rowptr[i + 1] - rowptr[i]);
+    for (int64_t r = s * kSlice; r < (s + 1) * kSlice; ++r) w = std::max(w, len(order[r]));
     sp[s + 1] = sp[s] + w;
   }
   A->nchunks = sp[A->nslices];
@@ -155,14 +167,16 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   std::vector<int> scol((size_t)A->nchunks * kSlice, 0);
   std::vector<int> slot_of((size_t)A->nnzb);
   std::vector<int> diag(A->br == A->bc ? (size_t)nbr : 0, -1);
-  for (int64_t i = 0; i < nbr; ++i) {
-    const int64_t s = i / kSlice, l = i % kSlice;
-    const int len = rowptr[i + 1] - rowptr[i];
+  for (int64_t r = 0; r < (int64_t)order.size(); ++r) {
+    const int i = order[r];
+    if (i < 0) continue;
+    const int64_t s = r / kSlice, l = r % kSlice;
+    const int n_i = rowptr[i + 1] - rowptr[i];
     const int w = sp[s + 1] - sp[s];
-    const int pad_col = len > 0 ? colidx[rowptr[i + 1] - 1] : 0;
+    const int pad_col = n_i > 0 ? colidx[rowptr[i + 1] - 1] : 0;
     for (int t = 0; t < w; ++t) {
       const int64_t slot = (int64_t)(sp[s] + t) * kSlice + l;
-      if (t < len) {
+      if (t < n_i) {
         const int k = rowptr[i] + t;
         scol[slot] = colidx[k];
         slot_of[k] = (int)slot;
@@ -182,8 +196,10 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   dfree(A->sell_col, st);
   dfree(A->slot_of, st);
   dfree(A->diag_slot, st);
+  dfree(A->slot_row, st);
   dfree(A->vals, st);
   dfree(A->vals32, st);
+  if (sort_rows) BAMG_TRY(upload(&A->slot_row, order, st));
   BAMG_TRY(upload(&A->rowptr, A->h_rowptr, st));
   BAMG_TRY(upload(&A->colidx, A->h_colidx, st));
   BAMG_TRY(upload(&A->slice_ptr, sp, st));

@@ -195,16 +195,16 @@ __global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict_
 
 template <int BR, int BC, int VS, typename T>
 __global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ sp, const int* __restrict__ col,
-                                                        const T* __restrict__ vals, int64_t n,
-                                                        const T* __restrict__ v, T* __restrict__ y, int accumulate,
-                                                        const int* done) {
+                                                        const T* __restrict__ vals, const int* __restrict__ srow,
+                                                        int64_t n, const T* __restrict__ v, T* __restrict__ y,
+                                                        int accumulate, const int* done) {
   pdl_enter();
   BAMG_DONE_RETURN
   const int64_t s = blockIdx.x;
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BR, sub = wp / BR;
-  const int64_t i = s * 32 + lane;
+  const int64_t i = srow ? (int64_t)srow[s * 32 + lane] : s * 32 + lane;
   const T acc = row_component<BR, BC, VS, T, T, T>(sp, col, vals, v, s, lane, a, sub);
-  if (sub == 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
+  if (sub == 0 && i >= 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
 }
 
 template <typename T>
@@ -218,19 +218,20 @@ __global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ 
 // y = M v (restriction with R = P^T), or y += M v (prolongation with P)
 template <int BR, int BC, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_transfer(const int* __restrict__ sp, const int* __restrict__ col,
-                                                          const T* __restrict__ vals, int64_t n, int64_t nthreads,
-                                                          const T* __restrict__ v, T* __restrict__ y, int accumulate,
-                                                          const int* done) {
+                                                          const T* __restrict__ vals, const int* __restrict__ srow,
+                                                          int64_t n, int64_t nthreads, const T* __restrict__ v,
+                                                          T* __restrict__ y, int accumulate, const int* done) {
   pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
-  int64_t i;
+  int64_t r;
   int sub;
-  row_of_thread<V>(t, i, sub);
+  row_of_thread<V>(t, r, sub);
   T acc[BR];
-  row_product<BR, BC, V, T, T, T>(sp, col, vals, v, i, sub, acc);
-  if (sub != 0 || i >= n) return;
+  row_product<BR, BC, V, T, T, T>(sp, col, vals, v, r, sub, acc);
+  const int64_t i = srow ? (int64_t)srow[r] : r;  // row position -> block row (sorted slices)
+  if (sub != 0 || i < 0 || i >= n) return;
 #pragma unroll
   for (int a = 0; a < BR; ++a) y[i * BR + a] = accumulate ? y[i * BR + a] + acc[a] : acc[a];
 }
@@ -354,13 +355,13 @@ static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int a
   if (BR == 6 && split_for<T>(M)) {
     BAMG_DISPATCH_VS(split_for<T>(M), {
       BAMG_CUDA(launch_k(k_transfer_split<BR, BC, VS, T>, dim3((unsigned)M->nslices), dim3(32 * BR * VS), st, M->slice_ptr, M->sell_col, vals,
-                                                                                     M->nbr, v, y, accumulate, done));
+                                                                                     M->slot_row, M->nbr, v, y, accumulate, done));
       BAMG_COUNT_LAUNCH; })
     BAMG_CUDA(cudaGetLastError());
     return Status{};
   }
   BAMG_DISPATCH_V(lanes_for<T>(M), { BAMG_CUDA(launch_k(k_transfer<BR, BC, V, T>, dim3((unsigned)((rows + kRowThreads - 1) / kRowThreads)), dim3(kRowThreads), st, 
-      M->slice_ptr, M->sell_col, vals, M->nbr, rows, v, y, accumulate, done)); BAMG_COUNT_LAUNCH; })
+      M->slice_ptr, M->sell_col, vals, M->slot_row, M->nbr, rows, v, y, accumulate, done)); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }

@@ -94,6 +94,8 @@ struct bamg_bsr {
   int* sell_col = nullptr;   // 32 * nchunks
   int* slot_of = nullptr;    // nnzb: CSR block -> slot
   int* diag_slot = nullptr;  // nbr (square blocks only, -1 if no diagonal block)
+  int* slot_row = nullptr;   // sorted slices: block row of each of the 32 * nslices row positions
+                             // (-1 = padding); null when row position = row
   bool all_diag = false;     // every block row has its diagonal block
   int vec = 1;               // lanes per block row of the FP64 row kernels (1..32, power of 2)
   int vec32 = 1;             // the same for kernels reading the FP32 copy
@@ -331,7 +333,11 @@ void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int
 // ------------------------------------------------------------ pattern helpers
 // Build the sliced form (and device/host CSR copies) from a host CSR pattern;
 // allocates zeroed values.  Used by COO preallocation and the Galerkin symbolic.
-Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx);
+// sort_rows: place the rows in the slices by decreasing length within
+// windows of 1,024 rows (sliced ELL with sorting), so that rows of equal
+// length share slices and little padding is stored; kernels then map each
+// row position to its row through slot_row.
+Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, bool sort_rows = false);
 Status bsr_ensure_fp32(bamg_bsr* A);   // refresh vals32 if the version changed
 void bsr_release(bamg_bsr* A);
 

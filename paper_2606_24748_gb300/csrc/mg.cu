@@ -235,7 +235,7 @@ __global__ void k_start_vector(double* __restrict__ v, int64_t n) {
 // One power step w_out = D^-1 A (w_in / ||w_in||) with D the block diagonal
 // (dinv) or the scalar diagonal; ||w_out|| goes to *norm_out.
 template <int BS, int V, typename TM>
-__global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restrict__ slice_ptr,
+__global__ void __launch_bounds__(256) k_power_step(const int* __restrict__ slice_ptr,
                                                             const int* __restrict__ col, const TM* __restrict__ vals,
                                                             const int* __restrict__ diag_slot,
                                                             const double* __restrict__ dinv, int scalar_diag,
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kRowThreads) k_power_step(const int* __restric
 // Rayleigh quotient w^T A w / w^T D w; in block mode also the Chebyshev data
 // for the interval [lower, upper] * lambda (Saad, Alg. 12.1 coefficients).
 template <int BS, int V, typename TM>
-__global__ void __launch_bounds__(kRowThreads) k_rayleigh(const int* __restrict__ slice_ptr,
+__global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const TM* __restrict__ vals,
                                                           const int* __restrict__ diag_slot, int scalar_diag,
                                                           const float* __restrict__ wts,
@@ -340,8 +340,10 @@ __global__ void __launch_bounds__(kRowThreads) k_rayleigh(const int* __restrict_
   }
 }
 
+// 256-thread CTAs: one thread per row of the fine operator fits in the 1,216
+// CTAs of the reduction partials.
 static unsigned red_grid(int64_t rows) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kRowThreads - 1) / kRowThreads, 1216));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 1216));
 }
 
 template <int BS, typename TM>
@@ -356,11 +358,11 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
   { k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS); BAMG_COUNT_LAUNCH; }
   for (int it = 0; it < mg->opts.power_its; ++it) {
     const double* nin = it == 0 ? nullptr : norms + ((it + 1) & 1);
-    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
+    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, scalar_diag ? nullptr : wts, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
-  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<g, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
+  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
                                                 scalar_diag ? nullptr : wts, w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
                                                 mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
@@ -632,7 +634,7 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       std::vector<int> zrow(zc.size());
       for (int64_t i = 0; i < L.n; ++i)
         for (int z = zr[i]; z < zr[i + 1]; ++z) zrow[z] = (int)i;
-      BAMG_TRY(bsr_set_pattern(P, std::move(zr), std::move(zc)));
+      BAMG_TRY(bsr_set_pattern(P, std::move(zr), std::move(zc), true));  // rows of 1..8 blocks: sorted slices
       BAMG_TRY(upload(&L.zrow, zrow, st));
       BAMG_TRY(upload(&L.agg, agg, st));
       BAMG_TRY(upload(&L.q, Q, st));

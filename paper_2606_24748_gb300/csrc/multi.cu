@@ -159,15 +159,16 @@ __global__ void __launch_bounds__(256) k_mcheb_rinit(const int* __restrict__ sp,
 // y = M v, or y += M v
 template <int BR, int BC, typename T>
 __global__ void __launch_bounds__(256) k_mtransfer(const int* __restrict__ sp, const int* __restrict__ col,
-                                                   const T* __restrict__ vals, int64_t n, int glog, int kp,
-                                                   const T* __restrict__ v, T* __restrict__ y, int accumulate,
-                                                   const int* done) {
+                                                   const T* __restrict__ vals, const int* __restrict__ srow,
+                                                   int64_t n, int glog, int kp, const T* __restrict__ v,
+                                                   T* __restrict__ y, int accumulate, const int* done) {
   BAMG_DONE_RETURN
-  int64_t i;
+  int64_t pos;
   int c0;
-  if (!row_cols(n, glog, i, c0)) return;
+  if (!row_cols(n, glog, pos, c0)) return;
   T acc[BR][4];
-  row_product4<BR, BC, T>(sp, col, vals, v, kp, i, c0, acc);
+  row_product4<BR, BC, T>(sp, col, vals, v, kp, pos, c0, acc);
+  const int64_t i = srow ? (int64_t)srow[pos] : pos;  // row position -> block row (sorted slices)
 #pragma unroll
   for (int a = 0; a < BR; ++a) {
     const int64_t o = (i * BR + a) * kp + c0;
@@ -511,8 +512,8 @@ Status mtransfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int kp, int
                  cudaStream_t st) {
   if (M->nbr == 0) return Status{};
   const int glog = ilog2(kp / 4);
-  { k_mtransfer<BR, BC, T><<<grid_for(M->nbr << glog), 256, 0, st>>>(M->slice_ptr, M->sell_col, vals, M->nbr, glog, kp,
-                                                                  v, y, accumulate, done); BAMG_COUNT_LAUNCH; }
+  { k_mtransfer<BR, BC, T><<<grid_for(M->nbr << glog), 256, 0, st>>>(M->slice_ptr, M->sell_col, vals, M->slot_row,
+                                                                  M->nbr, glog, kp, v, y, accumulate, done); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }

@@ -10,16 +10,17 @@ namespace bamg {
 template <int BR, int BC, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_spmv(const int* __restrict__ slice_ptr,
                                                       const int* __restrict__ col, const T* __restrict__ vals,
-                                                      const T* __restrict__ x, T* __restrict__ y, int64_t nbr,
-                                                      int64_t nthreads) {
+                                                      const int* __restrict__ srow, const T* __restrict__ x,
+                                                      T* __restrict__ y, int64_t nbr, int64_t nthreads) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
-  int64_t row;
+  int64_t pos;
   int sub;
-  row_of_thread<V>(t, row, sub);
+  row_of_thread<V>(t, pos, sub);
   T acc[BR];
-  row_product<BR, BC, V, T, T, T>(slice_ptr, col, vals, x, row, sub, acc);
-  if (sub == 0 && row < nbr) {
+  row_product<BR, BC, V, T, T, T>(slice_ptr, col, vals, x, pos, sub, acc);
+  const int64_t row = srow ? (int64_t)srow[pos] : pos;  // row position -> block row (sorted slices)
+  if (sub == 0 && row >= 0 && row < nbr) {
 #pragma unroll
     for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
   }
@@ -28,25 +29,27 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv(const int* __restrict__ sl
 // Component-split form for 6-row blocks (CTA = one slice, BR * VS warps).
 template <int BR, int BC, int VS, typename T>
 __global__ void __launch_bounds__(768) k_spmv_split(const int* __restrict__ slice_ptr, const int* __restrict__ col,
-                                                    const T* __restrict__ vals, const T* __restrict__ x,
-                                                    T* __restrict__ y, int64_t nbr) {
+                                                    const T* __restrict__ vals, const int* __restrict__ srow,
+                                                    const T* __restrict__ x, T* __restrict__ y, int64_t nbr) {
   const int64_t s = blockIdx.x;
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BR, sub = wp / BR;
   const T acc = row_component<BR, BC, VS, T, T, T>(slice_ptr, col, vals, x, s, lane, a, sub);
-  const int64_t i = s * 32 + lane;
-  if (sub == 0 && i < nbr) y[i * BR + a] = acc;
+  const int64_t i = srow ? (int64_t)srow[s * 32 + lane] : s * 32 + lane;
+  if (sub == 0 && i >= 0 && i < nbr) y[i * BR + a] = acc;
 }
 
 // Any block shape up to 8x8 (shapes without a specialisation).
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) k_spmv_any(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const T* __restrict__ vals,
-                                                          const T* __restrict__ x, T* __restrict__ y, int64_t nbr,
-                                                          int64_t nrows_pad, int br, int bc) {
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= nrows_pad) return;
-  const int64_t s = row >> 5;
-  const int lane = (int)(row & 31);
+                                                          const int* __restrict__ srow, const T* __restrict__ x,
+                                                          T* __restrict__ y, int64_t nbr, int64_t nrows_pad, int br,
+                                                          int bc) {
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= nrows_pad) return;
+  const int64_t s = pos >> 5;
+  const int lane = (int)(pos & 31);
+  const int64_t row = srow ? (int64_t)srow[pos] : pos;
   const int B = br * bc;
   T acc[8];
 #pragma unroll
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_any(const int* __restrict_
       }
     }
   }
-  if (row < nbr) {
+  if (row >= 0 && row < nbr) {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
       if (r < br) y[row * br + r] = acc[r];
@@ -74,14 +77,15 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_any(const int* __restrict_
 // consecutive X entries per block column.
 template <int BR, int BC, typename T>
 __global__ void __launch_bounds__(256) k_spmm(const int* __restrict__ slice_ptr, const int* __restrict__ col,
-                                              const T* __restrict__ vals, const T* __restrict__ X,
-                                              T* __restrict__ Y, int64_t nbr, int k) {
+                                              const T* __restrict__ vals, const int* __restrict__ srow,
+                                              const T* __restrict__ X, T* __restrict__ Y, int64_t nbr, int k) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = t / k;
-  const int j = (int)(t - row * k);
-  if (row >= nbr) return;
-  const int64_t s = row >> 5;
-  const int lane = (int)(row & 31);
+  const int64_t pos = t / k;
+  const int j = (int)(t - pos * k);
+  if (pos >= nbr) return;
+  const int64_t row = srow ? (int64_t)srow[pos] : pos;
+  const int64_t s = pos >> 5;
+  const int lane = (int)(pos & 31);
   T acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = T(0);
@@ -106,15 +110,16 @@ __global__ void __launch_bounds__(256) k_spmm(const int* __restrict__ slice_ptr,
 // vectors.
 template <int BR, int BC, typename T>
 __global__ void __launch_bounds__(256) k_spmm4(const int* __restrict__ slice_ptr, const int* __restrict__ col,
-                                               const T* __restrict__ vals, const T* __restrict__ X,
-                                               T* __restrict__ Y, int64_t nbr, int k) {
+                                               const T* __restrict__ vals, const int* __restrict__ srow,
+                                               const T* __restrict__ X, T* __restrict__ Y, int64_t nbr, int k) {
   const int G = k >> 2;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = t / G;
-  if (row >= nbr) return;
-  const int c0 = (int)(t - row * G) * 4;
+  const int64_t pos = t / G;
+  if (pos >= nbr) return;
+  const int64_t row = srow ? (int64_t)srow[pos] : pos;
+  const int c0 = (int)(t - pos * G) * 4;
   T acc[BR][4];
-  row_product4<BR, BC, T>(slice_ptr, col, vals, X, k, row, c0, acc);
+  row_product4<BR, BC, T>(slice_ptr, col, vals, X, k, pos, c0, acc);
 #pragma unroll
   for (int r = 0; r < BR; ++r) st4(Y + (row * BR + r) * k + c0, acc[r]);
 }
@@ -129,10 +134,10 @@ static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* 
     if (A->nslices == 0) return Status{};
     BAMG_DISPATCH_VS(-vec, {
       if (A->bc == 6)
-        k_spmv_split<6, 6, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y,
+        k_spmv_split<6, 6, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y,
                                                                             A->nbr);
       else
-        k_spmv_split<6, 3, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y,
+        k_spmv_split<6, 3, VS, T><<<(unsigned)A->nslices, 192 * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y,
                                                                             A->nbr);
       BAMG_COUNT_LAUNCH; })
     BAMG_CUDA(cudaGetLastError());
@@ -143,7 +148,7 @@ static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* 
   const unsigned blocks = (unsigned)((nt + kRowThreads - 1) / kRowThreads);
 #define BAMG_SPMV_CASE(R, C)                                                                                  \
   if (A->br == R && A->bc == C) {                                                                             \
-    BAMG_DISPATCH_V(vec, { k_spmv<R, C, V, T><<<blocks, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, \
+    BAMG_DISPATCH_V(vec, { k_spmv<R, C, V, T><<<blocks, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y, \
                                                                            A->nbr, nt); BAMG_COUNT_LAUNCH; }) \
     BAMG_CUDA(cudaGetLastError());                                                                            \
     return Status{};                                                                                          \
@@ -154,7 +159,7 @@ static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* 
   BAMG_SPMV_CASE(6, 3)
 #undef BAMG_SPMV_CASE
   const int64_t rows = A->nslices * kSlice;
-  { k_spmv_any<T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, x, y, A->nbr, rows, A->br, A->bc); BAMG_COUNT_LAUNCH; }
+  { k_spmv_any<T><<<(unsigned)((rows + kRowThreads - 1) / kRowThreads), kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y, A->nbr, rows, A->br, A->bc); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -265,9 +270,9 @@ Status launch_spmm(const bamg_bsr* A, const T* vals, const T* X, T* Y, int k, cu
 #define BAMG_SPMM_CASE(R, C)                                                                   \
   if (A->br == R && A->bc == C) {                                                              \
     if (four)                                                                                  \
-      { k_spmm4<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
+      { k_spmm4<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
     else                                                                                       \
-      { k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
+      { k_spmm<R, C, T><<<blocks, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, X, Y, A->nbr, k); BAMG_COUNT_LAUNCH; } \
     BAMG_CUDA(cudaGetLastError());                                                             \
     return Status{};                                                                           \
   }

@@ -379,3 +379,31 @@ def test_autotuned_hierarchy_gives_same_cycle():
         assert rel(x.cpu().numpy(), ref) <= TOL64 and rel(x1.cpu().numpy(), ref) <= TOL64
     finally:
         gp.close()
+
+
+def test_sorted_prolongator_products_match_oracle():
+    """Prolongators are stored with rows sorted by length inside each window
+    of slices; every product still writes each block row in place."""
+    ne = 13
+    h = hierarchy(ne)
+    gp = GpuProblem(ne)
+    try:
+        for l in range(B.bamg_mg_num_levels(gp.mg) - 1):
+            _, P = B.bamg_mg_get_level(gp.mg, l)
+            Ps = h.levels[l].P.scalar()
+            info = B.bamg_bsr_info(P)
+            rng = np.random.default_rng(l)
+            x = rng.standard_normal(Ps.shape[1])
+            choices = (1, 2, 4, 8) + ((-1, -2, -4) if info["bs_r"] == 6 else ())
+            for lanes in choices:
+                B.bamg_bsr_set_lanes(gp.ctx, P, lanes)
+                y = torch.zeros(Ps.shape[0], dtype=torch.float64, device="cuda")
+                B.bamg_bsr_spmv(gp.ctx, P, torch.from_numpy(x).cuda(), y)
+                assert rel(y.cpu().numpy(), Ps @ x) <= TOL64, (l, lanes)
+            for k in (3, 8):
+                X = rng.standard_normal((Ps.shape[1], k))
+                Y = torch.zeros((Ps.shape[0], k), dtype=torch.float64, device="cuda")
+                B.bamg_bsr_spmm(gp.ctx, P, torch.from_numpy(X).cuda(), Y, k, B.BAMG_FP64)
+                assert rel(Y.cpu().numpy(), Ps @ X) <= TOL64, (l, k)
+    finally:
+        gp.close()
