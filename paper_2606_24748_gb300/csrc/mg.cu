@@ -282,6 +282,41 @@ __global__ void __launch_bounds__(256) k_power_step(const int* __restrict__ slic
   if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) *norm_out = sqrt(out[0]);
 }
 
+// The same step (block diagonal only) in the component-split form for 6-row
+// blocks: CTA = one slice at a time (grid-stride over slices), BS * VS warps.
+template <int BS, int VS, typename TM>
+__global__ void __launch_bounds__(768) k_power_step_split(const int* __restrict__ slice_ptr,
+                                                          const int* __restrict__ col, const TM* __restrict__ vals,
+                                                          const double* __restrict__ dinv,
+                                                          const float* __restrict__ wts,
+                                                          const double* __restrict__ w_in,
+                                                          double* __restrict__ w_out, const double* norm_in,
+                                                          double* norm_out, int64_t n, int64_t nslices,
+                                                          double* partials, unsigned* counter) {
+  __shared__ double as[BS][32];
+  const double sc = norm_in ? 1.0 / *norm_in : 1.0;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BS, sub = wp / BS;
+  double local[1] = {0.0};
+  for (int64_t s = blockIdx.x; s < nslices; s += gridDim.x) {
+    const double acc = row_component<BS, BS, VS, TM, double, double>(slice_ptr, col, vals, w_in, s, lane, a, sub);
+    __syncthreads();  // the previous slice's readers of `as` are done
+    if (sub == 0) as[a][lane] = acc * sc;
+    __syncthreads();
+    const int64_t i = s * 32 + lane;
+    if (sub == 0 && i < n) {
+      const int64_t base = s * (32LL * BS * BS) + lane;
+      double t = 0.0;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) t = fma(dinv[base + 32 * (a * BS + c)], as[c][lane], t);
+      const double z = (wts ? (double)wts[i] : 1.0) * t;
+      w_out[i * BS + a] = z;
+      local[0] = fma(z, z, local[0]);
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(local, partials, counter, out) && threadIdx.x == 0) *norm_out = sqrt(out[0]);
+}
+
 // Rayleigh quotient w^T A w / w^T D w; in block mode also the Chebyshev data
 // for the interval [lower, upper] * lambda (Saad, Alg. 12.1 coefficients).
 template <int BS, int V, typename TM>
@@ -356,8 +391,18 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
   double* norms = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel;  // 2 scratch slots
   const unsigned g = red_grid(rows);
   { k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS); BAMG_COUNT_LAUNCH; }
+  const int split = (BS == 6 && !scalar_diag) ? split_for<TM>(A) : 0;
   for (int it = 0; it < mg->opts.power_its; ++it) {
     const double* nin = it == 0 ? nullptr : norms + ((it + 1) & 1);
+    if (split) {
+      const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(A->nslices, 1216));
+      BAMG_DISPATCH_VS(split, {
+        k_power_step_split<BS, VS, TM><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, dinv, wts,
+                                                                     w[it & 1], w[(it + 1) & 1], nin, norms + (it & 1),
+                                                                     n, A->nslices, ctx->d_partials, ctx->d_counters);
+        BAMG_COUNT_LAUNCH; })
+      continue;
+    }
     BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, scalar_diag ? nullptr : wts, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
