@@ -12,6 +12,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <array>
 
 #include "device.cuh"
 #include "internal.h"
@@ -191,11 +192,22 @@ __device__ void winv_cols(double* __restrict__ St, int64_t ld, const double* __r
 //             CTA 0 first updates tile (k+1,k+1), then factors and inverts it
 // so each step needs two barriers, and the inverse's updates fill the SMs
 // that the shrinking trailing matrix leaves idle.
-__global__ void __launch_bounds__(256) k_dense_factor(double* __restrict__ F, double* __restrict__ W, int64_t ld,
-                                                      int nt, double* __restrict__ Dinv, int* err) {
+__global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int64_t ld, int nt, double* Dinv,
+                                                      int* err, double* F2, double* W2, double* Dinv2) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[kT][kT + 1], w[kT][kT + 1];
-  const int G = gridDim.x, b = blockIdx.x;
+  // With a second matrix (F2 != null) the two factorisations run side by side
+  // on the two halves of the grid, in step with the same barriers.
+  const int nm = F2 ? 2 : 1;
+  const int G = (int)gridDim.x / nm;
+  const int mi = (int)blockIdx.x / G;
+  const bool idle = mi >= nm;  // an odd grid's last CTA only takes part in the barriers
+  const int b = idle ? (1 << 30) : (int)blockIdx.x - mi * G;
+  if (mi == 1) {
+    F = F2;
+    W = W2;
+    Dinv = Dinv2;
+  }
   if (b == 0) diag_tile(F, ld, 0, Dinv, err, a, w);
   __threadfence();
   grid.sync();
@@ -312,21 +324,43 @@ __global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, c
 //   S_0 = A_00;  S_k = A_kk - L_{k,k-1} L_{k,k-1}^T
 //   L_kk = chol(S_k);  L_{k+1,k} = A_{k+1,k} L_kk^-T
 // which costs about nc (s^3 / 6 + 2 s^3) multiply-adds instead of n^3 / 3 for
-// the dense factor and its inverse.  The solve with L then L^T is a chain
-// over the chunks; with W_k = L_kk^-1, M_k = W_k L_{k,k-1} and
-// N_k = W_k^T L_{k+1,k}^T formed here:
-//   y_k = W_k b_k - M_k y_{k-1};   x_k = W_k^T y_k - N_k x_{k+1}
-// i.e. two block-diagonal products and 2 (nc - 1) chained products.
+// the dense factor and its inverse.  The chain of chunk factorisations is
+// serial, so it is run from both ends at once ("twisted" block
+// factorisation): chunks 0 .. t-1 are eliminated downward as above, chunks
+// nc-1 .. t+1 upward,
+//   R_{nc-1} = A_{nc-1,nc-1};  R_k = A_kk - C_{k+1} C_{k+1}^T,
+//   Lt_k = chol(R_k);  C_k = A_{k-1,k} Lt_k^-T,
+// the two sides in lock step (one cooperative launch factors both chunks of
+// a round), and the middle chunk t takes both Schur complements:
+// S_t = A_tt - B_{t-1} B_{t-1}^T - C_{t+1} C_{t+1}^T.  With W_k the inverse
+// of each chunk's factor, M_k = W_k B_{k-1} (top and middle), Mt_k = W_k C_{k+1}
+// (bottom and middle), N_k = W_k^T B_k^T (top) and Nt_k = W_k^T C_k^T
+// (bottom), the solve is
+//   y = blockdiag(W) b;  y_k -= M_k y_{k-1} (top, downward);
+//   y_k -= Mt_k y_{k+1} (bottom, upward);  y_t -= M_t y_{t-1} + Mt_t y_{t+1};
+//   x = blockdiag(W^T) y;  x_k -= N_k x_{k+1} (top, from t down);
+//   x_k -= Nt_k x_{k-1} (bottom, from t up),
+// two block-diagonal products and about nc chained rounds in each
+// direction, each round one launch for both sides.
 
-// C = beta C + alpha A op(B) for s x s row-major matrices, op(B) = B or B^T;
-// one 32 x 32 output tile per CTA (256 threads, 4 outputs each); with
-// lower_only, tiles above the diagonal are skipped.
+// Up to kGemmBatch products C = beta C + alpha A op(B) of s x s row-major
+// matrices, op(B) = B or B^T, one per blockIdx.z; one 32 x 32 output tile per
+// CTA (256 threads, 4 outputs each); with lower_only, tiles above the
+// diagonal are skipped.
+constexpr int kGemmBatch = 8;
+struct GemmBatch {
+  double* C[kGemmBatch];
+  const double* A[kGemmBatch];
+  const double* B[kGemmBatch];
+};
+
 template <bool kTransB>
-__global__ void __launch_bounds__(256) k_chunk_gemm(double* __restrict__ C, const double* __restrict__ A,
-                                                    const double* __restrict__ B, int s, double alpha, double beta,
-                                                    int lower_only) {
+__global__ void __launch_bounds__(256) k_chunk_gemm(GemmBatch g, int s, double alpha, double beta, int lower_only) {
   const int ti = blockIdx.y, tj = blockIdx.x;
   if (lower_only && tj > ti) return;
+  double* __restrict__ C = g.C[blockIdx.z];
+  const double* __restrict__ A = g.A[blockIdx.z];
+  const double* __restrict__ B = g.B[blockIdx.z];
   __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
   const int tid = threadIdx.x, c = tid % kT, r0 = tid / kT;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -357,7 +391,7 @@ __global__ void __launch_bounds__(256) k_chunk_gemm(double* __restrict__ C, cons
 template <typename TM, int BS>
 __global__ void k_band_fill(int64_t nnzb, const int* __restrict__ rows, const int* __restrict__ colidx,
                             const int* __restrict__ slot_of, const TM* __restrict__ vals, double* __restrict__ D,
-                            double* __restrict__ Sub, int s, int* err) {
+                            double* __restrict__ Sub, double* __restrict__ Sup, int s, int* err) {
   constexpr int B = BS * BS;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nnzb * B) return;
@@ -370,7 +404,9 @@ __global__ void k_band_fill(int64_t nnzb, const int* __restrict__ rows, const in
     D[(ci * s + ri) * s + rj] = v;
   else if (ci == cj + 1)
     Sub[(cj * s + ri) * s + rj] = v;
-  else if (ci + 1 != cj && v != 0.0)
+  else if (ci + 1 == cj)
+    Sup[(ci * s + ri) * s + rj] = v;
+  else if (v != 0.0)
     set_err(err, kDevIndex);  // outside the band the chunks were sized for
 }
 
@@ -410,29 +446,44 @@ __global__ void k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows,
     if (lane == c) out[row * KP + c] = acc[c];
 }
 
-// y[r] -= sum_j M[r][j] z[j] for one chunk (s rows), KP vectors.
+// One round of the solve chains: up to two jobs (blockIdx.y), each
+// y[r] -= M1 z1 + M2 z2 over one chunk (s rows; M2 may be null), KP vectors.
+struct ChainRound {
+  const double* M1[2];
+  const double* z1[2];
+  const double* M2[2];
+  const double* z2[2];
+  double* y[2];
+};
+
 template <int KP>
-__global__ void k_chunk_chain(const double* __restrict__ M, int s, const double* __restrict__ z,
-                              double* __restrict__ y, const int* done) {
+__global__ void k_chunk_chain(ChainRound c, int s, const int* done) {
   pdl_enter();
   if (done && *done) return;
+  const int job = blockIdx.y;
   const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= s) return;
-  const double* mr = M + r * s;
   double acc[KP];
 #pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = 0.0;
-  for (int j = lane; j < s; j += 32) {
-    const double wv = mr[j];
+  for (int q = 0; q < KP; ++q) acc[q] = 0.0;
+  for (int term = 0; term < 2; ++term) {
+    const double* M = term == 0 ? c.M1[job] : c.M2[job];
+    const double* z = term == 0 ? c.z1[job] : c.z2[job];
+    if (!M) continue;
+    const double* mr = M + r * s;
+    for (int j = lane; j < s; j += 32) {
+      const double wv = mr[j];
 #pragma unroll
-    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, z[(int64_t)j * KP + c], acc[c]);
+      for (int q = 0; q < KP; ++q) acc[q] = fma(wv, z[(int64_t)j * KP + q], acc[q]);
+    }
   }
 #pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
+  for (int q = 0; q < KP; ++q) acc[q] = warp_sum(acc[q]);
+  double* y = c.y[job];
 #pragma unroll
-  for (int c = 0; c < KP; ++c)
-    if (lane == c) y[r * KP + c] -= acc[c];
+  for (int q = 0; q < KP; ++q)
+    if (lane == q) y[r * KP + q] -= acc[q];
 }
 
 template <typename TO>
@@ -453,88 +504,177 @@ static int64_t half_bandwidth(const bamg_bsr* A) {
   return (b + 1) * A->br - 1;
 }
 
-static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld, int ntl, double* dt) {
+static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld, int ntl, double* dt,
+                                 double* F2 = nullptr, double* W2 = nullptr, double* dt2 = nullptr) {
   int per_sm = 0;
   BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
   if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
   const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
   int* err = ctx->d_err;
-  void* args[] = {&F, &W, &ld, &ntl, &dt, &err};
+  void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2};
   BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, ctx->stream));
   BAMG_COUNT_LAUNCH;
   return Status{};
 }
 
+template <bool kTransB>
+static Status gemm_batch(const std::vector<std::array<const double*, 3>>& items, int s, double alpha, double beta,
+                         int lower_only, cudaStream_t st) {
+  for (size_t i0 = 0; i0 < items.size(); i0 += kGemmBatch) {
+    GemmBatch g = {};
+    const int cnt = (int)std::min<size_t>(kGemmBatch, items.size() - i0);
+    for (int q = 0; q < cnt; ++q) {
+      g.C[q] = const_cast<double*>(items[i0 + q][0]);
+      g.A[q] = items[i0 + q][1];
+      g.B[q] = items[i0 + q][2];
+    }
+    const dim3 grid((unsigned)(s / kT), (unsigned)(s / kT), (unsigned)cnt);
+    k_chunk_gemm<kTransB><<<grid, 256, 0, st>>>(g, s, alpha, beta, lower_only);
+    BAMG_COUNT_LAUNCH;
+  }
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+// Twisted block factorisation of the banded coarsest operator (see above).
 static Status band_factor(bamg_mg* mg) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
   Level& C = mg->levels.back();
   CoarseDense& D = mg->coarse;
   const bamg_bsr* A = C.A;
-  const int bs = C.bs, s = D.s, nc = D.nc;
+  const int bs = C.bs, s = D.s, nc = D.nc, t = nc / 2;
   const int64_t n = D.n, npad = D.npad, ss = (int64_t)s * s;
+  const int ntl = s / kT;
   if (!D.D) {
-    for (double** p : {&D.D, &D.Wb, &D.Wtb, &D.Mb}) BAMG_TRY(dalloc(p, nc * ss, st));
-    for (double** p : {&D.Sub, &D.Bb, &D.Nb}) BAMG_TRY(dalloc(p, std::max(1, nc - 1) * ss, st));
+    for (double** p : {&D.D, &D.Wb, &D.Wtb, &D.Mb, &D.Nb, &D.Mtb, &D.Ntb, &D.Bb}) BAMG_TRY(dalloc(p, nc * ss, st));
+    for (double** p : {&D.Sub, &D.Sup}) BAMG_TRY(dalloc(p, std::max(1, nc - 1) * ss, st));
     BAMG_TRY(dalloc(&D.b64, npad, st));
     BAMG_TRY(dalloc(&D.x64, npad, st));
-    BAMG_TRY(dalloc(&D.dinv_tiles, (int64_t)(s / kT) * kT * kT, st));
+    BAMG_TRY(dalloc(&D.dinv_tiles, 2 * (int64_t)ntl * kT * kT, st));
   }
+  auto Dk = [&](int k) { return D.D + k * ss; };
+  auto Wk = [&](int k) { return D.Wb + k * ss; };
+  auto Wt = [&](int k) { return D.Wtb + k * ss; };
+  auto BC = [&](int k) { return D.Bb + k * ss; };  // B_k (k < t) or C_k (k > t)
+  double* dt1 = D.dinv_tiles + (int64_t)ntl * kT * kT;
   const int pm = prof_begin(ctx, BAMG_PROF_COARSE_FACTOR, st);
   BAMG_CUDA(cudaMemsetAsync(D.D, 0, sizeof(double) * nc * ss, st));
   BAMG_CUDA(cudaMemsetAsync(D.Sub, 0, sizeof(double) * std::max(1, nc - 1) * ss, st));
+  BAMG_CUDA(cudaMemsetAsync(D.Sup, 0, sizeof(double) * std::max(1, nc - 1) * ss, st));
+  BAMG_CUDA(cudaMemsetAsync(D.Wb, 0, sizeof(double) * nc * ss, st));
   if (npad > n) { k_band_pad<<<(unsigned)((npad - n + 255) / 256), 256, 0, st>>>(D.D, n, npad, s); BAMG_COUNT_LAUNCH; }
   const int64_t nt_fill = A->nnzb * bs * bs;
   if (nt_fill > 0) {
     const unsigned b = (unsigned)((nt_fill + 255) / 256);
     const bool f32 = A->vals64_stale;
     if (bs == 6) {
-      if (f32) { k_band_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
-      else { k_band_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      if (f32) { k_band_fill<float, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, D.Sup, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      else { k_band_fill<double, 6><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, D.Sup, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
     } else {
-      if (f32) { k_band_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
-      else { k_band_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      if (f32) { k_band_fill<float, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals32, D.D, D.Sub, D.Sup, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
+      else { k_band_fill<double, 3><<<b, 256, 0, st>>>(A->nnzb, D.rows, A->colidx, A->slot_of, A->vals, D.D, D.Sub, D.Sup, s, ctx->d_err); BAMG_COUNT_LAUNCH; }
     }
   }
-  const int t = s / kT;
-  const dim3 g((unsigned)t, (unsigned)t);
-  for (int k = 0; k < nc; ++k) {
-    double* Dk = D.D + k * ss;
-    double* Wk = D.Wb + k * ss;
-    if (k > 0) { k_chunk_gemm<true><<<g, 256, 0, st>>>(Dk, D.Bb + (k - 1) * ss, D.Bb + (k - 1) * ss, s, -1.0, 1.0, 1); BAMG_COUNT_LAUNCH; }
-    BAMG_CUDA(cudaMemsetAsync(Wk, 0, sizeof(double) * ss, st));
-    BAMG_TRY(cooperative_factor(ctx, Dk, Wk, s, t, D.dinv_tiles));
-    { k_transpose_dense<<<g, 256, 0, st>>>(Wk, D.Wtb + k * ss, s); BAMG_COUNT_LAUNCH; }
-    if (k + 1 < nc) {
-      double* Bk = D.Bb + k * ss;
-      { k_chunk_gemm<true><<<g, 256, 0, st>>>(Bk, D.Sub + k * ss, Wk, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
-      { k_chunk_gemm<true><<<g, 256, 0, st>>>(D.Nb + k * ss, D.Wtb + k * ss, Bk, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
-    }
-    if (k > 0) { k_chunk_gemm<false><<<g, 256, 0, st>>>(D.Mb + k * ss, Wk, D.Bb + (k - 1) * ss, s, 1.0, 0.0, 0); BAMG_COUNT_LAUNCH; }
+  const dim3 tg((unsigned)ntl, (unsigned)ntl);
+  // rounds: top chunk r (r < t) and bottom chunk nc-1-r (> t), side by side
+  const int rounds = std::max(t, nc - 1 - t);
+  for (int r = 0; r < rounds; ++r) {
+    const int kt = r < t ? r : -1;
+    const int kb = (nc - 1 - r > t) ? nc - 1 - r : -1;
+    std::vector<std::array<const double*, 3>> syrk, panel;
+    if (kt > 0) syrk.push_back({Dk(kt), BC(kt - 1), BC(kt - 1)});
+    if (kb >= 0 && kb < nc - 1) syrk.push_back({Dk(kb), BC(kb + 1), BC(kb + 1)});
+    if (!syrk.empty()) BAMG_TRY(gemm_batch<true>(syrk, s, -1.0, 1.0, 1, st));
+    if (kt >= 0 && kb >= 0)
+      BAMG_TRY(cooperative_factor(ctx, Dk(kt), Wk(kt), s, ntl, D.dinv_tiles, Dk(kb), Wk(kb), dt1));
+    else
+      BAMG_TRY(cooperative_factor(ctx, Dk(kt >= 0 ? kt : kb), Wk(kt >= 0 ? kt : kb), s, ntl, D.dinv_tiles));
+    for (int k : {kt, kb})
+      if (k >= 0) { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(k), Wt(k), s); BAMG_COUNT_LAUNCH; }
+    if (kt >= 0) panel.push_back({BC(kt), D.Sub + kt * ss, Wk(kt)});          // B_k = A_{k+1,k} W_k^T
+    if (kb >= 0) panel.push_back({BC(kb), D.Sup + (kb - 1) * ss, Wk(kb)});    // C_k = A_{k-1,k} W_k^T
+    BAMG_TRY(gemm_batch<true>(panel, s, 1.0, 0.0, 0, st));
   }
+  // middle chunk: both Schur complements, then its factor
+  {
+    std::vector<std::array<const double*, 3>> syrk;
+    if (t > 0) syrk.push_back({Dk(t), BC(t - 1), BC(t - 1)});
+    if (t + 1 < nc) syrk.push_back({Dk(t), BC(t + 1), BC(t + 1)});
+    for (auto& it : syrk) BAMG_TRY(gemm_batch<true>({it}, s, -1.0, 1.0, 1, st));  // same output: one at a time
+    BAMG_TRY(cooperative_factor(ctx, Dk(t), Wk(t), s, ntl, D.dinv_tiles));
+    { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(t), Wt(t), s); BAMG_COUNT_LAUNCH; }
+  }
+  // chain matrices, off the critical path: all in two batched launches
+  std::vector<std::array<const double*, 3>> nn, nt;
+  for (int k = 1; k <= t; ++k) nn.push_back({D.Mb + k * ss, Wk(k), BC(k - 1)});    // M_k = W_k B_{k-1}
+  for (int k = t; k + 1 < nc; ++k) nn.push_back({D.Mtb + k * ss, Wk(k), BC(k + 1)}); // Mt_k = W_k C_{k+1}
+  for (int k = 0; k < t; ++k) nt.push_back({D.Nb + k * ss, Wt(k), BC(k)});         // N_k = W_k^T B_k^T
+  for (int k = t + 1; k < nc; ++k) nt.push_back({D.Ntb + k * ss, Wt(k), BC(k)});    // Nt_k = W_k^T C_k^T
+  BAMG_TRY(gemm_batch<false>(nn, s, 1.0, 0.0, 0, st));
+  BAMG_TRY(gemm_batch<true>(nt, s, 1.0, 0.0, 0, st));
   prof_end(ctx, pm, st);
   BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+template <int KP>
+static Status chain_round(const ChainRound& c, int jobs, int s, const int* done, cudaStream_t st) {
+  BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s), (unsigned)jobs), dim3(256), st, c, s, done));
+  BAMG_COUNT_LAUNCH;
   return Status{};
 }
 
 template <int KP, typename T>
 static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, const int* done, cudaStream_t st) {
   CoarseDense& D = mg->coarse;
-  const int s = D.s, nc = D.nc;
-  const int64_t ss = (int64_t)s * s, npad = D.npad;
-  // forward: y = blockdiag(W) b, then y_k -= M_k y_{k-1}
+  const int s = D.s, nc = D.nc, t = nc / 2;
+  const int64_t ss = (int64_t)s * s, npad = D.npad, cs = (int64_t)s * KP;
+  // forward: y = blockdiag(W) b, then the two chains toward the middle chunk
   { BAMG_CUDA(launch_k(k_chunk_mv<KP, T>, dim3(warps_grid(npad)), dim3(256), st, D.Wb, s, npad, b, D.n, y, done)); BAMG_COUNT_LAUNCH; }
-  for (int k = 1; k < nc; ++k) {
-    BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s)), dim3(256), st, D.Mb + k * ss, s, y + (int64_t)(k - 1) * s * KP,
-                                                     y + (int64_t)k * s * KP, done));
-    BAMG_COUNT_LAUNCH;
+  const int fr = std::max(t - 1, nc - 2 - t);
+  for (int r = 1; r <= fr; ++r) {
+    ChainRound c = {};
+    int jobs = 0;
+    if (r <= t - 1) {  // top chunk r from r - 1
+      c.M1[jobs] = D.Mb + r * ss;
+      c.z1[jobs] = y + (r - 1) * cs;
+      c.y[jobs++] = y + r * cs;
+    }
+    const int kb = nc - 1 - r;  // bottom chunk from kb + 1
+    if (kb > t) {
+      c.M1[jobs] = D.Mtb + kb * ss;
+      c.z1[jobs] = y + (kb + 1) * cs;
+      c.y[jobs++] = y + kb * cs;
+    }
+    if (jobs) BAMG_TRY(chain_round<KP>(c, jobs, s, done, st));
   }
-  // backward: z = blockdiag(W^T) y, then z_k -= N_k z_{k+1}
+  {
+    ChainRound c = {};
+    c.M1[0] = t > 0 ? D.Mb + t * ss : nullptr;
+    c.z1[0] = t > 0 ? y + (t - 1) * cs : nullptr;
+    c.M2[0] = t + 1 < nc ? D.Mtb + t * ss : nullptr;
+    c.z2[0] = t + 1 < nc ? y + (t + 1) * cs : nullptr;
+    c.y[0] = y + t * cs;
+    BAMG_TRY(chain_round<KP>(c, 1, s, done, st));
+  }
+  // backward: z = blockdiag(W^T) y, then outward from the middle chunk
   { BAMG_CUDA(launch_k(k_chunk_mv<KP, double>, dim3(warps_grid(npad)), dim3(256), st, D.Wtb, s, npad, y, npad, z, done)); BAMG_COUNT_LAUNCH; }
-  for (int k = nc - 2; k >= 0; --k) {
-    BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s)), dim3(256), st, D.Nb + k * ss, s, z + (int64_t)(k + 1) * s * KP,
-                                                     z + (int64_t)k * s * KP, done));
-    BAMG_COUNT_LAUNCH;
+  const int br = std::max(t, nc - 1 - t);
+  for (int r = 1; r <= br; ++r) {
+    ChainRound c = {};
+    int jobs = 0;
+    const int kt = t - r, kb = t + r;
+    if (kt >= 0) {
+      c.M1[jobs] = D.Nb + kt * ss;
+      c.z1[jobs] = z + (kt + 1) * cs;
+      c.y[jobs++] = z + kt * cs;
+    }
+    if (kb < nc) {
+      c.M1[jobs] = D.Ntb + kb * ss;
+      c.z1[jobs] = z + (kb - 1) * cs;
+      c.y[jobs++] = z + kb * cs;
+    }
+    if (jobs) BAMG_TRY(chain_round<KP>(c, jobs, s, done, st));
   }
   const int64_t m = D.n * KP;
   { BAMG_CUDA(launch_k(k_band_out<T>, dim3((unsigned)((m + 255) / 256)), dim3(256), st, m, z, x, done)); BAMG_COUNT_LAUNCH; }

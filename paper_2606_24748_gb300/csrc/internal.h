@@ -172,14 +172,17 @@ struct CoarseDense {
   double* dinv_tiles = nullptr;  // inverses of the 32x32 diagonal tiles of L
   bool factored = false;
   // Banded form (nc > 0): the padded matrix (npad = nc * s) split into chunks
-  // of s rows is block tridiagonal; per chunk k, s x s row-major:
-  //   D[k]  A_kk, then the Schur complement, then its Cholesky factor L_kk
-  //   Sub[k] A_{k+1,k};  Bb[k] = L_{k+1,k} = A_{k+1,k} L_kk^-T
-  //   Wb[k] = L_kk^-1,  Wtb[k] = its transpose
-  //   Mb[k] = W_k L_{k,k-1} (k >= 1),  Nb[k] = W_k^T L_{k+1,k}^T (k <= nc - 2)
+  // of s rows is block tridiagonal, factored from both ends toward the middle
+  // chunk t = nc / 2; per chunk k, s x s row-major:
+  //   D[k]   A_kk, then its Schur complement, then the chunk's Cholesky factor
+  //   Sub[k] A_{k+1,k};  Sup[k] A_{k,k+1}
+  //   Bb[k]  B_k = A_{k+1,k} W_k^T (k < t) or C_k = A_{k-1,k} W_k^T (k > t)
+  //   Wb[k]  W_k = inverse of the chunk's factor;  Wtb[k] its transpose
+  //   Mb[k] = W_k B_{k-1} (1 <= k <= t);  Mtb[k] = W_k C_{k+1} (t <= k <= nc-2)
+  //   Nb[k] = W_k^T B_k^T (k < t);        Ntb[k] = W_k^T C_k^T (k > t)
   int nc = 0, s = 0;
-  double *D = nullptr, *Sub = nullptr, *Wb = nullptr, *Wtb = nullptr, *Bb = nullptr, *Mb = nullptr,
-         *Nb = nullptr;
+  double *D = nullptr, *Sub = nullptr, *Sup = nullptr, *Wb = nullptr, *Wtb = nullptr, *Bb = nullptr,
+         *Mb = nullptr, *Nb = nullptr, *Mtb = nullptr, *Ntb = nullptr;
 };
 
 struct Level {
