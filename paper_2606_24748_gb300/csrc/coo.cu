@@ -38,11 +38,14 @@ __global__ void k_coo_sum(const int* __restrict__ seg, const int* __restrict__ p
   const int64_t k = t / B;
   const int e = (int)(t - k * B);
   const int s0 = seg[k], s1 = seg[k + 1];
-  double sum = 0.0;
-  for (int s = s0; s < s1; ++s) sum += __ldg(v + (int64_t)perm[s] * B + e);
+  // FP64 adds run at two per clock per SM: start from the first contribution
+  // instead of zero, and test for NaN / Inf on the exponent bits (integer
+  // pipe) rather than with FP64 comparisons.
+  double sum = s1 > s0 ? __ldg(v + (int64_t)perm[s0] * B + e) : 0.0;
+  for (int s = s0 + 1; s < s1; ++s) sum += __ldg(v + (int64_t)perm[s] * B + e);
   const int64_t a = vidx<B>(slot_of[k], e);
   if (add) sum += vals[a];
-  if (!isfinite(sum)) set_err(err, kDevNaN);
+  if ((__double_as_longlong(sum) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) set_err(err, kDevNaN);
   vals[a] = sum;
   if (vals32) vals32[a] = (float)sum;
 }

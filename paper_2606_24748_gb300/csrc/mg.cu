@@ -418,9 +418,11 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal) {
   Level& L = mg->levels[l];
   bamg_bsr* A = L.A;
-  // The mixed form estimates the spectrum of the operator its smoother applies
-  // (the FP32 copy), in FP64 arithmetic.
-  const bool f32 = A->vals64_stale || (mg->opts.precision == BAMG_FP32 && !scalar_diag);
+  // FP64 arithmetic on the FP64 values when they are current (the fine level
+  // in both forms); the coarse levels of the mixed form hold only the FP32
+  // copy, read and widened.  (The FP32 smoother's operator differs from the
+  // FP64 one by single-precision rounding, far inside the interval's margin.)
+  const bool f32 = A->vals64_stale;
   if (f32) BAMG_TRY(bsr_ensure_fp32(A));
   const float* wts = L.weights;
   if (L.bs == 3)
