@@ -156,7 +156,10 @@ BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, b
  * lanes for few, long rows); or, for 6x3 and 6x6 blocks only, the component
  * split: -VS = VS warps (1, 2 or 4) per output component of a 32-row slice,
  * each taking every VS-th block of the rows (no cross-lane sums, no idle
- * lanes; the FP64 pipe's two FMA per clock per SM make those count); 0 in
+ * lanes; the FP64 pipe's two FMA per clock per SM make those count), or
+ * -32 * VR (VR = 1, 2, 4) = one CTA per row, VR warps per component with
+ * their lanes over the row's blocks (for few, very long rows; used by the
+ * transfer and product kernels, the smoother kernels treat it as -1); 0 in
  * _set_lanes means -4.  _autotune times the product for every choice from a
  * flushed L2 on the context's stream and keeps the fastest, for the FP64
  * values and, when present, the FP32 copy (allocates work vectors; returns

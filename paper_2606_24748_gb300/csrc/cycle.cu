@@ -207,6 +207,21 @@ __global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ 
   if (sub == 0 && i >= 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
 }
 
+// Row form (see row_component_lanes): CTA = one row position.
+template <int BR, int BC, int VR, typename T>
+__global__ void __launch_bounds__(32 * BR * VR) k_transfer_rows(const int* __restrict__ sp, const int* __restrict__ col,
+                                                                const T* __restrict__ vals, const int* __restrict__ srow,
+                                                                int64_t n, const T* __restrict__ v, T* __restrict__ y,
+                                                                int accumulate, const int* done) {
+  pdl_enter();
+  BAMG_DONE_RETURN
+  const int64_t pos = blockIdx.x;
+  const T acc = row_component_lanes<BR, BC, VR, T, T, T>(sp, col, vals, v, pos);
+  const int64_t i = srow ? (int64_t)srow[pos] : pos;
+  const int a = threadIdx.x;
+  if (a < BR && i >= 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
+}
+
 template <typename T>
 __global__ void k_axpy_done(int64_t m, const T* __restrict__ d, T* __restrict__ x, const int* done) {
   pdl_enter();
@@ -352,6 +367,14 @@ static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int a
                        cudaStream_t st) {
   const int64_t rows = row_threads_for<T>(M);
   if (rows == 0) return Status{};
+  if (BR == 6 && split_for<T>(M) >= kSplitRows) {
+    BAMG_DISPATCH_ROWS(split_for<T>(M), {
+      BAMG_CUDA(launch_k(k_transfer_rows<BR, BC, VR, T>, dim3((unsigned)(M->nslices * kSlice)), dim3(32 * BR * VR), st,
+                         M->slice_ptr, M->sell_col, vals, M->slot_row, M->nbr, v, y, accumulate, done));
+      BAMG_COUNT_LAUNCH; })
+    BAMG_CUDA(cudaGetLastError());
+    return Status{};
+  }
   if (BR == 6 && split_for<T>(M)) {
     BAMG_DISPATCH_VS(split_for<T>(M), {
       BAMG_CUDA(launch_k(k_transfer_split<BR, BC, VS, T>, dim3((unsigned)M->nslices), dim3(32 * BR * VS), st, M->slice_ptr, M->sell_col, vals,

@@ -100,6 +100,41 @@ __device__ __forceinline__ TA row_component(const int* __restrict__ slice_ptr, c
   return acc;
 }
 
+// Row form of the component split, for matrices with few, very long rows
+// (the restriction to the coarsest levels): a CTA of BR * VS warps takes one
+// row position; warp (a, sub) sums output component a over every VS-th group
+// of 32 chunks of the row, one chunk per lane, then one shuffle tree.  With
+// VS > 1 the VS partial sums meet in shared memory; thread a < BR returns
+// component a's total (the other threads return 0).
+template <int BR, int BC, int VS, typename TM, typename TA, typename TX>
+__device__ __forceinline__ TA row_component_lanes(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                                  const TM* __restrict__ vals, const TX* __restrict__ x,
+                                                  int64_t pos) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = w / VS, sub = w % VS;
+  const int64_t s = pos >> 5;
+  const int l = (int)(pos & 31);
+  const int c0 = __ldg(slice_ptr + s), c1 = __ldg(slice_ptr + s + 1);
+  TA acc = TA(0);
+  for (int c = c0 + sub * 32 + lane; c < c1; c += 32 * VS) {
+    const int j = __ldg(col + (int64_t)c * 32 + l);
+    const TM* v = vals + (int64_t)c * (32 * BR * BC) + 32 * (a * BC) + l;
+#pragma unroll
+    for (int q = 0; q < BC; ++q) acc = fma((TA)__ldg(v + 32 * q), (TA)__ldg(x + (int64_t)j * BC + q), acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ TA part[BR * VS];
+  if (lane == 0) part[w] = acc;
+  __syncthreads();
+  TA total = TA(0);
+  if (threadIdx.x < BR) {
+#pragma unroll
+    for (int t = 0; t < VS; ++t) total += part[threadIdx.x * VS + t];
+  }
+  return total;
+}
+
 // Thread -> (row, sub-lane) for V lanes per row.
 template <int V>
 __device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub) {

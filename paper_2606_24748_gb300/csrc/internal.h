@@ -100,7 +100,8 @@ struct bamg_bsr {
   int vec = 1;               // lanes per block row of the FP64 row kernels (1..32, power of 2)
   int vec32 = 1;             // the same for kernels reading the FP32 copy
   int split = 0;             // 6-row blocks: 0 = lanes per row; 1, 2 or 4 = component split with
-  int split32 = 0;           //   that many warps per component of a slice (FP64 / FP32 kernels)
+  int split32 = 0;           //   that many warps per component of a slice; 32, 64, 128 = one CTA per
+                             //   row, split / 32 warps per component (FP64 / FP32 kernels)
   bool vec_tuned = false;
   std::vector<int> h_slice_ptr, h_slot_of;
   double* vals = nullptr;    // 32 * nchunks * B
@@ -399,6 +400,15 @@ template <typename T>
 inline int split_for(const bamg_bsr* A) {
   return sizeof(T) == 4 ? A->split32 : A->split;
 }
+// Split codes 32, 64 and 128: the row form (one CTA per row, split / 32 warps
+// per output component).
+constexpr int kSplitRows = 32;
+#define BAMG_DISPATCH_ROWS(s, ...)                          \
+  switch (s) {                                             \
+    case 128: { constexpr int VR = 4; __VA_ARGS__; } break; \
+    case 64: { constexpr int VR = 2; __VA_ARGS__; } break;  \
+    default: { constexpr int VR = 1; __VA_ARGS__; } break;  \
+  }
 // Run `body` with the compile-time warps per component VS matching s (1, 2 or 4).
 #define BAMG_DISPATCH_VS(s, ...)                            \
   switch (s) {                                             \

@@ -38,6 +38,18 @@ __global__ void __launch_bounds__(768) k_spmv_split(const int* __restrict__ slic
   if (sub == 0 && i >= 0 && i < nbr) y[i * BR + a] = acc;
 }
 
+// Row form (rectangular 6-row-block matrices with few, long rows).
+template <int BR, int BC, int VR, typename T>
+__global__ void __launch_bounds__(32 * BR * VR) k_spmv_rows(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                                            const T* __restrict__ vals, const int* __restrict__ srow,
+                                                            const T* __restrict__ x, T* __restrict__ y, int64_t nbr) {
+  const int64_t pos = blockIdx.x;
+  const T acc = row_component_lanes<BR, BC, VR, T, T, T>(slice_ptr, col, vals, x, pos);
+  const int64_t i = srow ? (int64_t)srow[pos] : pos;
+  const int a = threadIdx.x;
+  if (a < BR && i >= 0 && i < nbr) y[i * BR + a] = acc;
+}
+
 // Any block shape up to 8x8 (shapes without a specialisation).
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) k_spmv_any(const int* __restrict__ slice_ptr,
@@ -130,6 +142,18 @@ static bool can_split(const bamg_bsr* A) { return A->br == 6 && (A->bc == 3 || A
 // warps per component.
 template <typename T>
 static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* x, T* y, cudaStream_t st) {
+  if (vec <= -kSplitRows) {
+    if (A->nslices == 0) return Status{};
+    const unsigned g = (unsigned)(A->nslices * kSlice);
+    BAMG_DISPATCH_ROWS(-vec, {
+      if (A->bc == 6)
+        k_spmv_rows<6, 6, VR, T><<<g, 192 * VR, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y, A->nbr);
+      else
+        k_spmv_rows<6, 3, VR, T><<<g, 192 * VR, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y, A->nbr);
+      BAMG_COUNT_LAUNCH; })
+    BAMG_CUDA(cudaGetLastError());
+    return Status{};
+  }
   if (vec < 0) {
     if (A->nslices == 0) return Status{};
     BAMG_DISPATCH_VS(-vec, {
@@ -207,8 +231,10 @@ static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, int* out_spli
   Status s;
   // widths 1, 2, ..., 32, then (6-row blocks) the component-split form with
   // 1, 2 and 4 warps per component, coded as -1, -2, -4
-  static const int kChoices[] = {1, 2, 4, 8, 16, 32, -1, -2, -4};
-  const int n_choices = can_split(A) ? 9 : 6;
+  // and, for rectangular ones (the restriction), the row form with 1, 2 and
+  // 4 warps per component (-32, -64, -128)
+  static const int kChoices[] = {1, 2, 4, 8, 16, 32, -1, -2, -4, -32, -64, -128};
+  const int n_choices = can_split(A) ? (A->nbr != A->nbc || A->br != A->bc ? 12 : 9) : 6;
   for (int ci = 0; ci < n_choices; ++ci) {
     const int lv = kChoices[ci];
     for (int w = 0; w < 2 && s.ok(); ++w) s = launch_spmv_v<T>(A, lv, vals, x, y, st);

@@ -311,7 +311,8 @@ def test_lane_choice_invariance(br, bc):
         B.bamg_bsr_coo_set_values(ctx, A, torch.from_numpy(v).cuda(), 0)
         x = rng.standard_normal(nbc * bc)
         yref = ref.scalar() @ x
-        choices = (1, 2, 4, 8, 16, 32) + ((-1, -2, -4) if br == 6 else ())   # < 0: component split
+        # -1, -2, -4: component split; -32, -64, -128: one CTA per row
+        choices = (1, 2, 4, 8, 16, 32) + ((-1, -2, -4, -32, -64, -128) if br == 6 else ())
         for lanes in choices:
             B.bamg_bsr_set_lanes(ctx, A, lanes)
             assert B.bamg_bsr_get_lanes(A) == lanes
@@ -355,6 +356,33 @@ def test_component_split_hierarchy_gives_same_cycle(precision):
         x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
         out = B.bamg_cg_solve(gp.ctx, gp.mg, torch.from_numpy(body_force(gp.mesh)).cuda(), x, 1e-8, 200)
         assert out["converged"]
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("precision,lanes", [(B.BAMG_FP64, -32), (B.BAMG_FP64, -128), (B.BAMG_FP32, -64)])
+def test_row_form_restriction_gives_same_cycle(precision, lanes):
+    """The restriction's row form (a CTA per coarse row) changes only the
+    summation order of the cycle."""
+    ne = 16
+    h = hierarchy(ne)
+    gp = GpuProblem(ne, precision=precision)
+    try:
+        b = np.random.default_rng(8).standard_normal(gp.mesh.n_dofs)
+        B.bamg_mg_set_lanes(gp.ctx, gp.mg, 1)
+        y0 = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), y0)
+        for l in range(B.bamg_mg_num_levels(gp.mg) - 1):
+            R = B.bamg_mg_get_restriction(gp.mg, l)
+            assert R is not None
+            B.bamg_bsr_set_lanes(gp.ctx, R, lanes)
+            assert B.bamg_bsr_get_lanes(R) == lanes
+        y1 = torch.zeros_like(y0)
+        B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(b).cuda(), y1)
+        ref = omg.vcycle(h, b)
+        tol = TOL64 if precision == B.BAMG_FP64 else 1e-3
+        assert rel(y1.cpu().numpy(), ref) <= tol
+        assert rel(y1.cpu().numpy(), y0.cpu().numpy()) <= (1e-13 if precision == B.BAMG_FP64 else 1e-5)
     finally:
         gp.close()
 
