@@ -282,7 +282,7 @@ bamg_status bamg_ctx_create(void* cuda_stream, bamg_ctx** out) {
     BAMG_CUDA(cudaGetDevice(&c->device));
     BAMG_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     BAMG_TRY(dalloc(&c->d_err, 1, c->stream));
-    BAMG_TRY(dalloc(&c->d_partials, 8192 * 4, c->stream));
+    BAMG_TRY(dalloc(&c->d_partials, kRedGridMax * 4, c->stream));
     BAMG_TRY(dalloc(&c->d_counters, 64, c->stream));
     BAMG_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     BAMG_CUDA(cudaMemsetAsync(c->d_counters, 0, 64 * sizeof(unsigned), c->stream));

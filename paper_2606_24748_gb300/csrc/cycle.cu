@@ -527,15 +527,17 @@ __global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double
 
 // q = A p, alpha = rz / (p.q)
 template <int V>
-__global__ void __launch_bounds__(256) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
+__global__ void __launch_bounds__(256, 8) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
                                                        const double* __restrict__ vals, int64_t n, int64_t nthreads,
                                                        const double* __restrict__ p, double* __restrict__ q,
                                                        CgState* s, double* partials, unsigned* counter) {
   pdl_enter();
   if (s->done) return;
   double local[1] = {0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+  const int64_t ntasks = (nthreads + 31) >> 5;
+  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+    const int64_t t = g * 32 + (threadIdx.x & 31);
+    if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t i;
     int sub;
     row_of_thread<V>(t, i, sub);
@@ -624,15 +626,17 @@ __global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restri
 
 // ||b - A x||^2 into s->pq (final true residual)
 template <int V>
-__global__ void __launch_bounds__(256) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
+__global__ void __launch_bounds__(256, 8) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
                                                                const double* __restrict__ vals, int64_t n,
                                                                int64_t nthreads, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* out_norm2,
                                                                double* partials, unsigned* counter) {
   pdl_enter();
   double local[1] = {0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+  const int64_t ntasks = (nthreads + 31) >> 5;
+  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+    const int64_t t = g * 32 + (threadIdx.x & 31);
+    if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t i;
     int sub;
     row_of_thread<V>(t, i, sub);
@@ -651,13 +655,6 @@ __global__ void __launch_bounds__(256) k_true_residual(const int* __restrict__ s
 }
 
 static unsigned vec_grid(int64_t m) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 1216)); }
-// Reducing row kernels: 256 threads per CTA, so that one thread per row
-// (the fine operator has 274,625 rows at 64^3 elements) fits in the 1,216 CTAs
-// of the reduction partials.
-static unsigned row_grid(int64_t rows) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 1216));
-}
-
 // One CG iteration after the first preconditioner application.
 static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
@@ -667,7 +664,7 @@ static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   CgState* s = mg->cg;
   const int* done = &s->done;
   const int pa = prof_begin(ctx, BAMG_PROF_CG_AP, st);
-  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_cg_Ap<V>, dim3(row_grid(rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_cg_Ap<V>, dim3(deal_grid(k_cg_Ap<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
                                                   ctx->d_partials, ctx->d_counters + 2)); BAMG_COUNT_LAUNCH; })
   prof_end(ctx, pa, st);
   const int px = prof_begin(ctx, BAMG_PROF_CG_XR, st);
@@ -790,7 +787,7 @@ Status cg_epilogue(bamg_mg* mg, const double* b, double* x, double* true_r2, cud
   if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   const bamg_bsr* A = L0.A;
   const int64_t rows = row_threads(A);
-  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_true_residual<V>, dim3(row_grid(rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_true_residual<V>, dim3(deal_grid(k_true_residual<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
                                                           true_r2, ctx->d_partials, ctx->d_counters + 7)); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};

@@ -142,6 +142,15 @@ __device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub)
   sub = (int)(t - row * V);
 }
 
+// Balanced deal of warp tasks (32 consecutive virtual threads) for the
+// one-wave reducing row kernels: task g goes to CTA g mod grid, warp
+// (g / grid) mod W of it.  With a grid of SMs x resident CTAs every SM then
+// gets the same number of tasks to within one per CTA; numbering threads
+// straight through leaves some SMs a whole CTA short for the entire kernel.
+// Loop: for (g = deal_first(); g < ntasks; g += deal_stride()).
+__device__ __forceinline__ int64_t deal_first() { return blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); }
+__device__ __forceinline__ int64_t deal_stride() { return (int64_t)gridDim.x * (blockDim.x >> 5); }
+
 // Run `body` with the compile-time lane count matching v (1..32).
 #define BAMG_DISPATCH_V(v, ...)                \
   switch (v) {                                 \

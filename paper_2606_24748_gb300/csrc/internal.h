@@ -20,6 +20,22 @@ constexpr int kSlice = 32;
 constexpr int kRowThreads = 128;
 // CTAs of the fixed-grid reductions (a multiple of the 152 SMs of a GB300).
 constexpr int kRedBlocks = 608;
+constexpr int kRedGridMax = 8192;  // CTAs of a reducing row kernel (one partial slot each)
+
+// Grid of a one-wave reducing row kernel with 256-thread CTAs (deal_first /
+// deal_stride): the SMs times the CTAs of `kernel` resident on one, all of
+// them even when the rows would fit in fewer (the deal spreads the tasks
+// over every CTA), but no more CTAs than warp tasks.
+template <typename K>
+inline unsigned deal_grid(K kernel, int sm_count, int64_t threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t cap = std::min<int64_t>((int64_t)sm_count * per_sm, kRedGridMax);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 31) / 32, cap));
+}
 constexpr int kRedThreads = 256;
 
 struct Status {
@@ -64,7 +80,7 @@ struct bamg_ctx {
   int sm_count = 0;
   std::string err;
   int* d_err = nullptr;            // device error word (first error code wins)
-  double* d_partials = nullptr;    // kRedBlocks partial sums x 4 lanes
+  double* d_partials = nullptr;    // kRedGridMax partial sums x 4 lanes
   unsigned* d_counters = nullptr;  // last-block counters (16 slots)
   bamg::Prof prof;
 };

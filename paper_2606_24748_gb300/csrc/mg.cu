@@ -235,7 +235,7 @@ __global__ void k_start_vector(double* __restrict__ v, int64_t n) {
 // One power step w_out = D^-1 A (w_in / ||w_in||) with D the block diagonal
 // (dinv) or the scalar diagonal; ||w_out|| goes to *norm_out.
 template <int BS, int V, typename TM>
-__global__ void __launch_bounds__(256) k_power_step(const int* __restrict__ slice_ptr,
+__global__ void __launch_bounds__(256, 8) k_power_step(const int* __restrict__ slice_ptr,
                                                             const int* __restrict__ col, const TM* __restrict__ vals,
                                                             const int* __restrict__ diag_slot,
                                                             const double* __restrict__ dinv, int scalar_diag,
@@ -247,8 +247,10 @@ __global__ void __launch_bounds__(256) k_power_step(const int* __restrict__ slic
   constexpr int B = BS * BS;
   const double s = norm_in ? 1.0 / *norm_in : 1.0;
   double local[1] = {0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+  const int64_t ntasks = (nthreads + 31) >> 5;
+  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+    const int64_t t = g * 32 + (threadIdx.x & 31);
+    if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t row;
     int sub;
     row_of_thread<V>(t, row, sub);
@@ -329,8 +331,10 @@ __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_
                                                           double lower, double upper, int degree) {
   constexpr int B = BS * BS;
   double local[2] = {0.0, 0.0};
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nthreads; t += stride) {
+  const int64_t ntasks = (nthreads + 31) >> 5;
+  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+    const int64_t t = g * 32 + (threadIdx.x & 31);
+    if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t row;
     int sub;
     row_of_thread<V>(t, row, sub);
@@ -375,12 +379,6 @@ __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_
   }
 }
 
-// 256-thread CTAs: one thread per row of the fine operator fits in the 1,216
-// CTAs of the reduction partials.
-static unsigned red_grid(int64_t rows) {
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 1216));
-}
-
 template <int BS, typename TM>
 static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const double* dinv, const float* wts,
                          bool scalar_diag, double* out_scal) {
@@ -389,7 +387,6 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
   const int64_t n = A->nbr, rows = row_threads_for<TM>(A);
   double* w[2] = {mg->power_w[0], mg->power_w[1]};
   double* norms = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel;  // 2 scratch slots
-  const unsigned g = red_grid(rows);
   { k_start_vector<<<(unsigned)((n * BS + 255) / 256), 256, 0, st>>>(w[0], n * BS); BAMG_COUNT_LAUNCH; }
   const int split = (BS == 6 && !scalar_diag) ? split_for<TM>(A) : 0;
   for (int it = 0; it < mg->opts.power_its; ++it) {
@@ -403,11 +400,11 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
         BAMG_COUNT_LAUNCH; })
       continue;
     }
-    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
+    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<deal_grid(k_power_step<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, scalar_diag ? nullptr : wts, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
-  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
+  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<deal_grid(k_rayleigh<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
                                                 scalar_diag ? nullptr : wts, w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
                                                 mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
