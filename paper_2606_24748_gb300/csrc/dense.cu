@@ -72,9 +72,7 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
 
 // 1 / sqrt(d) by Newton's method for the reciprocal square root,
 // y <- y + y (1 - d y^2) / 2, from the single-precision estimate; each step
-// doubles the correct bits (about 22 -> 44 -> full double precision).  FP64
-// division and square root are long instruction sequences on the FP64 pipe,
-// and the pivots of a factorisation are one long serial chain of them.
+// doubles the correct bits (about 22 -> 44 -> full double precision).
 __device__ __forceinline__ double rsqrt_newton(double d) {
   const float f = (float)d;
   double y = (f > 1e-30f && f < 1e30f) ? (double)rsqrtf(f) : 1.0 / sqrt(d);
@@ -86,37 +84,74 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
+// 1 / d from the hardware's double-precision estimate (PTX rcp.approx.ftz.f64,
+// about 20 correct bits) and one third-order step of the iteration for the
+// reciprocal: with e = 1 - d y, y (1 + e + e^2) has relative error about e^3.
+// Three dependent FP64 operations: at 64 cycles each on this part, the pivot
+// chain of a factorisation is the critical path, and a float seed costs two
+// conversions more.
+__device__ __forceinline__ double rcp_cubic(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+// d > 0 and finite, tested on the bits (an FP64 compare is another 64 cycles).
+__device__ __forceinline__ bool positive_finite(double d) {
+  const long long b = __double_as_longlong(d);
+  return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// Lower-triangle entries (i, l), i >= l, of a tile, ordered by l descending:
+// the entries right of column j are the first (kT-1-j)(kT-j)/2.  Packed as
+// i << 5 | l; built once per CTA.
+__device__ void tri_table(unsigned short* tri) {
+  for (int p = threadIdx.x; p < kT * (kT + 1) / 2; p += blockDim.x) {
+    int l = kT - 1;
+    while (l > 0 && (kT - l) * (kT + 1 - l) / 2 <= p) --l;
+    tri[p] = (unsigned short)((l + p - (kT - 1 - l) * (kT - l) / 2) << 5 | l);
+  }
+}
+
 // Cholesky of the diagonal tile (k, k) in shared memory and the inverse of
-// the factor (one CTA); L is written back, L^-1 to Linv.  Pivot j stores
-// L_jj = d / sqrt(d) and 1 / L_jj, so the column scaling and the rows of the
-// inverse multiply instead of dividing.
+// the factor (one CTA); L is written back, L^-1 to Linv.  The sweep is the
+// square-root-free form A = Lu D Lu^T: column j's pivot d_j = a_jj, then
+// a_il -= a_ij a_lj / d_j for l > j, one barrier per column, and every
+// thread forms 1 / d_j itself.  Column j is left unscaled (a_ij = Lu_ij d_j),
+// so L = Lu D^(1/2) is a_ij / sqrt(d_j) at the end: the square roots leave the
+// serial chain.
 __device__ void diag_tile(double* __restrict__ M, int64_t ld, int k, double* __restrict__ Linv, int* err,
-                          double (*a)[kT + 1], double (*w)[kT + 1]) {
+                          double (*a)[kT + 1], double (*w)[kT + 1], const unsigned short* tri) {
   __shared__ double inv[kT];
   const int tid = threadIdx.x;
   double* base = M + (int64_t)k * kT * ld + (int64_t)k * kT;
   __syncthreads();
-  for (int e = tid; e < kT * kT; e += blockDim.x) a[e / kT][e % kT] = base[(int64_t)(e / kT) * ld + e % kT];
+  for (int e = tid; e < kT * kT; e += blockDim.x) a[e / kT][e % kT] = __ldcg(base + (int64_t)(e / kT) * ld + e % kT);
   __syncthreads();
   for (int j = 0; j < kT; ++j) {
-    if (tid == 0) {
-      double d = a[j][j];
-      if (!(d > 0.0)) {
-        set_err(err, kDevBreakdown);
-        d = 1.0;
-      }
-      const double r = rsqrt_newton(d);
-      a[j][j] = d * r;
-      inv[j] = r;
+    double d = a[j][j];
+    if (!positive_finite(d)) d = 1.0;  // reported below
+    const double r = rcp_cubic(d);
+    const int cnt = (kT - 1 - j) * (kT - j) / 2;
+    for (int p = tid; p < cnt; p += blockDim.x) {
+      const int code = tri[p], i = code >> 5, l = code & 31;
+      a[i][l] = fma(-a[i][j] * r, a[l][j], a[i][l]);
     }
     __syncthreads();
-    if (tid > j && tid < kT) a[tid][j] *= inv[j];
-    __syncthreads();
-    for (int e = tid; e < kT * kT; e += blockDim.x) {
-      const int i = e / kT, l = e % kT;
-      if (l > j && i >= l) a[i][l] -= a[i][j] * a[l][j];
+  }
+  if (tid < kT) {
+    double d = a[tid][tid];
+    if (!positive_finite(d)) {
+      set_err(err, kDevBreakdown);
+      d = 1.0;
     }
-    __syncthreads();
+    inv[tid] = rsqrt_newton(d);
+  }
+  __syncthreads();
+  for (int e = tid; e < kT * kT; e += blockDim.x) {
+    const int i = e / kT, l = e % kT;
+    if (l <= i) a[i][l] *= inv[l];
   }
   // W = L^-1 by doubling the inverted diagonal blocks: with diagonal blocks
   // W11, W22 of size h already inverted, the block below them is
@@ -196,6 +231,8 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
                                                       int* err, double* F2, double* W2, double* Dinv2) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[kT][kT + 1], w[kT][kT + 1];
+  __shared__ unsigned short tri[kT * (kT + 1) / 2];
+  tri_table(tri);
   // With a second matrix (F2 != null) the two factorisations run side by side
   // on the two halves of the grid, in step with the same barriers.
   const int nm = F2 ? 2 : 1;
@@ -208,7 +245,7 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
     W = W2;
     Dinv = Dinv2;
   }
-  if (b == 0) diag_tile(F, ld, 0, Dinv, err, a, w);
+  if (b == 0) diag_tile(F, ld, 0, Dinv, err, a, w, tri);
   __threadfence();
   grid.sync();
   for (int k = 0; k < nt; ++k) {
@@ -235,7 +272,7 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
                         F + (int64_t)g * kT * ld + (int64_t)k * kT, ld, a, w);
       __syncthreads();
       __threadfence_block();
-      diag_tile(F, ld, g, Dinv + (int64_t)g * kT * kT, err, a, w);
+      diag_tile(F, ld, g, Dinv + (int64_t)g * kT * kT, err, a, w, tri);
     }
     // item 0 of the trailing update is tile (k+1,k+1), done by CTA 0 above
     for (int item = (b == 0 ? G : b); item < n_trail + n_wupd; item += G) {
