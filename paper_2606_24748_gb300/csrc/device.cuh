@@ -162,27 +162,30 @@ __device__ __forceinline__ int64_t deal_stride() { return (int64_t)gridDim.x * (
     default: { constexpr int V = 1; __VA_ARGS__; } break;  \
   }
 
-// Deterministic grid reduction of NV doubles: every CTA reduces its threads'
-// values with a fixed shuffle tree, writes its partials, and the last CTA to
-// arrive (atomic ticket) sums the partials in CTA order with a fixed tree.
-// Returns true in the last CTA; out[] is valid in its thread 0.  The counter
-// is reset by the last CTA.  blockDim.x must be a multiple of 32, <= 1024.
+// Deterministic grid reduction of NV doubles: every CTA sums its threads'
+// values in a fixed order, writes its partials, and the last CTA to arrive
+// (atomic ticket) sums the partials in CTA order the same way.  Returns true
+// in the last CTA; out[] is valid in its thread 0.  The counter is reset by
+// the last CTA.  blockDim.x must be a multiple of 32, <= 1024.
+// An FP64 add costs a warp 64 cycles of an SM sub-partition here, so the CTA
+// sum goes through shared memory: lane l of warp 0 adds the values 32 apart
+// (nw - 1 adds), then one shuffle tree (5 adds): 12 FP64 warp instructions
+// for 256 threads instead of a shuffle tree per warp (45).
 template <int NV>
 __device__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials,
                             unsigned* __restrict__ counter, double (&out)[NV]) {
-  __shared__ double sm[32][NV];
+  __shared__ double buf[NV][1024];
   __shared__ bool is_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double w = warp_sum(v[k]);
-    if (lane == 0) sm[warp][k] = w;
-  }
+  for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double w = warp_sum(lane < nw ? sm[lane][k] : 0.0);
+      double w = buf[k][lane];
+      for (int i = 1; i < nw; ++i) w += buf[k][lane + 32 * i];
+      w = warp_sum(w);
       if (lane == 0) partials[(int64_t)blockIdx.x * NV + k] = w;
     }
     if (lane == 0) {
@@ -200,17 +203,15 @@ __device__ bool grid_reduce(double (&v)[NV], double* __restrict__ partials,
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(partials + (int64_t)b * NV + k);
-  __syncthreads();
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double w = warp_sum(acc[k]);
-    if (lane == 0) sm[warp][k] = w;
-  }
+  for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = acc[k];
   __syncthreads();
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double w = warp_sum(lane < nw ? sm[lane][k] : 0.0);
+      double w = buf[k][lane];
+      for (int i = 1; i < nw; ++i) w += buf[k][lane + 32 * i];
+      w = warp_sum(w);
       if (lane == 0) out[k] = w;
     }
   }
