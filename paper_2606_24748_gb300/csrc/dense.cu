@@ -454,33 +454,65 @@ __global__ void k_band_pad(double* __restrict__ D, int64_t n, int64_t npad, int 
   D[(c * s + r) * s + r] = 1.0;
 }
 
+// Chunk matrix-vector products, kChainSplit warps per row: each warp takes
+// every kChainSplit-th group of 32 columns, and the partial sums meet in
+// shared memory in warp order.  Every product here is latency-bound (one
+// 352 x 352 chunk is 124 K multiply-adds for the whole GPU); splitting the
+// row shortens each warp's chain of dependent FP64 adds (64 cycles each) and
+// spreads the rows over more SMs.
+constexpr int kChainSplit = 4;
+constexpr int kChainRows = 8 / kChainSplit;  // rows per 256-thread CTA
+
+// Sum of the kChainSplit warps' totals for KP vectors (acc: each warp's lane
+// values); the result is valid in threads sub == 0, lane < KP of each row.
+template <int KP>
+__device__ __forceinline__ void chain_combine(double (&acc)[KP], double (*part)[KP]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < KP; ++q) acc[q] = warp_sum(acc[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < KP; ++q) part[w][q] = acc[q];
+  }
+  __syncthreads();
+  if (w % kChainSplit == 0 && lane < KP) {
+    const int w0 = w;
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChainSplit; ++k) t += part[w0 + k][lane];
+    acc[0] = t;
+  }
+}
+
 // out[k s + r] = sum_j M_k[r][j] v[k s + j] for every chunk k (rows of v at
-// or past nvalid read as 0); warp per row, KP vectors.
+// or past nvalid read as 0), KP vectors; tri = 1: M_k lower triangular
+// (j <= r), 2: upper (j >= r), 0: full.
 template <int KP, typename TI>
-__global__ void k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows, const TI* __restrict__ v,
-                           int64_t nvalid, double* __restrict__ out, const int* done) {
+__global__ void __launch_bounds__(256) k_chunk_mv(const double* __restrict__ Mats, int s, int64_t rows,
+                                                  const TI* __restrict__ v, int64_t nvalid,
+                                                  double* __restrict__ out, int tri, const int* done) {
   pdl_enter();
   if (done && *done) return;
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= rows) return;
-  const int64_t k = row / s, r = row - k * s;
-  const double* mr = Mats + (k * s + r) * s;
-  const int64_t g0 = k * s;
+  __shared__ double part[8][KP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = w % kChainSplit;
+  const int64_t row = (int64_t)blockIdx.x * kChainRows + w / kChainSplit;
   double acc[KP];
 #pragma unroll
   for (int c = 0; c < KP; ++c) acc[c] = 0.0;
-  for (int j = lane; j < s; j += 32) {
-    if (g0 + j >= nvalid) break;
-    const double wv = mr[j];
+  if (row < rows) {
+    const int64_t k = row / s, r = row - k * s;
+    const double* mr = Mats + (k * s + r) * s;
+    const int64_t g0 = k * s;
+    const int j0 = tri == 2 ? (int)r : 0, j1 = tri == 1 ? (int)r + 1 : s;
+    const int jend = (int)std::min<int64_t>(j1, nvalid - g0);
+    for (int j = j0 + sub * 32 + lane; j < jend; j += 32 * kChainSplit) {
+      const double wv = mr[j];
 #pragma unroll
-    for (int c = 0; c < KP; ++c) acc[c] = fma(wv, (double)v[(g0 + j) * KP + c], acc[c]);
+      for (int c = 0; c < KP; ++c) acc[c] = fma(wv, (double)v[(g0 + j) * KP + c], acc[c]);
+    }
   }
-#pragma unroll
-  for (int c = 0; c < KP; ++c) acc[c] = warp_sum(acc[c]);
-#pragma unroll
-  for (int c = 0; c < KP; ++c)
-    if (lane == c) out[row * KP + c] = acc[c];
+  chain_combine<KP>(acc, part);
+  if (row < rows && sub == 0 && lane < KP) out[row * KP + lane] = acc[0];
 }
 
 // One round of the solve chains: up to two jobs (blockIdx.y), each
@@ -494,33 +526,31 @@ struct ChainRound {
 };
 
 template <int KP>
-__global__ void k_chunk_chain(ChainRound c, int s, const int* done) {
+__global__ void __launch_bounds__(256) k_chunk_chain(ChainRound c, int s, const int* done) {
   pdl_enter();
   if (done && *done) return;
+  __shared__ double part[8][KP];
   const int job = blockIdx.y;
-  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= s) return;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = w % kChainSplit;
+  const int64_t r = (int64_t)blockIdx.x * kChainRows + w / kChainSplit;
   double acc[KP];
 #pragma unroll
   for (int q = 0; q < KP; ++q) acc[q] = 0.0;
-  for (int term = 0; term < 2; ++term) {
-    const double* M = term == 0 ? c.M1[job] : c.M2[job];
-    const double* z = term == 0 ? c.z1[job] : c.z2[job];
-    if (!M) continue;
-    const double* mr = M + r * s;
-    for (int j = lane; j < s; j += 32) {
-      const double wv = mr[j];
+  if (r < s) {
+    for (int term = 0; term < 2; ++term) {
+      const double* M = term == 0 ? c.M1[job] : c.M2[job];
+      const double* z = term == 0 ? c.z1[job] : c.z2[job];
+      if (!M) continue;
+      const double* mr = M + r * s;
+      for (int j = sub * 32 + lane; j < s; j += 32 * kChainSplit) {
+        const double wv = mr[j];
 #pragma unroll
-      for (int q = 0; q < KP; ++q) acc[q] = fma(wv, z[(int64_t)j * KP + q], acc[q]);
+        for (int q = 0; q < KP; ++q) acc[q] = fma(wv, z[(int64_t)j * KP + q], acc[q]);
+      }
     }
   }
-#pragma unroll
-  for (int q = 0; q < KP; ++q) acc[q] = warp_sum(acc[q]);
-  double* y = c.y[job];
-#pragma unroll
-  for (int q = 0; q < KP; ++q)
-    if (lane == q) y[r * KP + q] -= acc[q];
+  chain_combine<KP>(acc, part);
+  if (r < s && sub == 0 && lane < KP) c.y[job][r * KP + lane] -= acc[0];
 }
 
 template <typename TO>
@@ -532,6 +562,7 @@ __global__ void k_band_out(int64_t m, const double* __restrict__ x, TO* __restri
 }
 
 static unsigned warps_grid(int64_t rows) { return (unsigned)std::max<int64_t>(1, (rows * 32 + 255) / 256); }
+static unsigned chain_grid(int64_t rows) { return (unsigned)std::max<int64_t>(1, (rows + kChainRows - 1) / kChainRows); }
 
 // Half-bandwidth of the coarsest operator in dofs.
 static int64_t half_bandwidth(const bamg_bsr* A) {
@@ -656,7 +687,7 @@ static Status band_factor(bamg_mg* mg) {
 }
 template <int KP>
 static Status chain_round(const ChainRound& c, int jobs, int s, const int* done, cudaStream_t st) {
-  BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(warps_grid(s), (unsigned)jobs), dim3(256), st, c, s, done));
+  BAMG_CUDA(launch_k(k_chunk_chain<KP>, dim3(chain_grid(s), (unsigned)jobs), dim3(256), st, c, s, done));
   BAMG_COUNT_LAUNCH;
   return Status{};
 }
@@ -667,7 +698,7 @@ static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, co
   const int s = D.s, nc = D.nc, t = nc / 2;
   const int64_t ss = (int64_t)s * s, npad = D.npad, cs = (int64_t)s * KP;
   // forward: y = blockdiag(W) b, then the two chains toward the middle chunk
-  { BAMG_CUDA(launch_k(k_chunk_mv<KP, T>, dim3(warps_grid(npad)), dim3(256), st, D.Wb, s, npad, b, D.n, y, done)); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_chunk_mv<KP, T>, dim3(chain_grid(npad)), dim3(256), st, D.Wb, s, npad, b, D.n, y, 1, done)); BAMG_COUNT_LAUNCH; }
   const int fr = std::max(t - 1, nc - 2 - t);
   for (int r = 1; r <= fr; ++r) {
     ChainRound c = {};
@@ -695,7 +726,7 @@ static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, co
     BAMG_TRY(chain_round<KP>(c, 1, s, done, st));
   }
   // backward: z = blockdiag(W^T) y, then outward from the middle chunk
-  { BAMG_CUDA(launch_k(k_chunk_mv<KP, double>, dim3(warps_grid(npad)), dim3(256), st, D.Wtb, s, npad, y, npad, z, done)); BAMG_COUNT_LAUNCH; }
+  { BAMG_CUDA(launch_k(k_chunk_mv<KP, double>, dim3(chain_grid(npad)), dim3(256), st, D.Wtb, s, npad, y, npad, z, 2, done)); BAMG_COUNT_LAUNCH; }
   const int br = std::max(t, nc - 1 - t);
   for (int r = 1; r <= br; ++r) {
     ChainRound c = {};
