@@ -100,6 +100,11 @@ typedef enum {
   BAMG_PROF_COUNT = 14
 } bamg_prof_slot;
 BAMG_API bamg_status bamg_ctx_profile(bamg_ctx* ctx, int enable);
+/* Enable timing for the slots in `mask` only (bit s = slot s; 0 disables).
+ * Every bracketed launch loses its programmatic overlap with its neighbours
+ * and each pair costs two event records, so a timed run that needs one
+ * kernel's duration should bracket that kernel alone. */
+BAMG_API bamg_status bamg_ctx_profile_slots(bamg_ctx* ctx, unsigned mask);
 BAMG_API bamg_status bamg_ctx_profile_read(bamg_ctx* ctx, int slot, double* total_ms, int64_t* launches);
 /* Number of kernels this library has launched in this process (kernels run
  * through CUDA graphs included, counted per graph launch). */

@@ -57,6 +57,7 @@ _SIGS = {
     "bamg_ctx_destroy": [_P],
     "bamg_ctx_sync": [_P],
     "bamg_ctx_profile": [_P, ctypes.c_int],
+    "bamg_ctx_profile_slots": [_P, ctypes.c_uint],
     "bamg_ctx_profile_read": [_P, ctypes.c_int, _P, _P],
     "bamg_bsr_create": [_P, ctypes.c_int, ctypes.c_int, _I64, _I64, _PP],
     "bamg_bsr_destroy": [_P],
@@ -174,6 +175,14 @@ def bamg_ctx_sync(ctx):
 
 def bamg_ctx_profile(ctx, enable: int):
     _check(lib().bamg_ctx_profile(ctx, int(enable)), ctx)
+
+
+def bamg_ctx_profile_slots(ctx, slots):
+    """Time only the named slots (names of PROF_SLOTS or slot numbers); empty disables."""
+    mask = 0
+    for s in slots:
+        mask |= 1 << (PROF_SLOTS[s] if isinstance(s, str) else int(s))
+    _check(lib().bamg_ctx_profile_slots(ctx, mask), ctx)
 
 
 def bamg_ctx_profile_read(ctx, slot: int) -> tuple[float, int]:

@@ -35,7 +35,7 @@ static cudaError_t record(cudaEvent_t e, cudaStream_t st) {
 }
 
 int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st) {
-  if (!ctx || !ctx->prof.on || slot < 0) return -1;
+  if (!ctx || !ctx->prof.on || slot < 0 || !((ctx->prof.mask >> slot) & 1u)) return -1;
   int idx = -1;
   ProfPair* q = prof_slot_pair(ctx, &idx);
   if (!q) return -1;
@@ -316,10 +316,15 @@ bamg_status bamg_ctx_destroy(bamg_ctx* c) {
 const char* bamg_last_error(const bamg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 bamg_status bamg_ctx_profile(bamg_ctx* c, int enable) {
+  return bamg_ctx_profile_slots(c, enable ? ~0u : 0u);
+}
+
+bamg_status bamg_ctx_profile_slots(bamg_ctx* c, unsigned mask) {
   if (!c) return BAMG_ERR_INVALID;
   Prof& p = c->prof;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, cuda_status(cudaGetLastError(), "profile"));
-  p.on = enable != 0;
+  p.on = mask != 0;
+  p.mask = mask;
   p.epoch++;
   p.eager_used = 0;
   for (int k = 0; k < BAMG_PROF_COUNT; ++k) {

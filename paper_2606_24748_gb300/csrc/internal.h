@@ -60,6 +60,7 @@ struct ProfPair {
 
 struct Prof {
   bool on = false;
+  unsigned mask = ~0u;  // slots that are timed while on
   uint64_t epoch = 0;
   std::vector<ProfPair> eager;
   size_t eager_used = 0;

@@ -234,6 +234,28 @@ def test_cg_matches_oracle(ne):
         gp.close()
 
 
+def test_profiling_slots_time_only_the_chosen_kernels():
+    """A slot mask brackets only the chosen launches; the solve is unchanged."""
+    ne = 16
+    gp = GpuProblem(ne)
+    try:
+        b = torch.from_numpy(body_force(gp.mesh)).cuda()
+        x0 = torch.zeros_like(b)
+        out0 = B.bamg_cg_solve(gp.ctx, gp.mg, b, x0, 1e-8, 200)
+        B.bamg_ctx_profile_slots(gp.ctx, ["cheb_step_l0", "cg_ap"])
+        x1 = torch.zeros_like(b)
+        out1 = B.bamg_cg_solve(gp.ctx, gp.mg, b, x1, 1e-8, 200)
+        got = {k: B.bamg_ctx_profile_read(gp.ctx, s) for k, s in B.PROF_SLOTS.items()}
+        B.bamg_ctx_profile(gp.ctx, 0)
+        its = out1["iterations"]
+        assert abs(got["cg_ap"][1] - its) <= 1 and got["cg_ap"][0] > 0
+        assert got["cheb_step_l0"][1] > 0
+        assert all(v[1] == 0 for k, v in got.items() if k not in ("cheb_step_l0", "cg_ap"))
+        assert its == out0["iterations"] and torch.equal(x0, x1)
+    finally:
+        gp.close()
+
+
 def test_hot_update_matches_oracle():
     ne = 13
     h = hierarchy(ne)
