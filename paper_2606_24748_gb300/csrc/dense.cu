@@ -385,10 +385,15 @@ __global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, c
 // CTA (256 threads, 4 outputs each); with lower_only, tiles above the
 // diagonal are skipped.
 constexpr int kGemmBatch = 8;
+// tri: which operand is triangular, so that whole zero tiles of the K loop
+// are skipped: 0 none, 1 A lower (K tiles <= ti), 2 A upper (>= ti),
+// 3 op(B) upper, i.e. B lower and transposed (<= tj).
+enum GemmTri : int { kTriNone = 0, kTriALower = 1, kTriAUpper = 2, kTriBtUpper = 3 };
 struct GemmBatch {
   double* C[kGemmBatch];
   const double* A[kGemmBatch];
   const double* B[kGemmBatch];
+  int tri[kGemmBatch];
 };
 
 template <bool kTransB>
@@ -400,8 +405,11 @@ __global__ void __launch_bounds__(256) k_chunk_gemm(GemmBatch g, int s, double a
   const double* __restrict__ B = g.B[blockIdx.z];
   __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
   const int tid = threadIdx.x, c = tid % kT, r0 = tid / kT;
+  const int tri = g.tri[blockIdx.z];
+  const int k0 = tri == kTriAUpper ? ti : 0;
+  const int k1 = tri == kTriALower ? ti + 1 : (tri == kTriBtUpper ? tj + 1 : s / kT);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int kt = 0; kt < s / kT; ++kt) {
+  for (int kt = k0; kt < k1; ++kt) {
     __syncthreads();
     for (int e = tid; e < kT * kT; e += blockDim.x) {
       const int i = e / kT, j = e % kT;
@@ -585,16 +593,24 @@ static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld
   return Status{};
 }
 
+struct GemmItem {
+  double* C;
+  const double* A;
+  const double* B;
+  int tri;
+};
+
 template <bool kTransB>
-static Status gemm_batch(const std::vector<std::array<const double*, 3>>& items, int s, double alpha, double beta,
-                         int lower_only, cudaStream_t st) {
+static Status gemm_batch(const std::vector<GemmItem>& items, int s, double alpha, double beta, int lower_only,
+                         cudaStream_t st) {
   for (size_t i0 = 0; i0 < items.size(); i0 += kGemmBatch) {
     GemmBatch g = {};
     const int cnt = (int)std::min<size_t>(kGemmBatch, items.size() - i0);
     for (int q = 0; q < cnt; ++q) {
-      g.C[q] = const_cast<double*>(items[i0 + q][0]);
-      g.A[q] = items[i0 + q][1];
-      g.B[q] = items[i0 + q][2];
+      g.C[q] = items[i0 + q].C;
+      g.A[q] = items[i0 + q].A;
+      g.B[q] = items[i0 + q].B;
+      g.tri[q] = items[i0 + q].tri;
     }
     const dim3 grid((unsigned)(s / kT), (unsigned)(s / kT), (unsigned)cnt);
     k_chunk_gemm<kTransB><<<grid, 256, 0, st>>>(g, s, alpha, beta, lower_only);
@@ -650,9 +666,9 @@ static Status band_factor(bamg_mg* mg) {
   for (int r = 0; r < rounds; ++r) {
     const int kt = r < t ? r : -1;
     const int kb = (nc - 1 - r > t) ? nc - 1 - r : -1;
-    std::vector<std::array<const double*, 3>> syrk, panel;
-    if (kt > 0) syrk.push_back({Dk(kt), BC(kt - 1), BC(kt - 1)});
-    if (kb >= 0 && kb < nc - 1) syrk.push_back({Dk(kb), BC(kb + 1), BC(kb + 1)});
+    std::vector<GemmItem> syrk, panel;
+    if (kt > 0) syrk.push_back({Dk(kt), BC(kt - 1), BC(kt - 1), kTriNone});
+    if (kb >= 0 && kb < nc - 1) syrk.push_back({Dk(kb), BC(kb + 1), BC(kb + 1), kTriNone});
     if (!syrk.empty()) BAMG_TRY(gemm_batch<true>(syrk, s, -1.0, 1.0, 1, st));
     if (kt >= 0 && kb >= 0)
       BAMG_TRY(cooperative_factor(ctx, Dk(kt), Wk(kt), s, ntl, D.dinv_tiles, Dk(kb), Wk(kb), dt1));
@@ -660,25 +676,26 @@ static Status band_factor(bamg_mg* mg) {
       BAMG_TRY(cooperative_factor(ctx, Dk(kt >= 0 ? kt : kb), Wk(kt >= 0 ? kt : kb), s, ntl, D.dinv_tiles));
     for (int k : {kt, kb})
       if (k >= 0) { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(k), Wt(k), s); BAMG_COUNT_LAUNCH; }
-    if (kt >= 0) panel.push_back({BC(kt), D.Sub + kt * ss, Wk(kt)});          // B_k = A_{k+1,k} W_k^T
-    if (kb >= 0) panel.push_back({BC(kb), D.Sup + (kb - 1) * ss, Wk(kb)});    // C_k = A_{k-1,k} W_k^T
+    // B_k = A_{k+1,k} W_k^T, C_k = A_{k-1,k} W_k^T (W_k lower triangular)
+    if (kt >= 0) panel.push_back({BC(kt), D.Sub + kt * ss, Wk(kt), kTriBtUpper});
+    if (kb >= 0) panel.push_back({BC(kb), D.Sup + (kb - 1) * ss, Wk(kb), kTriBtUpper});
     BAMG_TRY(gemm_batch<true>(panel, s, 1.0, 0.0, 0, st));
   }
   // middle chunk: both Schur complements, then its factor
   {
-    std::vector<std::array<const double*, 3>> syrk;
-    if (t > 0) syrk.push_back({Dk(t), BC(t - 1), BC(t - 1)});
-    if (t + 1 < nc) syrk.push_back({Dk(t), BC(t + 1), BC(t + 1)});
+    std::vector<GemmItem> syrk;
+    if (t > 0) syrk.push_back({Dk(t), BC(t - 1), BC(t - 1), kTriNone});
+    if (t + 1 < nc) syrk.push_back({Dk(t), BC(t + 1), BC(t + 1), kTriNone});
     for (auto& it : syrk) BAMG_TRY(gemm_batch<true>({it}, s, -1.0, 1.0, 1, st));  // same output: one at a time
     BAMG_TRY(cooperative_factor(ctx, Dk(t), Wk(t), s, ntl, D.dinv_tiles));
     { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(t), Wt(t), s); BAMG_COUNT_LAUNCH; }
   }
   // chain matrices, off the critical path: all in two batched launches
-  std::vector<std::array<const double*, 3>> nn, nt;
-  for (int k = 1; k <= t; ++k) nn.push_back({D.Mb + k * ss, Wk(k), BC(k - 1)});    // M_k = W_k B_{k-1}
-  for (int k = t; k + 1 < nc; ++k) nn.push_back({D.Mtb + k * ss, Wk(k), BC(k + 1)}); // Mt_k = W_k C_{k+1}
-  for (int k = 0; k < t; ++k) nt.push_back({D.Nb + k * ss, Wt(k), BC(k)});         // N_k = W_k^T B_k^T
-  for (int k = t + 1; k < nc; ++k) nt.push_back({D.Ntb + k * ss, Wt(k), BC(k)});    // Nt_k = W_k^T C_k^T
+  std::vector<GemmItem> nn, nt;
+  for (int k = 1; k <= t; ++k) nn.push_back({D.Mb + k * ss, Wk(k), BC(k - 1), kTriALower});     // M_k = W_k B_{k-1}
+  for (int k = t; k + 1 < nc; ++k) nn.push_back({D.Mtb + k * ss, Wk(k), BC(k + 1), kTriALower});  // Mt_k = W_k C_{k+1}
+  for (int k = 0; k < t; ++k) nt.push_back({D.Nb + k * ss, Wt(k), BC(k), kTriAUpper});          // N_k = W_k^T B_k^T
+  for (int k = t + 1; k < nc; ++k) nt.push_back({D.Ntb + k * ss, Wt(k), BC(k), kTriAUpper});     // Nt_k = W_k^T C_k^T
   BAMG_TRY(gemm_batch<false>(nn, s, 1.0, 0.0, 0, st));
   BAMG_TRY(gemm_batch<true>(nt, s, 1.0, 0.0, 0, st));
   prof_end(ctx, pm, st);
