@@ -20,6 +20,7 @@
 namespace bamg {
 
 constexpr int kT = 32;  // tile size
+constexpr int kFactorCounters = 32;  // two context counters: quarter updates done, per matrix
 
 template <typename TM, int BS>
 __global__ void k_dense_fill(int64_t nnzb, const int* __restrict__ rowptr_rows, const int* __restrict__ colidx,
@@ -68,6 +69,21 @@ __device__ __forceinline__ void tile_update(double* __restrict__ C, const double
     double* p = C + (int64_t)(r0 + 8 * q) * ld + c;
     *p = kSyrk ? *p - acc[q] : *p + acc[q];
   }
+}
+
+// Rows [r0, r0 + 8) of C -= A A^T for a 32 x 32 tile C and a 32 x 32 tile A
+// (one quarter of a diagonal-tile update; 256 threads, one output each).
+__device__ __forceinline__ void tile_syrk_rows8(double* __restrict__ C, const double* __restrict__ Ab, int64_t ld,
+                                                int r0, double (*As)[kT + 1], double (*Bs)[kT + 1]) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  for (int e = tid; e < kT * kT; e += blockDim.x) Bs[e / kT][e % kT] = Ab[(int64_t)(e / kT) * ld + e % kT];
+  __syncthreads();
+  const int r = tid / kT, c = tid % kT;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int l = 0; l < kT; ++l) acc = fma(Bs[r0 + r][l], Bs[c][l], acc);
+  C[(int64_t)(r0 + r) * ld + c] -= acc;
 }
 
 // 1 / sqrt(d) by Newton's method for the reciprocal square root,
@@ -228,7 +244,8 @@ __device__ void winv_cols(double* __restrict__ St, int64_t ld, const double* __r
 // so each step needs two barriers, and the inverse's updates fill the SMs
 // that the shrinking trailing matrix leaves idle.
 __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int64_t ld, int nt, double* Dinv,
-                                                      int* err, double* F2, double* W2, double* Dinv2) {
+                                                      int* err, double* F2, double* W2, double* Dinv2,
+                                                      unsigned* qctr) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[kT][kT + 1], w[kT][kT + 1];
   __shared__ unsigned short tri[kT * (kT + 1) / 2];
@@ -263,22 +280,43 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
     }
     __threadfence();
     grid.sync();
-    // phase 2
+    // phase 2: items 0-3 are the four 8-row quarters of the next diagonal
+    // tile's update (CTAs 1-4 take them first and count them in qctr), then
+    // the rest of the trailing update and the inverse's updates; CTA 0 waits
+    // for the quarters and factors that tile meanwhile.
     const int T = nt - k - 1;
     const int n_trail = T * (T + 1) / 2, n_wupd = T * (k + 1);
+    const int n_items = T > 0 ? 4 + (n_trail - 1) + n_wupd : 0;
     if (b == 0 && T > 0) {
       const int g = k + 1;
-      tile_update<true>(F + (int64_t)g * kT * ld + (int64_t)g * kT, F + (int64_t)g * kT * ld + (int64_t)k * kT,
-                        F + (int64_t)g * kT * ld + (int64_t)k * kT, ld, a, w);
+      if (threadIdx.x == 0) {
+        const unsigned target = 4u * (unsigned)(k + 1);
+        int spins = 0;
+        while (atomicAdd(qctr + mi, 0u) < target) {
+          if (++spins > (1 << 22)) {  // about 0.4 s: record and go on rather than wait forever
+            set_err(err, kDevTimeout);
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence();
+      }
       __syncthreads();
-      __threadfence_block();
       diag_tile(F, ld, g, Dinv + (int64_t)g * kT * kT, err, a, w, tri);
     }
-    // item 0 of the trailing update is tile (k+1,k+1), done by CTA 0 above
-    for (int item = (b == 0 ? G : b); item < n_trail + n_wupd; item += G) {
-      if (item == 0) continue;
-      if (item < n_trail) {
-        int idx = item, i = 0;
+    for (int item = b - 1; b > 0 && item < n_items; item += G - 1) {
+      if (item < 4) {
+        const int g = k + 1;
+        tile_syrk_rows8(F + (int64_t)g * kT * ld + (int64_t)g * kT, F + (int64_t)g * kT * ld + (int64_t)k * kT, ld,
+                        item * 8, a, w);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(qctr + mi, 1u);
+        continue;
+      }
+      const int it0 = item - 4 + 1;  // trailing item 0 is the diagonal tile, done above in quarters
+      if (it0 < n_trail) {
+        int idx = it0, i = 0;
         while (idx > i) {  // row-major lower triangle (i, j), j <= i
           idx -= i + 1;
           ++i;
@@ -288,7 +326,7 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
                           F + (int64_t)gi * kT * ld + (int64_t)k * kT, F + (int64_t)gj * kT * ld + (int64_t)k * kT,
                           ld, a, w);
       } else {
-        const int it = item - n_trail;
+        const int it = it0 - n_trail;
         const int r = k + 1 + it / (k + 1), j = it % (k + 1);
         tile_update<false>(W + (int64_t)r * kT * ld + (int64_t)j * kT, F + (int64_t)r * kT * ld + (int64_t)k * kT,
                            W + (int64_t)k * kT * ld + (int64_t)j * kT, ld, a, w);
@@ -586,8 +624,11 @@ static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld
   BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
   if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
   const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
+  if (grid / (F2 ? 2 : 1) < 5) return make_status(BAMG_ERR_CUDA, "dense factor needs at least five CTAs per matrix");
   int* err = ctx->d_err;
-  void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2};
+  unsigned* qctr = ctx->d_counters + kFactorCounters;
+  BAMG_CUDA(cudaMemsetAsync(qctr, 0, 2 * sizeof(unsigned), ctx->stream));
+  void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2, &qctr};
   BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, ctx->stream));
   BAMG_COUNT_LAUNCH;
   return Status{};
