@@ -535,7 +535,9 @@ __global__ void __launch_bounds__(256, 8) k_cg_Ap(const int* __restrict__ sp, co
   if (s->done) return;
   double local[1] = {0.0};
   const int64_t ntasks = (nthreads + 31) >> 5;
-  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+  int64_t t0, t1;
+  deal_range(ntasks, t0, t1);
+  for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t i;
@@ -634,7 +636,9 @@ __global__ void __launch_bounds__(256, 8) k_true_residual(const int* __restrict_
   pdl_enter();
   double local[1] = {0.0};
   const int64_t ntasks = (nthreads + 31) >> 5;
-  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+  int64_t t0, t1;
+  deal_range(ntasks, t0, t1);
+  for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t i;

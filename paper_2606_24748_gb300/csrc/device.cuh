@@ -143,13 +143,18 @@ __device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub)
 }
 
 // Balanced deal of warp tasks (32 consecutive virtual threads) for the
-// one-wave reducing row kernels: task g goes to CTA g mod grid, warp
-// (g / grid) mod W of it.  With a grid of SMs x resident CTAs every SM then
-// gets the same number of tasks to within one per CTA; numbering threads
-// straight through leaves some SMs a whole CTA short for the entire kernel.
-// Loop: for (g = deal_first(); g < ntasks; g += deal_stride()).
-__device__ __forceinline__ int64_t deal_first() { return blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5); }
-__device__ __forceinline__ int64_t deal_stride() { return (int64_t)gridDim.x * (blockDim.x >> 5); }
+// one-wave reducing row kernels: CTA c takes a contiguous run of tasks, the
+// runs differing in length by at most one, and its warps take every W-th
+// task of the run.  With a grid of SMs x resident CTAs every SM then gets the
+// same number of rows to within one task per CTA (numbering threads straight
+// through leaves some SMs a whole CTA short for the entire kernel), and
+// neighbouring rows stay in one CTA, where they share gathered x in L1.
+// Loop: for (g = t0 + warp; g < t1; g += W) after deal_range(ntasks, t0, t1).
+__device__ __forceinline__ void deal_range(int64_t ntasks, int64_t& t0, int64_t& t1) {
+  const int64_t G = gridDim.x, c = blockIdx.x, q = ntasks / G, rem = ntasks - q * G;
+  t0 = c * q + (c < rem ? c : rem);
+  t1 = t0 + q + (c < rem ? 1 : 0);
+}
 
 // Run `body` with the compile-time lane count matching v (1..32).
 #define BAMG_DISPATCH_V(v, ...)                \

@@ -22,8 +22,8 @@ constexpr int kRowThreads = 128;
 constexpr int kRedBlocks = 608;
 constexpr int kRedGridMax = 8192;  // CTAs of a reducing row kernel (one partial slot each)
 
-// Grid of a one-wave reducing row kernel with 256-thread CTAs (deal_first /
-// deal_stride): the SMs times the CTAs of `kernel` resident on one, all of
+// Grid of a one-wave reducing row kernel with 256-thread CTAs (deal_range):
+// the SMs times the CTAs of `kernel` resident on one, all of
 // them even when the rows would fit in fewer (the deal spreads the tasks
 // over every CTA), but no more CTAs than warp tasks.
 template <typename K>

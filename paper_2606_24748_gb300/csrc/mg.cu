@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(256, 8) k_power_step(const int* __restrict__ s
   const double s = norm_in ? 1.0 / *norm_in : 1.0;
   double local[1] = {0.0};
   const int64_t ntasks = (nthreads + 31) >> 5;
-  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+  int64_t t0, t1;
+  deal_range(ntasks, t0, t1);
+  for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t row;
@@ -332,7 +334,9 @@ __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_
   constexpr int B = BS * BS;
   double local[2] = {0.0, 0.0};
   const int64_t ntasks = (nthreads + 31) >> 5;
-  for (int64_t g = deal_first(); g < ntasks; g += deal_stride()) {
+  int64_t t0, t1;
+  deal_range(ntasks, t0, t1);
+  for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
     int64_t row;
