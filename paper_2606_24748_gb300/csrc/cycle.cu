@@ -12,6 +12,7 @@
 // one CUDA graph and launched in batches without a host round trip per
 // iteration.
 #include <algorithm>
+#include <type_traits>
 
 #include "device.cuh"
 #include "internal.h"
@@ -397,6 +398,63 @@ static Status transfer_prof(bamg_mg* mg, const bamg_bsr* M, const T* vals, const
   Status s = transfer<BR, BC, T>(M, vals, v, y, accumulate, done, st);
   prof_end(mg->ctx, pt, st);
   return s;
+}
+
+// Warps per component of a coarse level's smoother: the lanes autotuner times
+// the plain product, and the fused Chebyshev kernels of the same matrix can
+// prefer another split.  Time the level's own pre- and post-smoothing with 1,
+// 2 and 4 warps per component and keep the fastest.  Only for levels the
+// autotuner put in the split form; the level's vectors are scratch here.
+template <typename T>
+static Status tune_smoother_split(bamg_mg* mg, int l) {
+  Level& L = mg->levels[l];
+  bamg_bsr* A = L.A;
+  int& split = std::is_same<T, double>::value ? A->split : A->split32;
+  if (L.bs != 6 || A->bc != 6 || split < 1 || split > 4) return Status{};
+  cudaStream_t st = mg->ctx->stream;
+  cudaEvent_t e0, e1;
+  BAMG_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return make_status(BAMG_ERR_CUDA, "event");
+  }
+  Status s;
+  const int keep = split;
+  float best = 1e30f;
+  int best_vs = keep;
+  for (int vs : {1, 2, 4}) {
+    split = vs;
+    for (int w = 0; w < 2 && s.ok(); ++w) {
+      s = smooth_down<6, T>(mg, l, nullptr, st);
+      if (s.ok()) s = smooth_up<6, T>(mg, l, nullptr, st);
+    }
+    float t[5];
+    for (int rep = 0; rep < 5 && s.ok(); ++rep) {
+      cudaEventRecord(e0, st);
+      s = smooth_down<6, T>(mg, l, nullptr, st);
+      if (s.ok()) s = smooth_up<6, T>(mg, l, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess)
+        s = make_status(BAMG_ERR_CUDA, "smoother timing");
+    }
+    if (!s.ok()) break;
+    std::sort(t, t + 5);
+    if (t[2] < best) {
+      best = t[2];
+      best_vs = vs;
+    }
+  }
+  split = s.ok() ? best_vs : keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+Status mg_tune_smoothers(bamg_mg* mg) {
+  const int nl = (int)mg->levels.size();
+  for (int l = 1; l + 1 < nl; ++l)
+    BAMG_TRY(mg->opts.precision == BAMG_FP32 ? tune_smoother_split<float>(mg, l) : tune_smoother_split<double>(mg, l));
+  return Status{};
 }
 
 template <typename T>

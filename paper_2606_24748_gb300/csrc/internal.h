@@ -389,6 +389,7 @@ Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st);  // features -> 
 Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st);  // FP64 pre-smoothing of level l (b -> x, r)
 Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st);     // levels[l+1].b = R_l r_l
 Status mg_precond(bamg_mg* mg, const double* r, double* z, cudaStream_t st);  // one V-cycle
+Status mg_tune_smoothers(bamg_mg* mg);  // warps per component of the coarse smoothers, by timing them
 // The phases of one PCG solve on stream st (the batch solver captures them):
 // setup, r = b, z = M r, p = z; one iteration (every kernel returns at once
 // when the solve is done); x = the iterate, ||b - A x||^2 into *true_r2.

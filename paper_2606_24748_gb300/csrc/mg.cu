@@ -810,6 +810,7 @@ bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, cons
       if (s.ok() && L.P) s = bsr_autotune(L.P, nullptr);
       if (s.ok() && L.R) s = bsr_autotune(L.R, nullptr);
     }
+    if (s.ok()) s = mg_tune_smoothers(mg);
   }
   if (s.ok()) s = check_device_error(ctx);
   if (!s.ok()) {
