@@ -43,7 +43,7 @@ MAXIT = 500
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/traffic_cheb_step_l0_64cubed_fp64.md), with a fingerprint of the
 # kernel's sources at capture time; reported as null once they change.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.4e6, "d6f05f6416bb9f07")}
+TRAFFIC = {("cheb_step_l0", 64, False): (589.5e6, "2afcb46c5b2bd38c")}
 TRAFFIC_SOURCES = ("paper_2606_24748_gb300/csrc/device.cuh", "paper_2606_24748_gb300/csrc/cycle.cu")
 
 
