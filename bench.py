@@ -301,11 +301,13 @@ def run_ours(args):
     # inside the timed region only the roofline candidates are bracketed by
     # events (each bracket costs the kernel its overlap with its neighbours)
     B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
+    lib_setup_bytes, _ = B.bamg_device_memory(wl.ctx, reset_peak=True)
     launches0 = B.bamg_kernel_launches()
     clocks.start()
     ms, outs = timed(torch, dist, lambda k: wl.step(W + k), K)
     clk = clocks.stop()
     launches = B.bamg_kernel_launches() - launches0
+    _, lib_peak_bytes = B.bamg_device_memory(wl.ctx)
     prof = {name: B.bamg_ctx_profile_read(wl.ctx, slot) for name, slot in B.PROF_SLOTS.items()}
     # every slot, in a separate untimed pass (the per-kernel breakdown)
     B.bamg_ctx_profile(wl.ctx, 1)
@@ -339,8 +341,17 @@ def run_ours(args):
         "kernel_ms": {k: {"total_ms": round(v[0], 3), "launches": v[1]} for k, v in table.items()},
         "kernel_ms_steps": KERNEL_TABLE_STEPS,
     }
+    free_b, total_b = torch.cuda.mem_get_info()
+    result["memory_gb"] = {
+        "library_after_setup": round(lib_setup_bytes / 1e9, 3),
+        "library_peak_in_timed_steps": round(lib_peak_bytes / 1e9, 3),
+        "resident_inputs": round(torch.cuda.max_memory_allocated() / 1e9, 3),
+        "device_used": round((total_b - free_b) / 1e9, 3),
+        "note": "library = its stream-ordered pool allocations (hierarchy, plans, vectors); "
+                "inputs = the value streams and vectors bench.py keeps resident through torch"}
     # phases (separate, untimed pass for the breakdown)
     result["phases_ms"] = phases(wl, torch, B)
+    result["ptap_reuse"] = ptap_reuse(wl, torch, B)
     if not args.no_e2e:
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
     if not args.no_multi and args.precision == "fp64" and rank == 0 and world == 1:
@@ -421,6 +432,33 @@ def roofline(wl, prof, B):
         out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 3), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"})
     return out
+
+
+def ptap_reuse(wl, torch, B):
+    """Finest-level Galerkin product with a fresh symbolic plan (symbolic plus
+    the first numeric pass) against the numeric pass alone on a cached plan."""
+    A0, P0 = B.bamg_mg_get_level(wl.mg, 0)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan, Ac = B.bamg_ptap_symbolic(wl.ctx, A0, P0)
+    B.bamg_ptap_numeric(wl.ctx, plan, A0, P0, Ac)
+    torch.cuda.synchronize()
+    both = (time.perf_counter() - t0) * 1e3
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        B.bamg_ptap_numeric(wl.ctx, plan, A0, P0, Ac)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    B.bamg_ptap_destroy(plan)
+    B.bamg_bsr_destroy(Ac)
+    num = sorted(ts)[2]
+    return {"level": 0, "symbolic_plus_numeric_ms": round(both, 2), "numeric_ms": round(num, 3),
+            "ratio": round(both / num, 1),
+            "timing": "symbolic + first numeric: host clock around synchronised calls; numeric: CUDA events, median of 5"}
 
 
 def phases(wl, torch, B):

@@ -109,6 +109,12 @@ BAMG_API bamg_status bamg_ctx_profile_read(bamg_ctx* ctx, int slot, double* tota
 /* Number of kernels this library has launched in this process (kernels run
  * through CUDA graphs included, counted per graph launch). */
 BAMG_API uint64_t bamg_kernel_launches(void);
+/* Device memory of the library on the context's device: every library
+ * allocation is stream-ordered from the device's default memory pool, so the
+ * pool's bytes in use and their high-water mark (since the last reset) are the
+ * library's own.  Either output may be NULL; reset_peak != 0 restarts the
+ * high-water mark at the current use after reading it. */
+BAMG_API bamg_status bamg_device_memory(bamg_ctx* ctx, uint64_t* in_use, uint64_t* peak, int reset_peak);
 
 /* ------------------------------------------------------- block matrices */
 

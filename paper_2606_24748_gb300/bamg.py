@@ -58,6 +58,7 @@ _SIGS = {
     "bamg_ctx_sync": [_P],
     "bamg_ctx_profile": [_P, ctypes.c_int],
     "bamg_ctx_profile_slots": [_P, ctypes.c_uint],
+    "bamg_device_memory": [_P, _P, _P, ctypes.c_int],
     "bamg_ctx_profile_read": [_P, ctypes.c_int, _P, _P],
     "bamg_bsr_create": [_P, ctypes.c_int, ctypes.c_int, _I64, _I64, _PP],
     "bamg_bsr_destroy": [_P],
@@ -189,6 +190,13 @@ def bamg_ctx_profile_read(ctx, slot: int) -> tuple[float, int]:
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(lib().bamg_ctx_profile_read(ctx, int(slot), ctypes.byref(ms), ctypes.byref(n)), ctx)
     return ms.value, n.value
+
+
+def bamg_device_memory(ctx, reset_peak: bool = False) -> tuple[int, int]:
+    """(bytes in use, high-water mark) of the library's device allocations."""
+    used, peak = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().bamg_device_memory(ctx, ctypes.byref(used), ctypes.byref(peak), int(reset_peak)), ctx)
+    return used.value, peak.value
 
 
 def bamg_kernel_launches() -> int:

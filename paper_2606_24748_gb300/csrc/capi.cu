@@ -347,6 +347,24 @@ bamg_status bamg_ctx_profile_read(bamg_ctx* c, int slot, double* total_ms, int64
 
 uint64_t bamg_kernel_launches(void) { return g_launches.load(); }
 
+bamg_status bamg_device_memory(bamg_ctx* c, uint64_t* in_use, uint64_t* peak, int reset_peak) {
+  if (!c) return BAMG_ERR_INVALID;
+  cudaMemPool_t pool;
+  uint64_t used = 0, high = 0;  // the attributes are 64-bit counts
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess)
+    return fail(c, cuda_status(cudaGetLastError(), "memory pool attributes"));
+  if (in_use) *in_use = (uint64_t)used;
+  if (peak) *peak = (uint64_t)high;
+  if (reset_peak) {
+    uint64_t zero = 0;  // the pool restarts the mark at the current use
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess)
+      return fail(c, cuda_status(cudaGetLastError(), "memory pool reset"));
+  }
+  return BAMG_OK;
+}
+
 bamg_status bamg_ctx_sync(bamg_ctx* c) {
   if (!c) return BAMG_ERR_INVALID;
   Status s = check_device_error(c);

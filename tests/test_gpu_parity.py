@@ -256,6 +256,23 @@ def test_profiling_slots_time_only_the_chosen_kernels():
         gp.close()
 
 
+def test_device_memory_counts_the_library_allocations():
+    """The pool counters see a hierarchy's allocations and their high-water mark."""
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    try:
+        used0, _ = B.bamg_device_memory(ctx, reset_peak=True)
+        gp = GpuProblem(12)
+        try:
+            used1, peak1 = B.bamg_device_memory(gp.ctx)
+            assert used1 > used0 and peak1 >= used1
+        finally:
+            gp.close()
+        used2, peak2 = B.bamg_device_memory(ctx)
+        assert used2 < used1 and peak2 >= peak1
+    finally:
+        B.bamg_ctx_destroy(ctx)
+
+
 def test_hot_update_matches_oracle():
     ne = 13
     h = hierarchy(ne)
