@@ -239,7 +239,9 @@ typedef struct {
                                (FP32 operators, smoother and vectors; FP64 CG,
                                eigen-estimates and coarsest solve) */
   int autotune;             /* 1 (default): bamg_bsr_autotune every level's
-                               operator, prolongator and restriction at setup */
+                               operator, prolongator and restriction at setup,
+                               then time each coarse level's own smoothing pass
+                               to pick its warps per component */
   int coarse_solver;        /* coarsest-level exact solve: 0 (default) = banded
                                block-tridiagonal Cholesky when the level's
                                half-bandwidth splits it into >= 3 chunks, else
