@@ -19,4 +19,5 @@ Modules
   splitmix     the splitmix64 counter-based generator (start vectors)
   learned      features, targets, MLP and Adam of the learned smoother weights
   multi_rhs    many right-hand sides: the cycle and CG column by column
+  strength     block-norm strength graph, Luby MIS and MIS aggregates (Sec. 2.2, 3.2, 6)
 """
