@@ -181,6 +181,42 @@ BAMG_API bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms);
 BAMG_API bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes);
 BAMG_API bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes);
 
+/* ---- Block operator inspection and the aggregation graph (Sec. 2.2, 3.2, 6) */
+
+/* Frobenius norm of every stored block (Sec. 3.2: the block norm is the
+ * coupling weight), in block-CSR order (block rows in order, columns
+ * ascending), into the device array out (nnzb doubles).  3x3, 3x6, 6x3 and
+ * 6x6 blocks; needs current FP64 values (BAMG_ERR_STATE after an FP32-only
+ * product). */
+BAMG_API bamg_status bamg_bsr_block_norms(bamg_bsr* A, double* out);
+typedef enum { BAMG_NORM_FROBENIUS = 0, BAMG_NORM_INFINITY = 1 } bamg_norm_type;
+/* Norm of the whole matrix taken over its blocks: Frobenius, or the largest
+ * absolute scalar row sum.  *out is a host double; waits for the stream. */
+BAMG_API bamg_status bamg_bsr_norm(bamg_bsr* A, int type, double* out);
+/* Strength-of-connection graph of a square block operator (Sec. 2.2 with the
+ * block norm of Sec. 3.2).  With s the sum of a block's squared entries
+ * (row-major, each product and sum rounded apart), j is a strong neighbour of
+ * block row i when j != i, s_ij > 0 and s_ij^2 >= (eps^4 s_ii) s_jj, which is
+ * ||A_ij||_F >= eps sqrt(||A_ii||_F ||A_jj||_F) decided without a square root.
+ * Output: CSR graph in caller-owned device arrays, rowptr (nbr + 1 ints) and
+ * col (col_capacity ints; neighbours in ascending order); *nedges (host) gets
+ * the edge count.  BAMG_ERR_INVALID if col_capacity < edges (nnzb always
+ * suffices) or eps < 0.  Waits for the stream once (the edge count). */
+BAMG_API bamg_status bamg_strength_graph(bamg_bsr* A, double eps, int* rowptr, int* col, int64_t col_capacity,
+                                         int64_t* nedges);
+/* Device MIS coarsening (Sec. 6) of a symmetric CSR graph of n vertices
+ * (device arrays rowptr, col).  Vertex weights are splitmix64(i, seed) with
+ * ties broken by i; Luby rounds (enter when beating every non-excluded
+ * neighbour, then exclude the neighbours of entered vertices) reach the greedy
+ * maximal independent set in descending (weight, i) order.  Aggregates: one
+ * per set vertex, numbered in vertex order; every other vertex joins its
+ * neighbour in the set of largest (weight, j).  agg: device array of n ints
+ * (caller-owned); *n_agg and *rounds (host) get the aggregate and round
+ * counts.  Waits for the stream after every round.  A graph that is not
+ * symmetric can leave a vertex without a set neighbour: BAMG_ERR_INVALID. */
+BAMG_API bamg_status bamg_mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rowptr, const int* col, uint64_t seed,
+                                        int* agg, int64_t* n_agg, int* rounds);
+
 /* Residual norm ||b - A x||_2 for a square operator with 3x3 or 6x6 blocks,
  * written to *norm (device double) on A's context stream; x, b are device
  * FP64 vectors.  This entry point allocates no device memory at all, for

@@ -25,6 +25,8 @@ STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG
  BAMG_ERR_NOT_CONVERGED, BAMG_ERR_TIMEOUT) = range(1, 9)
 BAMG_FP64 = 0
 BAMG_FP32 = 1
+BAMG_NORM_FROBENIUS = 0
+BAMG_NORM_INFINITY = 1
 PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
               "coo": 5, "coarse_factor": 6, "smooth_coarse": 7, "transfer": 8, "coarse_solve": 9,
               "l0_vector": 10, "cg_xr": 11, "cg_vector": 12, "refresh": 13}
@@ -73,6 +75,10 @@ _SIGS = {
     "bamg_bsr_residual_norm_noalloc": [_P, _P, _P, _P],
     "bamg_bsr_set_lanes": [_P, ctypes.c_int],
     "bamg_bsr_get_lanes": [_P, _P],
+    "bamg_bsr_block_norms": [_P, _P],
+    "bamg_bsr_norm": [_P, ctypes.c_int, _P],
+    "bamg_strength_graph": [_P, ctypes.c_double, _P, _P, ctypes.c_int64, _P],
+    "bamg_mis_aggregate": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint64, _P, _P, _P],
     "bamg_bsr_spmm": [_P, _P, _P, ctypes.c_int, ctypes.c_int],
     "bamg_ptap_symbolic": [_P, _P, _PP, _PP],
     "bamg_ptap_numeric": [_P, _P, _P, _P],
@@ -254,6 +260,32 @@ def bamg_bsr_autotune(ctx, A) -> tuple[int, float]:
 
 def bamg_bsr_set_lanes(ctx, A, lanes: int):
     _check(lib().bamg_bsr_set_lanes(A, int(lanes)), ctx)
+
+
+def bamg_bsr_block_norms(ctx, A, out):
+    """Frobenius norm of every stored block (block-CSR order) into the device tensor out."""
+    _check(lib().bamg_bsr_block_norms(A, _ptr(out)), ctx)
+
+
+def bamg_bsr_norm(ctx, A, kind: int = BAMG_NORM_FROBENIUS) -> float:
+    v = ctypes.c_double()
+    _check(lib().bamg_bsr_norm(A, int(kind), ctypes.byref(v)), ctx)
+    return v.value
+
+
+def bamg_strength_graph(ctx, A, eps: float, rowptr, col) -> int:
+    """Strong-coupling graph into device int32 tensors rowptr (nbr + 1) and col; returns the edge count."""
+    ne = ctypes.c_int64()
+    _check(lib().bamg_strength_graph(A, float(eps), _ptr(rowptr), _ptr(col), int(col.numel()), ctypes.byref(ne)), ctx)
+    return ne.value
+
+
+def bamg_mis_aggregate(ctx, n: int, rowptr, col, seed: int, agg) -> tuple[int, int]:
+    """MIS aggregates of a device CSR graph into the int32 tensor agg; returns (aggregates, rounds)."""
+    na, rounds = ctypes.c_int64(), ctypes.c_int()
+    _check(lib().bamg_mis_aggregate(ctx, int(n), _ptr(rowptr), _ptr(col), ctypes.c_uint64(seed), _ptr(agg),
+                                    ctypes.byref(na), ctypes.byref(rounds)), ctx)
+    return na.value, rounds.value
 
 
 def bamg_bsr_get_lanes(A) -> int:
