@@ -140,6 +140,14 @@ BAMG_API bamg_status bamg_bsr_coo_preallocate(bamg_bsr* A, int64_t n, const int3
  * block becomes the sum of its contributions; add = 1: the sum is added.
  * Deterministic (fixed summation order).  Increments the matrix version. */
 BAMG_API bamg_status bamg_bsr_coo_set_values(bamg_bsr* A, const double* v, int add);
+/* Element-by-element assembly of the same COO stream: every contribution is
+ * added straight into its block with an FP64 atomic (the baseline the
+ * blocked COO path of Sec. 5 replaces; kept for measurement).  Same arguments
+ * and result as bamg_bsr_coo_set_values up to the order of the additions,
+ * which atomics do not fix: sums may differ in the last bits and from run to
+ * run.  No NaN check.  The first call builds a per-entry slot map (4 bytes per
+ * COO entry, owned by the matrix). */
+BAMG_API bamg_status bamg_bsr_coo_scatter_values(bamg_bsr* A, const double* v, int add);
 
 /* Sizes and version (any pointer may be NULL). */
 BAMG_API bamg_status bamg_bsr_info(const bamg_bsr* A, int* bs_r, int* bs_c, int64_t* nbr, int64_t* nbc,

@@ -76,6 +76,7 @@ _SIGS = {
     "bamg_bsr_set_lanes": [_P, ctypes.c_int],
     "bamg_bsr_get_lanes": [_P, _P],
     "bamg_bsr_block_norms": [_P, _P],
+    "bamg_bsr_coo_scatter_values": [_P, _P, ctypes.c_int],
     "bamg_bsr_norm": [_P, ctypes.c_int, _P],
     "bamg_strength_graph": [_P, ctypes.c_double, _P, _P, ctypes.c_int64, _P],
     "bamg_mis_aggregate": [_P, ctypes.c_int64, _P, _P, ctypes.c_uint64, _P, _P, _P],
@@ -260,6 +261,11 @@ def bamg_bsr_autotune(ctx, A) -> tuple[int, float]:
 
 def bamg_bsr_set_lanes(ctx, A, lanes: int):
     _check(lib().bamg_bsr_set_lanes(A, int(lanes)), ctx)
+
+
+def bamg_bsr_coo_scatter_values(ctx, A, v, add: int = 0):
+    """Element-by-element (atomic) assembly of the COO stream v."""
+    _check(lib().bamg_bsr_coo_scatter_values(A, _ptr(v), int(add)), ctx)
 
 
 def bamg_bsr_block_norms(ctx, A, out):

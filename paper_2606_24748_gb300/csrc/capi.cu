@@ -127,6 +127,7 @@ void bsr_release(bamg_bsr* A) {
   dfree(A->vals32, st);
   dfree(A->coo_perm, st);
   dfree(A->coo_seg, st);
+  dfree(A->coo_slot, st);
   A->has_pattern = false;
   A->nnzb = 0;
   A->nslices = A->nchunks = 0;

@@ -170,11 +170,69 @@ static Status coo_set_values(bamg_bsr* A, const double* v, int add) {
   return Status{};
 }
 
+// Element-by-element assembly, the baseline blocked COO is measured against
+// (Sec. 5): every contribution is added straight into its block with an FP64
+// atomic.  The slot of each input entry comes from the COO plan.
+__global__ void k_coo_entry_slot(const int* __restrict__ seg, const int* __restrict__ perm,
+                                 const int* __restrict__ slot_of, int64_t nnzb, int* __restrict__ entry_slot) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nnzb) return;
+  const int slot = slot_of[k];
+  for (int s = seg[k]; s < seg[k + 1]; ++s) entry_slot[perm[s]] = slot;
+}
+
+template <int B>
+__global__ void k_coo_scatter(int64_t n, const int* __restrict__ entry_slot, const double* __restrict__ v,
+                              double* __restrict__ vals) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * B) return;
+  const int64_t k = t / B;
+  const int e = (int)(t - k * B);
+  const int slot = entry_slot[k];
+  if (slot >= 0) atomicAdd(vals + vidx<B>(slot, e), __ldg(v + t));
+}
+
+static Status coo_scatter_values(bamg_bsr* A, const double* v, int add) {
+  if (!A->has_pattern || !A->coo_seg) return make_status(BAMG_ERR_STATE, "coo_scatter_values before coo_preallocate");
+  if (A->coo_n > 0 && !v) return make_status(BAMG_ERR_INVALID, "null value array");
+  const int B = (int)A->block_elems();
+  if (B != 9 && B != 18 && B != 36) return make_status(BAMG_ERR_INVALID, "element-by-element assembly supports 3x3, 3x6, 6x3 and 6x6 blocks");
+  cudaStream_t st = A->ctx->stream;
+  if (!A->coo_slot && A->coo_n > 0) {
+    BAMG_TRY(dalloc(&A->coo_slot, A->coo_n, st));
+    BAMG_CUDA(cudaMemsetAsync(A->coo_slot, 0xFF, sizeof(int) * (size_t)A->coo_n, st));  // -1: ignored entries
+    if (A->nnzb > 0) {
+      k_coo_entry_slot<<<(unsigned)((A->nnzb + 255) / 256), 256, 0, st>>>(A->coo_seg, A->coo_perm, A->slot_of, A->nnzb,
+                                                                          A->coo_slot);
+      BAMG_COUNT_LAUNCH;
+    }
+  }
+  if (!add) BAMG_CUDA(cudaMemsetAsync(A->vals, 0, sizeof(double) * (size_t)(A->nslots() * B), st));
+  const int64_t nt = A->coo_n * B;
+  if (nt > 0) {
+    const unsigned blocks = (unsigned)((nt + 255) / 256);
+    if (B == 9) k_coo_scatter<9><<<blocks, 256, 0, st>>>(A->coo_n, A->coo_slot, v, A->vals);
+    else if (B == 18) k_coo_scatter<18><<<blocks, 256, 0, st>>>(A->coo_n, A->coo_slot, v, A->vals);
+    else k_coo_scatter<36><<<blocks, 256, 0, st>>>(A->coo_n, A->coo_slot, v, A->vals);
+    BAMG_COUNT_LAUNCH;
+  }
+  BAMG_CUDA(cudaGetLastError());
+  A->version++;  // the float copy, if any, is now behind and is refreshed on its next use
+  A->vals64_stale = false;
+  return Status{};
+}
+
 }  // namespace bamg
 
 using namespace bamg;
 
 extern "C" {
+
+bamg_status bamg_bsr_coo_scatter_values(bamg_bsr* A, const double* v, int add) {
+  if (!A) return BAMG_ERR_INVALID;
+  Status s = coo_scatter_values(A, v, add);
+  return s.ok() ? BAMG_OK : fail(A->ctx, s);
+}
 
 bamg_status bamg_bsr_coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const int32_t* bj) {
   if (!A) return BAMG_ERR_INVALID;

@@ -130,6 +130,7 @@ struct bamg_bsr {
   int64_t coo_n = 0;
   int* coo_perm = nullptr;   // contributions in (row, col, input order) order
   int* coo_seg = nullptr;    // nnzb + 1 offsets into coo_perm
+  int* coo_slot = nullptr;   // per input entry: its block's slot, -1 if ignored (element-by-element path)
   int64_t block_elems() const { return (int64_t)br * bc; }
   int64_t nslots() const { return nchunks * bamg::kSlice; }
 };

@@ -273,6 +273,25 @@ def test_device_memory_counts_the_library_allocations():
         B.bamg_ctx_destroy(ctx)
 
 
+@pytest.mark.parametrize("ne", [5, 12])
+def test_element_by_element_assembly_matches_oracle(ne):
+    """Atomic scatter of the COO stream gives the oracle's operator (up to the
+    order of the additions); add = 1 accumulates."""
+    _, _, Ao = problem(ne)
+    gp = GpuProblem(ne, setup=False)
+    try:
+        B.bamg_bsr_coo_scatter_values(gp.ctx, gp.A, gp.vals, 0)
+        import scipy.sparse.linalg as spla
+        ref = Ao.scalar()
+        got = read_bsr(gp.ctx, gp.A).scalar()
+        assert spla.norm(got - ref) <= TOL64 * spla.norm(ref)
+        B.bamg_bsr_coo_scatter_values(gp.ctx, gp.A, gp.vals, 1)
+        got2 = read_bsr(gp.ctx, gp.A).scalar()
+        assert spla.norm(got2 - 2 * ref) <= TOL64 * spla.norm(2 * ref)
+    finally:
+        gp.close()
+
+
 def test_hot_update_matches_oracle():
     ne = 13
     h = hierarchy(ne)
