@@ -1,0 +1,115 @@
+"""Parity at the full benchmark size (64^3 elements, 823,875 dofs, 3 levels), in
+the configuration bench.py times (autotuned lanes and splits): sampled block
+rows that the oracle computes one by one from the COO stream, and properties
+that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_24748_gb300 import bamg as B
+from workloads.elasticity import Mesh, body_force, coo_stream, element_scale
+
+from gpu_helpers import TOL64, GpuProblem, rel
+from test_pins_workload import rigid_modes
+
+pytestmark = pytest.mark.gpu
+NE = 64
+
+
+@pytest.fixture(scope="module")
+def big():
+    gp = GpuProblem(NE)
+    yield gp
+    gp.close()
+
+
+@pytest.fixture(scope="module")
+def stream():
+    mesh = Mesh(NE)
+    s = coo_stream(mesh, 0.3, element_scale(mesh))
+    bi, bj, v = s.bi.numpy(), s.bj.numpy(), s.vals.numpy().reshape(-1, 3, 3)
+    order = np.argsort(bi, kind="stable")
+    return bi, bj, v, order, np.searchsorted(bi[order], np.arange(mesh.n_nodes + 1))
+
+
+def oracle_block_row(stream, I):
+    """Block row I of the assembled operator: the sum of the stream's
+    contributions to each (I, J), J ascending."""
+    bi, bj, v, order, start = stream
+    idx = order[start[I]:start[I + 1]]
+    cols = np.unique(bj[idx])
+    return cols, np.array([v[idx[bj[idx] == J]].sum(axis=0) for J in cols])
+
+
+def test_sampled_rows_of_assembly_and_product(big, stream):
+    rng = np.random.default_rng(64)
+    n = big.mesh.n_nodes
+    x = rng.standard_normal(3 * n)
+    y = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+    B.bamg_bsr_spmv(big.ctx, big.A, torch.from_numpy(x).cuda(), y)
+    y = y.cpu().numpy()
+    rows = rng.choice(n, 300, replace=False)
+    rows[:3] = [0, n // 2, n - 1]
+    for I in rows:
+        cols, blocks = oracle_block_row(stream, I)
+        want = sum(blocks[k] @ x[3 * J:3 * J + 3] for k, J in enumerate(cols))
+        # rounding bound of a sum of products: a small multiple of eps * sum |a| |x|
+        bound = sum(np.abs(blocks[k]) @ np.abs(x[3 * J:3 * J + 3]) for k, J in enumerate(cols))
+        assert np.all(np.abs(y[3 * I:3 * I + 3] - want) <= 1e-13 * bound), I
+
+
+def test_rigid_modes_are_in_the_kernel_of_interior_rows(big):
+    x = rigid_modes(big.mesh.coords())
+    clamp = np.repeat(big.mesh.dirichlet().astype(bool), 3)
+    for k in range(6):
+        y = torch.zeros(x.shape[0], dtype=torch.float64, device="cuda")
+        B.bamg_bsr_spmv(big.ctx, big.A, torch.from_numpy(np.ascontiguousarray(x[:, k])).cuda(), y)
+        y = y.cpu().numpy()
+        ijk = big.mesh.node_ijk()
+        inner = np.repeat(((ijk > 1) & (ijk < big.mesh.m - 1)).all(axis=1), 3) & ~clamp
+        assert np.abs(y[inner]).max() <= 1e-12 * np.abs(y).max() + 1e-14
+
+
+def test_galerkin_identity_on_every_level(big):
+    """x_c^T A_c y_c = (P x_c)^T A (P y_c) and A_c symmetric, with the library's own products."""
+    rng = np.random.default_rng(3)
+    nl = B.bamg_mg_num_levels(big.mg)
+    assert nl == 3
+    for l in range(nl - 1):
+        A, P = B.bamg_mg_get_level(big.mg, l)
+        Ac, _ = B.bamg_mg_get_level(big.mg, l + 1)
+        ic, ia = B.bamg_bsr_info(Ac), B.bamg_bsr_info(A)
+        nc, nf = ic["nbr"] * ic["bs_r"], ia["nbr"] * ia["bs_r"]
+
+        def mv(M, v, m):
+            out = torch.zeros(m, dtype=torch.float64, device="cuda")
+            B.bamg_bsr_spmv(big.ctx, M, v, out)
+            return out
+
+        xc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+        yc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+        lhs = float(xc @ mv(Ac, yc, nc))
+        lhs_t = float(yc @ mv(Ac, xc, nc))
+        px, py = mv(P, xc, nf), mv(P, yc, nf)
+        rhs = float(px @ mv(A, py, nf))
+        scale = float(torch.linalg.norm(px) * torch.linalg.norm(mv(A, py, nf)))
+        assert abs(lhs - rhs) <= 1e-12 * scale, l
+        assert abs(lhs - lhs_t) <= 1e-12 * scale, l
+
+
+@pytest.mark.parametrize("precision", [B.BAMG_FP64, B.BAMG_FP32])
+def test_cg_reaches_the_tolerance_with_the_true_residual(big, precision):
+    gp = big if precision == B.BAMG_FP64 else GpuProblem(NE, precision=precision)
+    try:
+        b = torch.from_numpy(body_force(gp.mesh)).cuda()
+        x = torch.zeros_like(b)
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)
+        assert out["converged"] and out["iterations"] <= 40
+        r = torch.zeros_like(b)   # b - A x with the plain product, not CG's recurrence
+        B.bamg_bsr_spmv(gp.ctx, gp.A, x, r)
+        true_rel = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+        assert true_rel <= 1.05e-8
+        assert out["true_rnorm"] / out["bnorm"] == pytest.approx(true_rel, rel=1e-6, abs=1e-12)
+    finally:
+        if gp is not big:
+            gp.close()
