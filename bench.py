@@ -53,7 +53,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--ne", type=int, default=64, help="elements per direction")
+    p.add_argument("--ne", type=int, default=None, help="elements per direction (default 64 for Q1, 32 for Q2)")
+    p.add_argument("--element", default="q1", choices=["q1", "q2"],
+                   help="q2: 27-node hexahedra (up to 125 blocks per row; 32^3 has the dofs of Q1 64^3)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     p.add_argument("--no-compare", action="store_true", help="skip the mixed-precision comparison run")
     p.add_argument("--no-e2e", action="store_true")
@@ -172,20 +174,29 @@ def step_bytes(levels, n_coo, precond_applications, cg_its, mixed, power_its=15)
     return sum(parts.values()), parts, vc
 
 
-def level_count(ne, max_coarse_dofs=2100):
+def level_count(ne, max_coarse_dofs=2100, order=1):
     """Levels of the hierarchy: coarsen (3x3x3 node aggregates) while a level has more dofs."""
-    m, bs, n = ne + 1, 3, 1
+    m, bs, n = order * ne + 1, 3, 1
     while bs * m ** 3 > max_coarse_dofs:
         m, bs, n = max(1, m // 3), 6, n + 1
     return n
 
 
-def workload_config(ne, precision, world):
-    mesh = Mesh(ne)
-    nl = level_count(ne)
-    n_coo = 64 * ne ** 3 + (ne + 1) ** 2
-    nnzb = (3 * ne + 1) ** 3          # 27-point node adjacency: (3m - 2)^3 blocks, m = ne + 1
-    return {"workload": f"elasticity {ne}^3 Q1 elements, {mesh.n_dofs} dofs, {nl}-level SA-AMG, reuse step "
+def blocks_1d(ne, order):
+    """Node couplings along one direction: every node couples to the nodes of
+    the elements it belongs to (the block count of A is this number cubed)."""
+    if order == 1:
+        return 3 * ne + 1             # 27-point adjacency: 3m - 2, m = ne + 1
+    m = 2 * ne + 1
+    return sum(min(m - 1, i + (2 if i % 2 == 0 else 1)) - max(0, i - (2 if i % 2 == 0 else 1)) + 1 for i in range(m))
+
+
+def workload_config(ne, precision, world, order=1):
+    mesh = Mesh(ne, order)
+    nl = level_count(ne, order=order)
+    n_coo = mesh.nodes_per_element ** 2 * ne ** 3 + mesh.m ** 2
+    nnzb = blocks_1d(ne, order) ** 3
+    return {"workload": f"elasticity {ne}^3 Q{order} elements, {mesh.n_dofs} dofs, {nl}-level SA-AMG, reuse step "
                         f"(COO re-assembly, PtAP all levels, smoother refresh, PCG V(2,2) Chebyshev to rtol 1e-8), "
                         f"{'mixed FP32/FP64' if precision == 'mixed' else 'FP64'}",
             "elements": ne, "dofs": mesh.n_dofs, "levels": nl, "precision": precision,
@@ -220,9 +231,9 @@ def apply_tune_cache(B, ctx, mg, path):
 
 
 class Workload:
-    def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000, autotune=1, tune_cache=""):
+    def __init__(self, B, torch, ne, nu, precision, n_inputs, seed0=1000, autotune=1, tune_cache="", order=1):
         self.B, self.torch = B, torch
-        self.mesh = Mesh(ne)
+        self.mesh = Mesh(ne, order)
         m = self.mesh
         self.ctx = B.bamg_ctx_create(torch.cuda.current_stream())
         self.bi, self.bj = coo_indices(m, "cuda")
@@ -291,8 +302,8 @@ def run_ours(args):
         tdist.init_process_group("nccl")
         dist = tdist
     K, W = args.steps, args.warmup
-    stream_bytes = 72 * 64 * args.ne ** 3
-    wl = Workload(B, torch, args.ne, 0.3, args.precision,
+    stream_bytes = 72 * Mesh(args.ne, args.order).nodes_per_element ** 2 * args.ne ** 3
+    wl = Workload(B, torch, args.ne, 0.3, args.precision, order=args.order,
                   n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))), autotune=args.autotune,
                   tune_cache=args.tune_cache)
     for k in range(W):
@@ -331,8 +342,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if wl.mixed else "f64",
-        "data": "synthetic: seeded Q1 elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
-        "config": workload_config(args.ne, args.precision, world),
+        "data": f"synthetic: seeded Q{args.order} elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
+        "config": workload_config(args.ne, args.precision, world, args.order),
         "cg_iterations": its, "bytes_per_step": int(bytes_step),
         "bytes_parts": {k: int(v) for k, v in parts.items()},
         "gpu_launches": int(launches),
@@ -369,7 +380,7 @@ def run_ours(args):
         wl = None
         result["mixed"] = compare_mixed(args, torch, B, x64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline()
+        result["cpu_baseline"] = cpu_baseline(ne=24 // args.order, order=args.order)
     if wl is not None:
         wl.close()
     if dist:
@@ -738,8 +749,9 @@ def compare_mixed(args, torch, B, x64=None):
     """Time to rtol 1e-8 of the mixed-precision form on the same workload, and
     its solution against the FP64 form's for the same input."""
     K = max(3, min(args.steps, 10))
-    stream_bytes = 72 * 64 * args.ne ** 3
-    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))))
+    stream_bytes = 72 * Mesh(args.ne, args.order).nodes_per_element ** 2 * args.ne ** 3
+    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))),
+                  order=args.order)
     for k in range(2):
         wl.step(k)
     ms, outs = timed(torch, None, lambda k: wl.step(k), K)
@@ -775,11 +787,11 @@ class OracleSample:
     setup once (untimed), then per step COO assembly of a perturbed operator,
     the Galerkin products on every level, the smoother refresh and PCG."""
 
-    def __init__(self, ne):
+    def __init__(self, ne, order=1):
         from oracle import multigrid as omg
         from oracle.assembly import coo_assemble_blocks
         self.omg, self.coo = omg, coo_assemble_blocks
-        self.m = m = Mesh(ne)
+        self.m = m = Mesh(ne, order)
         bi, bj = coo_indices(m)
         self.bi, self.bj = bi.numpy(), bj.numpy()
         v0 = coo_values(m, 0.3, element_scale(m)).numpy()
@@ -801,8 +813,8 @@ class OracleSample:
         return dt, nbytes, its
 
 
-def cpu_baseline(steps=8, ne=24):
-    s = OracleSample(ne)
+def cpu_baseline(steps=8, ne=24, order=1):
+    s = OracleSample(ne, order)
     tot_t, tot_b = 0.0, 0.0
     for k in range(steps):
         dt, nb, _ = s.step(seed=k + 1)
@@ -810,8 +822,8 @@ def cpu_baseline(steps=8, ne=24):
         tot_b += nb
     return {"value": round(tot_b / tot_t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle reuse steps (COO assembly, Galerkin products, smoother refresh, "
-                      f"PCG to 1e-8) of the same elasticity problem at {ne}^3 elements "
-                      f"({3 * (ne + 1) ** 3} dofs), single-threaded scipy/numpy on the host",
+                      f"PCG to 1e-8) of the same elasticity problem at {ne}^3 Q{order} elements "
+                      f"({3 * (order * ne + 1) ** 3} dofs), single-threaded scipy/numpy on the host",
             "seconds": round(tot_t, 2)}
 
 
@@ -822,8 +834,8 @@ def run_reference(args):
     if rank != 0:
         return None
     K, W = args.steps, args.warmup
-    ne = 24
-    sample = OracleSample(ne)
+    ne = 24 // args.order   # the same dofs for Q1 and Q2
+    sample = OracleSample(ne, args.order)
     for k in range(W):
         sample.step(seed=100 + k)
     tt, tb = 0.0, 0.0
@@ -833,12 +845,13 @@ def run_reference(args):
         tb += nb
     value = tb / tt / 1e9
     desc = (f"oracle reuse step (COO assembly, Galerkin products, smoother refresh, PCG to 1e-8) per step "
-            f"on a {ne}^3-element sample ({3 * (ne + 1) ** 3} dofs) of the same problem, single-threaded")
+            f"on a {ne}^3-element Q{args.order} sample ({3 * (args.order * ne + 1) ** 3} dofs) of the same problem, "
+            f"single-threaded")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": round(tt / K * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic: seeded Q1 elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
-            "config": workload_config(args.ne, args.precision, args.gpus),
+            "data": f"synthetic: seeded Q{args.order} elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
+            "config": workload_config(args.ne, args.precision, args.gpus, args.order),
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "kind": "oracle", "cores": 1, "sample": desc},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -860,6 +873,9 @@ def run_only(args):
 
 def main():
     args = parse()
+    args.order = 2 if args.element == "q2" else 1
+    if args.ne is None:
+        args.ne = 64 // args.order
     if args.only and args.impl == "ours":
         print(json.dumps(run_only(args)), flush=True)
         return

@@ -9,8 +9,8 @@ from workloads.elasticity import Mesh, coo_stream, element_scale
 
 
 @functools.lru_cache(maxsize=None)
-def problem(ne: int, nu: float = 0.3, seed: int | None = None):
-    mesh = Mesh(ne)
+def problem(ne: int, nu: float = 0.3, seed: int | None = None, order: int = 1):
+    mesh = Mesh(ne, order)
     delta = None
     if seed is not None:
         from workloads.elasticity import perturbation
@@ -22,8 +22,8 @@ def problem(ne: int, nu: float = 0.3, seed: int | None = None):
 
 
 @functools.lru_cache(maxsize=None)
-def hierarchy(ne: int, nu: float = 0.3, max_coarse_dofs: int = omg.MAX_COARSE_DOFS):
-    mesh, _, A = problem(ne, nu)
+def hierarchy(ne: int, nu: float = 0.3, max_coarse_dofs: int = omg.MAX_COARSE_DOFS, order: int = 1):
+    mesh, _, A = problem(ne, nu, order=order)
     return omg.setup(A, mesh.coords(), mesh.dirichlet(), mesh.grid, max_coarse_dofs)
 
 

@@ -1,4 +1,5 @@
-"""3D linear elasticity on the unit cube with trilinear (Q1) hexahedra.
+"""3D linear elasticity on the unit cube with trilinear (Q1) or triquadratic
+(Q2) hexahedra.
 
 Problem inputs for the blocked smoothed-aggregation AMG reuse phase: the
 mesh, the 24x24 element stiffness, the blocked COO value stream (one 3x3 block
@@ -9,9 +10,12 @@ generator for the workloads the paper measures: Q1 hexahedral 3D elasticity,
 block size 3 (Sec. 4.1), assembled through blocked COO (Sec. 3.4, Sec. 5).
 
 Conventions (all fixed here and used by every consumer):
-  * ``ne`` elements per direction, ``m = ne + 1`` nodes per direction,
-    ``h = 1 / ne``; node ``n = ix + m*iy + m*m*iz`` at ``(ix, iy, iz) * h``.
-  * element ``e = ex + ne*ey + ne*ne*ez``; local node ``a = bx + 2*by + 4*bz``.
+  * ``ne`` elements per direction of side ``h = 1 / ne``, element order
+    ``p`` (1: Q1, 8 nodes; 2: Q2, 27 nodes), ``m = p*ne + 1`` nodes per
+    direction at spacing ``h / p``; node ``n = ix + m*iy + m*m*iz`` at
+    ``(ix, iy, iz) * h / p``.
+  * element ``e = ex + ne*ey + ne*ne*ez``; local node
+    ``a = bx + (p+1)*by + (p+1)^2*bz`` with ``bx, by, bz`` in ``0..p``.
   * dof ``3*n + c`` for displacement component ``c``.
   * Dirichlet: every node with ``ix == 0`` is clamped in all 3 components.
     Element blocks touching a clamped node are zero, and one extra identity
@@ -20,7 +24,8 @@ Conventions (all fixed here and used by every consumer):
     every structural block stays in the pattern.
   * Element stiffness ``K_e = (E_e * h) * K_ref(nu)`` where ``K_ref`` is the
     stiffness of the unit cube with E = 1 (stiffness scales with E and, in
-    3D, linearly with the element size h).
+    3D, linearly with the element size h).  Q1 uses 2x2x2 Gauss points and
+    Q2 3x3x3, exact for both stiffnesses on a cube.
 """
 from __future__ import annotations
 
@@ -33,14 +38,20 @@ import torch
 @dataclasses.dataclass(frozen=True)
 class Mesh:
     ne: int
+    order: int = 1
 
     @property
     def m(self) -> int:
-        return self.ne + 1
+        return self.order * self.ne + 1
 
     @property
     def h(self) -> float:
+        """Element side."""
         return 1.0 / self.ne
+
+    @property
+    def nodes_per_element(self) -> int:
+        return (self.order + 1) ** 3
 
     @property
     def n_nodes(self) -> int:
@@ -64,7 +75,7 @@ class Mesh:
         return np.stack([n % m, (n // m) % m, n // (m * m)], axis=1)
 
     def coords(self) -> np.ndarray:
-        return self.node_ijk().astype(np.float64) * self.h
+        return self.node_ijk().astype(np.float64) * (self.h / self.order)
 
     def dirichlet(self) -> np.ndarray:
         return (self.node_ijk()[:, 0] == 0).astype(np.uint8)
@@ -73,9 +84,10 @@ class Mesh:
         ne, m = self.ne, self.m
         e = np.arange(self.n_el, dtype=np.int64)
         ex, ey, ez = e % ne, (e // ne) % ne, e // (ne * ne)
-        base = ex + m * ey + m * m * ez
-        a = np.arange(8)
-        off = (a & 1) + m * ((a >> 1) & 1) + m * m * ((a >> 2) & 1)
+        p = self.order
+        base = p * (ex + m * ey + m * m * ez)
+        a = np.arange((p + 1) ** 3)
+        off = (a % (p + 1)) + m * ((a // (p + 1)) % (p + 1)) + m * m * (a // (p + 1) ** 2)
         return base[:, None] + off[None, :]
 
     def element_centroids(self) -> np.ndarray:
@@ -100,6 +112,52 @@ def lame(E: float, nu: float) -> tuple[float, float]:
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return lam, mu
+
+
+def lagrange_1d(degree: int, t: float) -> tuple[np.ndarray, np.ndarray]:
+    """Values and derivatives of the 1-D Lagrange basis on [0, 1] with
+    equispaced nodes (degree 1: 0, 1; degree 2: 0, 1/2, 1)."""
+    if degree == 1:
+        return np.array([1.0 - t, t]), np.array([-1.0, 1.0])
+    if degree == 2:
+        return (np.array([(1.0 - t) * (1.0 - 2.0 * t), 4.0 * t * (1.0 - t), t * (2.0 * t - 1.0)]),
+                np.array([4.0 * t - 3.0, 4.0 - 8.0 * t, 4.0 * t - 1.0]))
+    raise ValueError("degree must be 1 or 2")
+
+
+def element_stiffness_q(E: float, nu: float, h: float, degree: int, order: int) -> np.ndarray:
+    """Isotropic Q1 / Q2 stiffness of a cube of side h with ``order`` Gauss
+    points per direction; dofs ordered 3*a + c, a = bx + (p+1) by + (p+1)^2 bz."""
+    lam, mu = lame(E, nu)
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[[0, 1, 2], [0, 1, 2]] += 2.0 * mu
+    D[[3, 4, 5], [3, 4, 5]] = mu
+    pts, wts = gauss_rule(order)
+    q = degree + 1
+    nn = q ** 3
+    idx = np.array([[a % q, (a // q) % q, a // (q * q)] for a in range(nn)])
+    K = np.zeros((3 * nn, 3 * nn))
+    for i, xi in enumerate(pts):
+        for j, eta in enumerate(pts):
+            for k, zeta in enumerate(pts):
+                (fx, dx), (fy, dy), (fz, dz) = (lagrange_1d(degree, t) for t in (xi, eta, zeta))
+                grad = np.stack([dx[idx[:, 0]] * fy[idx[:, 1]] * fz[idx[:, 2]],
+                                 fx[idx[:, 0]] * dy[idx[:, 1]] * fz[idx[:, 2]],
+                                 fx[idx[:, 0]] * fy[idx[:, 1]] * dz[idx[:, 2]]], axis=1) / h
+                B = np.zeros((6, 3 * nn))
+                for a in range(nn):
+                    gx, gy, gz = grad[a]
+                    c = 3 * a
+                    B[0, c] = gx
+                    B[1, c + 1] = gy
+                    B[2, c + 2] = gz
+                    B[3, c], B[3, c + 1] = gy, gx
+                    B[4, c + 1], B[4, c + 2] = gz, gy
+                    B[5, c], B[5, c + 2] = gz, gx
+                w = wts[i] * wts[j] * wts[k] * h ** 3
+                K += w * (B.T @ D @ B)
+    return K
 
 
 def element_stiffness(E: float, nu: float, h: float = 1.0, order: int = 2) -> np.ndarray:
@@ -136,10 +194,15 @@ def element_stiffness(E: float, nu: float, h: float = 1.0, order: int = 2) -> np
     return K
 
 
-def reference_blocks(nu: float) -> np.ndarray:
-    """K_ref(nu) cut into its 64 3x3 blocks, ordered (a, b) -> 8*a + b."""
-    K = element_stiffness(1.0, nu, 1.0, 2)
-    return K.reshape(8, 3, 8, 3).transpose(0, 2, 1, 3).reshape(64, 3, 3).copy()
+def reference_blocks(nu: float, degree: int = 1) -> np.ndarray:
+    """K_ref(nu) cut into its nn^2 3x3 blocks (nn = 8 or 27 nodes), ordered
+    (a, b) -> nn*a + b."""
+    if degree == 1:
+        K = element_stiffness(1.0, nu, 1.0, 2)
+    else:
+        K = element_stiffness_q(1.0, nu, 1.0, degree, degree + 1)
+    nn = (degree + 1) ** 3
+    return K.reshape(nn, 3, nn, 3).transpose(0, 2, 1, 3).reshape(nn * nn, 3, 3).copy()
 
 
 def element_scale(mesh: Mesh, E_el: np.ndarray | None = None,
@@ -166,9 +229,9 @@ class CooStream:
 
 def coo_indices(mesh: Mesh, device="cpu") -> tuple[torch.Tensor, torch.Tensor]:
     conn = torch.as_tensor(mesh.connectivity(), device=device)
-    n_el = conn.shape[0]
-    bi = conn[:, :, None].expand(n_el, 8, 8).reshape(-1)
-    bj = conn[:, None, :].expand(n_el, 8, 8).reshape(-1)
+    n_el, nn = conn.shape
+    bi = conn[:, :, None].expand(n_el, nn, nn).reshape(-1)
+    bj = conn[:, None, :].expand(n_el, nn, nn).reshape(-1)
     dn = torch.as_tensor(np.nonzero(mesh.dirichlet())[0], device=device)
     bi = torch.cat([bi, dn]).to(torch.int32)
     bj = torch.cat([bj, dn]).to(torch.int32)
@@ -183,21 +246,22 @@ def coo_values(mesh: Mesh, nu: float, scale: np.ndarray, device="cpu",
     host and device); blocks touching a clamped node are exact zeros; the
     trailing clamped-node blocks are identities.
     """
-    kb = torch.as_tensor(reference_blocks(nu), device=device)
+    kb = torch.as_tensor(reference_blocks(nu, mesh.order), device=device)
     s = torch.as_tensor(np.asarray(scale, dtype=np.float64), device=device)
     conn = torch.as_tensor(mesh.connectivity(), device=device)
     dirn = torch.as_tensor(mesh.dirichlet().astype(bool), device=device)
-    n_el = conn.shape[0]
+    n_el, nn = conn.shape
+    nb = nn * nn
     n_dir = int(mesh.dirichlet().sum())
-    n_coo = 64 * n_el + n_dir
+    n_coo = nb * n_el + n_dir
     if out is None:
         out = torch.empty((n_coo, 3, 3), dtype=torch.float64, device=device)
-    el = out[: 64 * n_el].view(n_el, 64, 3, 3)
+    el = out[: nb * n_el].view(n_el, nb, 3, 3)
     torch.mul(s[:, None, None, None], kb[None], out=el)
-    dn = dirn[conn]                                             # (n_el, 8)
-    touch = (dn[:, :, None] | dn[:, None, :]).reshape(n_el, 64)  # (n_el, 64)
+    dn = dirn[conn]                                             # (n_el, nn)
+    touch = (dn[:, :, None] | dn[:, None, :]).reshape(n_el, nb)  # (n_el, nn^2)
     el.masked_fill_(touch[:, :, None, None], 0.0)
-    out[64 * n_el:] = torch.eye(3, dtype=torch.float64, device=device)
+    out[nb * n_el:] = torch.eye(3, dtype=torch.float64, device=device)
     return out
 
 
@@ -209,11 +273,18 @@ def coo_stream(mesh: Mesh, nu: float, scale: np.ndarray, device="cpu") -> CooStr
 def body_force(mesh: Mesh) -> np.ndarray:
     """Consistent load of the unit body force f = (0, 0, -1); zero on clamped dofs.
 
-    For Q1 each element node receives -h^3/8 in z (the integral of its shape
-    function over the element).
+    Each element node receives minus the integral of its shape function over
+    the element in z: h^3/8 for Q1; for Q2 the product of the 1-D quadratic
+    weights (1/6, 2/3, 1/6) times h^3.
     """
     f = np.zeros(mesh.n_nodes)
-    np.add.at(f, mesh.connectivity().reshape(-1), -(mesh.h ** 3) / 8.0)
+    if mesh.order == 1:
+        w = np.full(8, 1.0 / 8.0)
+    else:
+        w1 = np.array([1.0, 4.0, 1.0]) / 6.0
+        w = np.array([w1[a % 3] * w1[(a // 3) % 3] * w1[a // 9] for a in range(27)])
+    conn = mesh.connectivity()
+    np.add.at(f, conn.reshape(-1), np.tile(-(mesh.h ** 3) * w, conn.shape[0]))
     b = np.zeros((mesh.n_nodes, 3))
     b[:, 2] = f
     b[mesh.dirichlet().astype(bool)] = 0.0
@@ -244,7 +315,7 @@ def inclusion_moduli(mesh: Mesh, seed: int) -> np.ndarray:
     radii = rng.uniform(0.05, 0.15, k)
     moduli = 10.0 ** rng.uniform(-2.0, 2.0, k)
     E = np.ones(mesh.n_el)
-    xc = mesh.element_centroids()
+    xc = mesh.element_centroids()  # element geometry: the same for Q1 and Q2
     for c, r, Ek in zip(centres, radii, moduli):
         inside = np.sum((xc - c) ** 2, axis=1) <= r * r
         E[inside] = Ek
