@@ -1,5 +1,5 @@
 """Q2 elements (27-node hexahedra, up to 125 blocks per row): the whole
-reuse path against the oracle (the paper's nonzeros-per-row study, Sec. 4.7)."""
+reuse path against the oracle (the paper's nonzeros-per-row study, Sec. 4.6)."""
 import numpy as np
 import pytest
 import torch
