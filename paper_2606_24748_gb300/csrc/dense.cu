@@ -607,7 +607,6 @@ __global__ void k_band_out(int64_t m, const double* __restrict__ x, TO* __restri
   if (t < m) out[t] = (TO)x[t];
 }
 
-static unsigned warps_grid(int64_t rows) { return (unsigned)std::max<int64_t>(1, (rows * 32 + 255) / 256); }
 static unsigned chain_grid(int64_t rows) { return (unsigned)std::max<int64_t>(1, (rows + kChainRows - 1) / kChainRows); }
 
 // Half-bandwidth of the coarsest operator in dofs.

@@ -134,7 +134,7 @@ __global__ void k_smooth_prolongator(int64_t nz, const int* __restrict__ zrow, c
   if (t >= nz * B) return;
   const int64_t z = t / B;
   const int e = (int)(t - z * B);
-  const int r = e / 6, c = e - r * 6;
+  const int r = e / 6;  // row of the 6-column block
   const int i = zrow[z];
   const double d = Avals[vidx<BS * BS>(diag_slot[i], r * BS + r)];
   double v = -omega / d * Z[z * B + e];
