@@ -270,6 +270,21 @@ class Workload:
         B.bamg_ctx_destroy(self.ctx)
 
 
+def slowest_rank_ms(torch, dist, ms_step, device="cuda"):
+    """Per-step time of the slowest rank: every rank runs a replica, and the
+    job ends with the last one (the maximum over ranks)."""
+    if not dist:
+        return ms_step
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, bytes_step, ms_step):
+    """Whole-job GB/s: the algorithmic bytes of all replicas over the slowest rank's step time."""
+    return world * bytes_step / (ms_step / 1e3) / 1e9
+
+
 def timed(torch, dist, fn, K):
     st = torch.cuda.current_stream()
     if dist:
@@ -327,14 +342,10 @@ def run_ours(args):
     table = {name: B.bamg_ctx_profile_read(wl.ctx, slot) for name, slot in B.PROF_SLOTS.items()}
     B.bamg_ctx_profile(wl.ctx, 0)
     its = [o["iterations"] for o in outs]
-    ms_step = ms / K
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = slowest_rank_ms(torch, dist, ms / K)
     per_step = [step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]
     bytes_step = float(np.mean(per_step))
-    value = world * bytes_step / (ms_step / 1e3) / 1e9
+    value = replica_value(world, bytes_step, ms_step)
     _, parts, vc_bytes = step_bytes(wl.levels, wl.n_coo, its[-1] + 1, its[-1], wl.mixed)
 
     roof = roofline(wl, prof, B)
@@ -595,14 +606,10 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
         run(k, True)
     state["n"] = 0
     ms, outs = timed(torch, dist, step, K)
-    ms_step = ms / K
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = slowest_rank_ms(torch, dist, ms / K)
     its = [o["iterations"] for o in outs]
     bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]))
-    return {"value": round(world * bytes_step / (ms_step / 1e3) / 1e9, 2), "unit": "GB/s",
+    return {"value": round(replica_value(world, bytes_step, ms_step), 2), "unit": "GB/s",
             "ms_per_step": round(ms_step, 4),
             "h2d_bytes_per_step": int(host_in[0].numel() * 8 + host_b.numel() * 8),
             "overlap": "next step's value stream copied on a second stream during the current step",
@@ -871,11 +878,25 @@ def run_only(args):
     return out
 
 
-def main():
-    args = parse()
+def finish_args(args):
     args.order = 2 if args.element == "q2" else 1
     if args.ne is None:
         args.ne = 64 // args.order
+    return args
+
+
+def parse_args_for_test(argv):
+    """The parsed command line for ``argv`` (tests call the arms directly)."""
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py", *argv]
+        return finish_args(parse())
+    finally:
+        sys.argv = saved
+
+
+def main():
+    args = finish_args(parse())
     if args.only and args.impl == "ours":
         print(json.dumps(run_only(args)), flush=True)
         return
