@@ -47,3 +47,10 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = bench.parse_args_for_test(["--impl", "reference", "--steps", "1", "--warmup", "0"])
     assert bench.run_reference(args) is None
+
+
+def test_all_core_oracle_baseline_runs_spawned_replicas():
+    """The all-core CPU baseline: single-threaded oracle processes from a spawn
+    pool, timed from their common start."""
+    r = bench.cpu_baseline_all_cores(4, 1, steps=1, max_procs=2)
+    assert r["cores"] <= 2 and r["value"] > 0 and r["seconds"] > 0
