@@ -840,13 +840,21 @@ def cpu_baseline(steps=8, ne=24, order=1):
 
 
 def _oracle_replica(ne, order, steps, seed0, barrier, queue):
-    """One single-threaded oracle process of the all-core baseline."""
-    s = OracleSample(ne, order)
-    barrier.wait(timeout=600)
-    t0, nb = time.time(), 0.0
-    for k in range(steps):
-        nb += s.step(seed=seed0 + k)[1]
-    queue.put((t0, time.time(), nb))
+    """One single-threaded oracle process of the all-core baseline.  A failure
+    breaks the barrier, so that no sibling waits for it, and is reported."""
+    try:
+        s = OracleSample(ne, order)
+        barrier.wait(timeout=300)
+        t0, nb = time.time(), 0.0
+        for k in range(steps):
+            nb += s.step(seed=seed0 + k)[1]
+        queue.put((t0, time.time(), nb))
+    except Exception as e:
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        queue.put(("error", f"{type(e).__name__}: {e}", 0.0))
 
 
 def cpu_baseline_all_cores(ne, order, steps=2, max_procs=64):
@@ -865,15 +873,22 @@ def cpu_baseline_all_cores(ne, order, steps=2, max_procs=64):
               for i in range(procs)]
         for p in ps:
             p.start()
-        res = [queue.get(timeout=900) for _ in ps]
-        for p in ps:
-            p.join(timeout=60)
+        try:
+            res = [queue.get(timeout=600) for _ in ps]
+        finally:
+            for p in ps:
+                p.join(timeout=30)
+                if p.is_alive():
+                    p.terminate()
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
+    errors = [r[1] for r in res if r[0] == "error"]
+    if errors:
+        raise RuntimeError(errors[0])
     t0, t1 = min(r[0] for r in res), max(r[1] for r in res)
     return {"value": round(sum(r[2] for r in res) / (t1 - t0) / 1e9, 4), "unit": "GB/s", "cores": procs,
             "sample": f"{procs} single-threaded oracle processes, {steps} reuse steps each, same problem",
