@@ -121,3 +121,60 @@ def test_weighted_vcycle_symmetric_and_targets_in_range():
     T = OL.smoother_targets(h, rng.standard_normal((2, h.levels[0].A.nbr * 3)))
     assert len(T) == h.n_levels - 1
     assert np.all((T[0] >= 0.5) & (T[0] <= 2.0))
+
+
+def dense_presmoothing_residual(L, degree, rhs, weights=None):
+    """Residual after degree-m Chebyshev pre-smoothing from x = 0, from the
+    generalised eigenpairs A V = M V Lam (V^T M V = I, M = D W^{-1}): the
+    residual operator is M V p(Lam) V^T, p the Chebyshev error polynomial."""
+    import scipy.linalg as sla
+    from test_pins_smoother import cheb_error_poly
+    Db = diagonal_blocks(L.A)
+    if weights is not None:
+        Db = Db / np.asarray(weights, dtype=np.float64)[:, None, None]
+    M = sla.block_diag(*Db)
+    lam, V = sla.eigh(L.A.dense(), M)
+    return M @ (V @ (cheb_error_poly(L.lam, degree)(lam) * (V.T @ rhs)))
+
+
+def expected_targets(h, B, restrict_residual=True):
+    res = [[] for _ in range(h.n_levels - 1)]
+    for b in B:
+        rhs = b
+        for l in range(h.n_levels - 1):
+            L = h.levels[l]
+            r = dense_presmoothing_residual(L, h.degree, rhs, L.weights)
+            res[l].append(r)
+            rhs = L.P.dense().T @ (r if restrict_residual else rhs)
+    return [OL.local_damping(h.levels[l].As, h.levels[l].Dinv, res[l]) for l in range(h.n_levels - 1)]
+
+
+def test_smoother_targets_follow_the_level_composition():
+    """Level l's targets come from the residual after its pre-smoothing, with
+    the restricted pre-smoothed residual of level l-1 as right-hand side; on
+    a three-level hierarchy both levels are checked against the dense
+    spectral form of the pre-smoothing residual."""
+    h = hierarchy(8, max_coarse_dofs=100)
+    assert h.n_levels == 3
+    B = np.random.default_rng(21).standard_normal((3, h.levels[0].A.nbr * 3))
+    got = OL.smoother_targets(h, B)
+    ref = expected_targets(h, B)
+    assert len(got) == 2
+    for g, r in zip(got, ref):
+        assert np.allclose(g, r, rtol=1e-5, atol=1e-6)
+        assert np.ptp(r) > 0.05            # the targets are not all the same value
+    # planted mistake: restricting the level's input instead of its residual
+    wrong = expected_targets(h, B, restrict_residual=False)
+    assert not np.allclose(wrong[1], got[1], rtol=1e-3, atol=1e-3)
+
+
+def test_smoother_targets_with_weights_use_the_weighted_smoother():
+    import copy
+    h = copy.deepcopy(hierarchy(8, max_coarse_dofs=100))
+    rng = np.random.default_rng(22)
+    omg.set_weights(h, [rng.uniform(0.6, 1.6, h.levels[0].A.nbr), None])
+    B = rng.standard_normal((2, h.levels[0].A.nbr * 3))
+    got = OL.smoother_targets(h, B)
+    ref = expected_targets(h, B)
+    for g, r in zip(got, ref):
+        assert np.allclose(g, r, rtol=1e-5, atol=1e-6)

@@ -90,3 +90,54 @@ def test_cg_with_vcycle_reaches_tolerance():
     x_star = np.linalg.solve(As.toarray(), b)
     assert np.linalg.norm(x - x_star) <= 1e-5 * np.linalg.norm(x_star)
     assert its < 30
+
+
+def dense_two_level_error(h):
+    """E = S (I - P A_c^{-1} P^T A) S of a two-level hierarchy, from dense
+    matrices and the Chebyshev error polynomial (no call into the V-cycle)."""
+    L0, L1 = h.levels
+    Ad, Pd = L0.A.dense(), L0.P.dense()
+    S = smoother_error(L0, h.degree)
+    CGC = np.eye(Ad.shape[0]) - Pd @ np.linalg.solve(L1.A.dense(), Pd.T @ Ad)
+    return Ad, S @ CGC @ S
+
+
+def stationary_reference(Ad, E, b, its):
+    """||r_k|| of x_{k+1} = x_k + M r_k with M = (I - E) A^{-1}: the residual
+    obeys r_{k+1} = (I - A M) r_k = A E A^{-1} r_k."""
+    T = Ad @ E @ np.linalg.inv(Ad)
+    r = b.copy()
+    out = [float(np.linalg.norm(r))]
+    for _ in range(its):
+        r = T @ r
+        out.append(float(np.linalg.norm(r)))
+    return np.array(out)
+
+
+def test_stationary_iteration_equals_dense_error_operator_powers():
+    h = hierarchy(8)
+    Ad, E = dense_two_level_error(h)
+    b = np.random.default_rng(11).standard_normal(Ad.shape[0])
+    its = 6
+    ref = stationary_reference(Ad, E, b, its)
+    got = np.array(omg.stationary(h, b, its))
+    assert got.shape == ref.shape
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * ref[0])
+    # the factor the learned smoother is judged by follows from the same powers
+    assert (got[-1] / got[0]) ** (1 / its) < 1.0
+
+
+def test_stationary_pin_rejects_a_planted_mistake():
+    """A stationary loop that applies the cycle to b instead of the current
+    residual differs from the error-operator powers (the pin can tell)."""
+    h = hierarchy(8)
+    Ad, E = dense_two_level_error(h)
+    b = np.random.default_rng(12).standard_normal(Ad.shape[0])
+    As = h.levels[0].As
+    x = np.zeros_like(b)
+    wrong = [float(np.linalg.norm(b))]
+    for _ in range(4):
+        x = x + omg.vcycle(h, b)           # planted: b in place of r
+        wrong.append(float(np.linalg.norm(b - As @ x)))
+    ref = stationary_reference(Ad, E, b, 4)
+    assert not np.allclose(wrong, ref, rtol=1e-3)
