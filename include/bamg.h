@@ -75,6 +75,15 @@ BAMG_API const char* bamg_last_error(const bamg_ctx* ctx);
 /* Wait for the context's stream, then turn the device error word into a
  * status (and clear it). */
 BAMG_API bamg_status bamg_ctx_sync(bamg_ctx* ctx);
+/* Bounded device waits (a CTA polling a counter that other CTAs of the same
+ * launch advance, e.g. inside the coarsest-level factorisation) give up
+ * after `polls` polls, record BAMG_ERR_TIMEOUT in the device error word and
+ * go on, so that no kernel waits forever; the status reaches the host at
+ * the next call that reads the error word (bamg_ctx_sync, bamg_cg_solve).
+ * Default 2^22 polls (about 0.4 s).  0 gives up at the first wait without
+ * polling, which exercises the timeout path deterministically (the results
+ * of that call are then not valid).  BAMG_ERR_INVALID for polls < 0. */
+BAMG_API bamg_status bamg_ctx_set_wait_limit(bamg_ctx* ctx, int64_t polls);
 
 /* Kernel timing for benchmarks.  While enabled, the library brackets the
  * launches of the kernels listed in bamg_prof_slot with CUDA events on the
@@ -109,6 +118,16 @@ BAMG_API bamg_status bamg_ctx_profile_read(bamg_ctx* ctx, int slot, double* tota
 /* Number of kernels this library has launched in this process (kernels run
  * through CUDA graphs included, counted per graph launch). */
 BAMG_API uint64_t bamg_kernel_launches(void);
+/* Measured FMA throughput of the FP64 (precision = BAMG_FP64) or FP32
+ * (BAMG_FP32) pipe on the context's device, in TFLOP/s (2 flop per FMA),
+ * written to *tflops (host).  A benchmark aid, not a step of the method: it
+ * gives the rooflines of the ALU-bound kernels a measured denominator
+ * (Sec. 4.2 ties SpMV to memory traffic; on this part the FP64 FMA pipe
+ * binds first).  Independent FMA chains on every SM at full occupancy, one
+ * timed launch of about 0.1 s after a warm-up.  Allocates a few KB on the
+ * context's stream and waits for it.  BAMG_ERR_INVALID for another
+ * precision or a null pointer. */
+BAMG_API bamg_status bamg_probe_fma_rate(bamg_ctx* ctx, int precision, double* tflops);
 /* Device memory of the library on the context's device: every library
  * allocation is stream-ordered from the device's default memory pool, so the
  * pool's bytes in use and their high-water mark (since the last reset) are the
@@ -228,10 +247,12 @@ BAMG_API bamg_status bamg_mis_aggregate(bamg_ctx* ctx, int64_t n, const int* row
 /* Residual norm ||b - A x||_2 for a square operator with 3x3 or 6x6 blocks,
  * written to *norm (device double) on A's context stream; x, b are device
  * FP64 vectors.  This entry point allocates no device memory at all, for
- * callers that cannot call cudaMalloc: code running inside a CUDA host
- * callback (where CUDA calls that allocate are not allowed), or components
- * of a larger application whose device memory is all pre-reserved by its own
- * pool.  The paper has no counterpart; it is an operational addition.
+ * callers that cannot call cudaMalloc: components of a larger application
+ * whose device memory is all pre-reserved by that application's own pool, so
+ * that a further cudaMalloc would fail or break the pool's accounting.  (It
+ * still launches a kernel and issues a memset, so it is no use from a CUDA
+ * host callback, where no CUDA call is allowed.)  The paper has no
+ * counterpart; it is an operational addition.
  *  - Scratch: the reduction's partial sums live in a file-scope device array
  *    of 4096 doubles (32 KB) plus one counter, which every GPU that loads the
  *    library holds until the process exits.  One partial per 128 thread
@@ -256,6 +277,10 @@ BAMG_API bamg_status bamg_bsr_residual_norm_noalloc(const bamg_bsr* A, const dou
  * a plan holding the intermediate pattern and the gather lists that the
  * numeric phase reuses.  Ac is owned by the caller (bamg_bsr_destroy). */
 BAMG_API bamg_status bamg_ptap_symbolic(bamg_bsr* A, bamg_bsr* P, bamg_ptap** plan, bamg_bsr** Ac);
+/* State gate of a plan (Sec. 3.5): how many times the numeric phase rebuilt
+ * its block-ordered copy of P, which it does only when P's version differs
+ * from the one cached (host output). */
+BAMG_API bamg_status bamg_ptap_get_refreshes(const bamg_ptap* plan, uint64_t* p_refreshes);
 /* Numeric Galerkin recompute with the reused pattern (Sec. 3.1 "hot PtAP",
  * Sec. 3.5): Ac = P^T A P in FP64.  The plan caches a gather-friendly copy of
  * P and rebuilds it only when P's version changed (state gate, Sec. 3.5).
@@ -378,6 +403,13 @@ BAMG_API bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** 
 /* The cached restriction R = P^T of a level (NULL on the coarsest level);
  * owned by the hierarchy, refreshed when P changes. */
 BAMG_API bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R);
+/* State gate (Sec. 3.5): how many times the level's prolongator-side caches
+ * were rebuilt since setup: the block-ordered copy of P inside the level's
+ * Galerkin plan (*p_refreshes) and R = P^T (*r_refreshes).  Both are
+ * rebuilt only when P's version changed (cold setup or bamg_mg_resetup),
+ * never by bamg_mg_update.  Host outputs; either may be NULL. */
+BAMG_API bamg_status bamg_mg_get_gate_counts(const bamg_mg* mg, int level, uint64_t* p_refreshes,
+                                             uint64_t* r_refreshes);
 BAMG_API bamg_status bamg_mg_get_level_scalars(const bamg_mg* mg, int level, double* lambda_max,
                                       double* omega);
 BAMG_API bamg_status bamg_mg_get_dinv(const bamg_mg* mg, int level, double* dinv);

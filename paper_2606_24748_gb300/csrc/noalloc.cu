@@ -1,8 +1,8 @@
 // Residual norm ||b - A x||_2 of a square 3x3- or 6x6-block operator with no
 // device allocation: the partial sums of the reduction live in a file-scope
 // device array instead of the context's work buffers.  For callers that
-// cannot call cudaMalloc (code running inside a CUDA host callback, or inside
-// a framework whose device memory is entirely pre-reserved by its own pool).
+// cannot call cudaMalloc: code inside a framework whose device memory is
+// entirely pre-reserved by its own pool.
 #include <mutex>
 
 #include "device.cuh"

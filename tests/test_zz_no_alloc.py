@@ -1,7 +1,7 @@
 """The allocation-free residual-norm entry point.
 
-Some callers cannot call cudaMalloc (code inside a CUDA host callback, or an
-application whose device memory is all pre-reserved by its own pool); they use
+Some callers cannot call cudaMalloc (an application whose device memory is
+all pre-reserved by its own pool, where one more allocation would fail); they use
 bamg_bsr_residual_norm_noalloc, whose reduction scratch is a fixed device
 array inside the library.  Its result must equal the residual norm that the
 existing CG entry point reports for the same solution, on two calls in a row.
