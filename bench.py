@@ -37,7 +37,10 @@ from workloads.elasticity import (Mesh, body_force, coo_indices, coo_values, ele
                                   perturbation)
 
 METRIC = "PtAP+V-cycle HBM GB/s; CG time to rtol 1e-8, FP64 vs mixed/learned"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x flop/FMA x max clock
+# FP64 FMA peak from unit counts and the maximum clock (SMs x DFMA/clk/SM x
+# flop/FMA x 2.07 GHz); the roofline's denominator is the probe's measured
+# rate (bamg_probe_fma_rate), this figure is reported beside it
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 RTOL = 1e-8
 MAXIT = 500
 # DRAM bytes per launch of the dominant kernel from one ncu capture
@@ -67,7 +70,9 @@ def parse():
                         "else written after tuning; makes a run under a profiler use the timed run's choices")
     p.add_argument("--no-multi", action="store_true", help="skip the 16-right-hand-side measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the 32-problem batch measurement")
-    p.add_argument("--only", default="", choices=["", "multi", "batch"],
+    p.add_argument("--no-large", action="store_true",
+                   help="skip the 127^3 FP64-vs-mixed comparison (4 levels, 6.3 M dofs)")
+    p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large"],
                    help="run only that measurement (its own JSON object; used for profiling)")
     return p.parse_args()
 
@@ -146,8 +151,16 @@ def level_sizes(B, mg):
     return out
 
 
-def step_bytes(levels, n_coo, precond_applications, cg_its, mixed, power_its=15):
+def vcycles_per_solve(cg_its):
+    """V-cycles of a PCG solve that took cg_its iterations: one before the
+    first iteration and one after every iteration that did not converge
+    (the last iteration's test ends the solve before its preconditioner)."""
+    return cg_its
+
+
+def step_bytes(levels, n_coo, cg_its, mixed, power_its=15):
     """Algorithmic bytes of one reuse step (see bytes_model)."""
+    precond_applications = vcycles_per_solve(cg_its)
     s = 4 if mixed else 8
     A0 = levels[0]["A"]
     parts = {}
@@ -317,6 +330,9 @@ def run_ours(args):
         tdist.init_process_group("nccl")
         dist = tdist
     K, W = args.steps, args.warmup
+    pctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    alu = alu_peaks(B, pctx)
+    B.bamg_ctx_destroy(pctx)
     stream_bytes = 72 * Mesh(args.ne, args.order).nodes_per_element ** 2 * args.ne ** 3
     wl = Workload(B, torch, args.ne, 0.3, args.precision, order=args.order,
                   n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))), autotune=args.autotune,
@@ -343,12 +359,12 @@ def run_ours(args):
     B.bamg_ctx_profile(wl.ctx, 0)
     its = [o["iterations"] for o in outs]
     ms_step = slowest_rank_ms(torch, dist, ms / K)
-    per_step = [step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]
+    per_step = [step_bytes(wl.levels, wl.n_coo, i, wl.mixed)[0] for i in its]
     bytes_step = float(np.mean(per_step))
     value = replica_value(world, bytes_step, ms_step)
-    _, parts, vc_bytes = step_bytes(wl.levels, wl.n_coo, its[-1] + 1, its[-1], wl.mixed)
+    _, parts, vc_bytes = step_bytes(wl.levels, wl.n_coo, its[-1], wl.mixed)
 
-    roof = roofline(wl, prof, B)
+    roof = roofline(wl, prof, B, alu)
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -359,6 +375,7 @@ def run_ours(args):
         "bytes_parts": {k: int(v) for k, v in parts.items()},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "alu_peaks": alu,
         "clocks": clk,
         "kernel_ms": {k: {"total_ms": round(v[0], 3), "launches": v[1]} for k, v in table.items()},
         "kernel_ms_steps": KERNEL_TABLE_STEPS,
@@ -379,7 +396,7 @@ def run_ours(args):
     if not args.no_e2e:
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
     if not args.no_multi and args.precision == "fp64" and rank == 0 and world == 1:
-        result["multi_rhs"] = multi_rhs(wl, torch, B)
+        result["multi_rhs"] = multi_rhs(wl, torch, B, alu)
     if not args.no_batch and rank == 0 and world == 1:
         result["batch"] = batch_solve(torch, B)
     if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
@@ -389,7 +406,12 @@ def run_ours(args):
                                  "true_residual_rel": out0["true_rnorm"] / out0["bnorm"]}
         wl.close()
         wl = None
-        result["mixed"] = compare_mixed(args, torch, B, x64)
+        result["mixed"] = compare_mixed(args, torch, B, x64, alu)
+    if not args.no_large and args.order == 1 and args.ne < 127 and rank == 0 and world == 1:
+        if wl is not None:
+            wl.close()
+            wl = None
+        result["large"] = large_compare(torch, B, alu)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(ne=24 // args.order, order=args.order)
     if wl is not None:
@@ -412,7 +434,17 @@ def sources_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
-def roofline(wl, prof, B):
+def alu_peaks(B, ctx):
+    """Measured FMA rates of the FP64 and FP32 pipes (TFLOP/s) on this GPU."""
+    fp64 = B.bamg_probe_fma_rate(ctx, B.BAMG_FP64)
+    fp32 = B.bamg_probe_fma_rate(ctx, B.BAMG_FP32)
+    return {"fp64_tflops": round(fp64, 4), "fp32_tflops": round(fp32, 2),
+            "fp64_derived_tflops": round(FP64_PEAK_DERIVED_TFLOPS, 4),
+            "how": "bamg_probe_fma_rate: 8 independent FMA chains per thread, full occupancy on every SM, "
+                   "one launch of >= 0.1 s timed with CUDA events after a warm-up"}
+
+
+def roofline(wl, prof, B, alu):
     """Dominant kernel of the timed region: algorithmic bytes/flops per launch / mean duration."""
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
@@ -446,12 +478,15 @@ def roofline(wl, prof, B):
         traffic = int(rec[0])
     out = {"kernel": name, "launches": cnt, "avg_ms": round(avg_s * 1e3, 4), "bytes_per_launch": int(bts),
            "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3), "traffic": traffic}
-    fp64_bound = (not wl.mixed) and fl is not None and (fl / (FP64_PEAK_TFLOPS * 1e12)) > (bts / (hbm * 1e9))
+    peak64 = alu["fp64_tflops"]
+    fp64_bound = (not wl.mixed) and fl is not None and (fl / (peak64 * 1e12)) > (bts / (hbm * 1e9))
     if fp64_bound:
         tf = fl / avg_s / 1e12
-        out.update({"bound": "alu", "achieved": round(tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
-                    "unit": "TFLOP/s", "frac": round(tf / FP64_PEAK_TFLOPS, 3),
-                    "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)"})
+        out.update({"bound": "alu", "achieved": round(tf, 4), "peak": peak64,
+                    "unit": "TFLOP/s", "frac": round(tf / peak64, 3),
+                    "peak_source": "FP64 FMA pipe, measured in this run (bamg_probe_fma_rate)",
+                    "peak_derived": round(FP64_PEAK_DERIVED_TFLOPS, 4),
+                    "frac_of_derived": round(tf / FP64_PEAK_DERIVED_TFLOPS, 3)})
     else:
         out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 3), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"})
@@ -608,7 +643,7 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
     ms, outs = timed(torch, dist, step, K)
     ms_step = slowest_rank_ms(torch, dist, ms / K)
     its = [o["iterations"] for o in outs]
-    bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i + 1, i, wl.mixed)[0] for i in its]))
+    bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i, wl.mixed)[0] for i in its]))
     return {"value": round(replica_value(world, bytes_step, ms_step), 2), "unit": "GB/s",
             "ms_per_step": round(ms_step, 4),
             "h2d_bytes_per_step": int(host_in[0].numel() * 8 + host_b.numel() * 8),
@@ -629,7 +664,7 @@ def event_ms(torch, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def multi_rhs(wl, torch, B, k=16):
+def multi_rhs(wl, torch, B, alu, k=16):
     """k seeded N(0,1) right-hand sides (clamped dofs zeroed) on the workload's
     operator: blocked SpMM against k SpMVs, and the k-column PCG against k
     single-vector solves, in the FP64 form and the mixed form."""
@@ -664,7 +699,7 @@ def multi_rhs(wl, torch, B, k=16):
                                "tflops": round(flops / t_mm / 1e9, 4),
                                "k_spmv_ms": round(t_mv, 4), "speedup_vs_k_spmv": round(t_mv / t_mm, 2)}
         if prec == B.BAMG_FP64:
-            out[f"spmm_{name}"]["frac_fp64_peak"] = round(flops / t_mm / 1e9 / FP64_PEAK_TFLOPS, 3)
+            out[f"spmm_{name}"]["frac_fp64_peak"] = round(flops / t_mm / 1e9 / alu["fp64_tflops"], 3)
     # k-column PCG vs k single solves: FP64 hierarchy (the workload's) and a mixed one
     ctx, A = wl.ctx, wl.A
     o = B.bamg_mg_opts_default()
@@ -731,7 +766,7 @@ def batch_solve(torch, B, seed=7, count=32):
     same = all(i["iterations"] == o["iterations"] for i, o in zip(infos, seq[-1]))
     nbytes = 0
     for p, it in zip(probs, its):
-        _, parts, _ = step_bytes(p["levels"], p["n_coo"], it + 1, it, False)
+        _, parts, _ = step_bytes(p["levels"], p["n_coo"], it, False)
         nbytes += parts["vcycles"] + parts["cg"]
     out = {"problems": count, "seed": seed,
            "dofs_total": int(sum(p["b"].numel() for p in probs)),
@@ -752,19 +787,26 @@ def batch_solve(torch, B, seed=7, count=32):
     return out
 
 
-def compare_mixed(args, torch, B, x64=None):
-    """Time to rtol 1e-8 of the mixed-precision form on the same workload, and
-    its solution against the FP64 form's for the same input."""
-    K = max(3, min(args.steps, 10))
-    stream_bytes = 72 * Mesh(args.ne, args.order).nodes_per_element ** 2 * args.ne ** 3
-    wl = Workload(B, torch, args.ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))),
+def compare_mixed(args, torch, B, x64, alu, ne=None, steps=None):
+    """Time to rtol 1e-8 of the mixed-precision form on the same workload, its
+    roofline, and its solution against the FP64 form's for the same input."""
+    ne = args.ne if ne is None else ne
+    K = max(3, min(args.steps, 10)) if steps is None else steps
+    stream_bytes = 72 * Mesh(ne, args.order).nodes_per_element ** 2 * ne ** 3
+    wl = Workload(B, torch, ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))),
                   order=args.order)
-    for k in range(2):
+    for k in range(3):
         wl.step(k)
+    B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
     ms, outs = timed(torch, None, lambda k: wl.step(k), K)
+    prof = {name: B.bamg_ctx_profile_read(wl.ctx, slot) for name, slot in B.PROF_SLOTS.items()}
+    B.bamg_ctx_profile_slots(wl.ctx, [])
     ph = phases(wl, torch, B)
     its = [o["iterations"] for o in outs]
-    res = {"ms_per_step": round(ms / K, 4), "cg_iterations": its, "phases_ms": ph,
+    bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i, True)[0] for i in its]))
+    res = {"ms_per_step": round(ms / K, 4), "steps": K, "cg_iterations": its,
+           "value": round(bytes_step / (ms / K / 1e3) / 1e9, 2), "unit": "GB/s", "phases_ms": ph,
+           "roofline": roofline(wl, prof, B, alu),
            "true_residual_rel": outs[-1]["true_rnorm"] / outs[-1]["bnorm"]}
     if x64 is not None:
         out0 = wl.step(0)
@@ -774,6 +816,39 @@ def compare_mixed(args, torch, B, x64=None):
                          "solution_rel_diff_vs_fp64": float(d.item())}
     wl.close()
     return res
+
+
+def large_compare(torch, B, alu, ne=127, steps=5, warmup=3):
+    """The 127^3-element problem (128^3 nodes, 6,291,456 dofs, 4 levels): the
+    FP64 reuse step against the mixed one (FP32 V-cycle under FP64 CG), each
+    timed over `steps` steps after `warmup`, with the rooflines of their
+    dominant kernels and the mixed solution's distance from the FP64 one for
+    the same input (both recompute the true residual at exit)."""
+    args = parse_args_for_test(["--ne", str(ne), "--steps", str(steps)])
+    stream_bytes = 72 * 64 * ne ** 3
+    wl = Workload(B, torch, ne, 0.3, "fp64", n_inputs=min(steps, max(2, int(16e9 // stream_bytes))))
+    for k in range(warmup):
+        wl.step(k)
+    B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
+    ms, outs = timed(torch, None, lambda k: wl.step(k), steps)
+    prof = {name: B.bamg_ctx_profile_read(wl.ctx, slot) for name, slot in B.PROF_SLOTS.items()}
+    B.bamg_ctx_profile_slots(wl.ctx, [])
+    its = [o["iterations"] for o in outs]
+    bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i, False)[0] for i in its]))
+    fp64 = {"ms_per_step": round(ms / steps, 4), "steps": steps, "cg_iterations": its,
+            "value": round(bytes_step / (ms / steps / 1e3) / 1e9, 2), "unit": "GB/s",
+            "roofline": roofline(wl, prof, B, alu),
+            "true_residual_rel": outs[-1]["true_rnorm"] / outs[-1]["bnorm"]}
+    out0 = wl.step(0)
+    x64 = wl.x.clone()
+    fp64["input0"] = {"cg_iterations": out0["iterations"], "true_residual_rel": out0["true_rnorm"] / out0["bnorm"]}
+    levels = len(wl.levels)
+    wl.close()
+    mixed = compare_mixed(args, torch, B, x64, alu, ne=ne, steps=steps)
+    return {"workload": f"elasticity {ne}^3 Q1 elements, {3 * (ne + 1) ** 3} dofs, {levels}-level SA-AMG, "
+                        f"reuse step, FP64 against mixed FP32/FP64",
+            "fp64": fp64, "mixed": mixed,
+            "mixed_speedup": round(fp64["ms_per_step"] / mixed["ms_per_step"], 3)}
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
@@ -816,7 +891,7 @@ class OracleSample:
         h2 = omg.update(self.h, A)
         x, its, info = krylov.pcg(h2.levels[0].As, self.b, lambda r: omg.vcycle(h2, r), RTOL, MAXIT)
         dt = time.perf_counter() - t0
-        nbytes = step_bytes(oracle_levels(h2), int(self.bi.size), its + 1, its, False)[0]
+        nbytes = step_bytes(oracle_levels(h2), int(self.bi.size), its, False)[0]
         return dt, nbytes, its
 
 
@@ -919,7 +994,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": round(tt / K * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": f"synthetic: seeded Q{args.order} elasticity, per-element stiffness perturbed by U[-1%,1%] each step",
-            "config": workload_config(args.ne, args.precision, args.gpus, args.order),
+            "config": dict(workload_config(ne, args.precision, args.gpus, args.order),
+                           sample_of=workload_config(args.ne, args.precision, args.gpus, args.order)["workload"],
+                           l2="host run (no GPU cache)",
+                           note="the oracle runs a smaller mesh of the same problem; GB/s of algorithmic "
+                                "bytes is compared across the two sizes"),
             "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "kind": "oracle", "cores": 1, "sample": desc},
             "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -933,8 +1012,21 @@ def run_only(args):
         build()
     if args.only == "batch":
         return {"only": "batch", "batch": batch_solve(torch, B)}
+    if args.only in ("peaks", "large"):
+        ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+        clocks = Clocks(0)
+        clocks.start()
+        alu = alu_peaks(B, ctx)
+        clk = clocks.stop()
+        B.bamg_ctx_destroy(ctx)
+        if args.only == "peaks":
+            return {"only": "peaks", "alu_peaks": alu, "clocks": clk}
+        return {"only": "large", "alu_peaks": alu, "large": large_compare(torch, B, alu, ne=args.ne, steps=args.steps)}
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    alu = alu_peaks(B, ctx)
+    B.bamg_ctx_destroy(ctx)
     wl = Workload(B, torch, args.ne, 0.3, "fp64", n_inputs=1)
-    out = {"only": "multi", "multi_rhs": multi_rhs(wl, torch, B)}
+    out = {"only": "multi", "multi_rhs": multi_rhs(wl, torch, B, alu)}
     wl.close()
     return out
 

@@ -58,6 +58,10 @@ _SIGS = {
     "bamg_ctx_create": [_P, _PP],
     "bamg_ctx_destroy": [_P],
     "bamg_ctx_sync": [_P],
+    "bamg_probe_fma_rate": [_P, ctypes.c_int, _P],
+    "bamg_ctx_set_wait_limit": [_P, _I64],
+    "bamg_mg_get_gate_counts": [_P, ctypes.c_int, _P, _P],
+    "bamg_ptap_get_refreshes": [_P, _P],
     "bamg_ctx_profile": [_P, ctypes.c_int],
     "bamg_ctx_profile_slots": [_P, ctypes.c_uint],
     "bamg_device_memory": [_P, _P, _P, ctypes.c_int],
@@ -208,6 +212,30 @@ def bamg_device_memory(ctx, reset_peak: bool = False) -> tuple[int, int]:
 
 def bamg_kernel_launches() -> int:
     return int(lib().bamg_kernel_launches())
+
+
+def bamg_ctx_set_wait_limit(ctx, polls: int):
+    _check(lib().bamg_ctx_set_wait_limit(ctx, int(polls)), ctx)
+
+
+def bamg_mg_get_gate_counts(mg, level: int) -> tuple[int, int]:
+    """(rebuilds of the plan's block-ordered P, rebuilds of R) of a level."""
+    p, r = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().bamg_mg_get_gate_counts(mg, int(level), ctypes.byref(p), ctypes.byref(r)), None)
+    return p.value, r.value
+
+
+def bamg_ptap_get_refreshes(plan) -> int:
+    p = ctypes.c_uint64()
+    _check(lib().bamg_ptap_get_refreshes(plan, ctypes.byref(p)), None)
+    return p.value
+
+
+def bamg_probe_fma_rate(ctx, precision: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the FP64 or FP32 pipe."""
+    out = ctypes.c_double()
+    _check(lib().bamg_probe_fma_rate(ctx, int(precision), ctypes.byref(out)), ctx)
+    return out.value
 
 
 # ---------------------------------------------------------- block matrices

@@ -316,6 +316,12 @@ bamg_status bamg_ctx_destroy(bamg_ctx* c) {
 
 const char* bamg_last_error(const bamg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+bamg_status bamg_ctx_set_wait_limit(bamg_ctx* c, int64_t polls) {
+  if (!c || polls < 0) return BAMG_ERR_INVALID;
+  c->wait_limit = polls;
+  return BAMG_OK;
+}
+
 bamg_status bamg_ctx_profile(bamg_ctx* c, int enable) {
   return bamg_ctx_profile_slots(c, enable ? ~0u : 0u);
 }

@@ -245,7 +245,7 @@ __device__ void winv_cols(double* __restrict__ St, int64_t ld, const double* __r
 // that the shrinking trailing matrix leaves idle.
 __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int64_t ld, int nt, double* Dinv,
                                                       int* err, double* F2, double* W2, double* Dinv2,
-                                                      unsigned* qctr) {
+                                                      unsigned* qctr, int64_t wait_limit) {
   cooperative_groups::grid_group grid = cooperative_groups::this_grid();
   __shared__ double a[kT][kT + 1], w[kT][kT + 1];
   __shared__ unsigned short tri[kT * (kT + 1) / 2];
@@ -290,13 +290,16 @@ __global__ void __launch_bounds__(256) k_dense_factor(double* F, double* W, int6
     if (b == 0 && T > 0) {
       const int g = k + 1;
       if (threadIdx.x == 0) {
+        // bounded: after wait_limit polls (about 0.4 s at the default of
+        // 2^22) record a timeout and go on rather than wait forever; every
+        // CTA still reaches the next grid barrier
         const unsigned target = 4u * (unsigned)(k + 1);
-        int spins = 0;
-        while (atomicAdd(qctr + mi, 0u) < target) {
-          if (++spins > (1 << 22)) {  // about 0.4 s: record and go on rather than wait forever
+        for (int64_t polls = 0;; ++polls) {
+          if (polls >= wait_limit) {
             set_err(err, kDevTimeout);
             break;
           }
+          if (atomicAdd(qctr + mi, 0u) >= target) break;
           __nanosleep(64);
         }
         __threadfence();
@@ -627,7 +630,8 @@ static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld
   int* err = ctx->d_err;
   unsigned* qctr = ctx->d_counters + kFactorCounters;
   BAMG_CUDA(cudaMemsetAsync(qctr, 0, 2 * sizeof(unsigned), ctx->stream));
-  void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2, &qctr};
+  int64_t wait_limit = ctx->wait_limit;
+  void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2, &qctr, &wait_limit};
   BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, ctx->stream));
   BAMG_COUNT_LAUNCH;
   return Status{};

@@ -83,6 +83,7 @@ struct bamg_ctx {
   int* d_err = nullptr;            // device error word (first error code wins)
   double* d_partials = nullptr;    // kRedGridMax partial sums x 4 lanes
   unsigned* d_counters = nullptr;  // last-block counters (16 slots)
+  int64_t wait_limit = int64_t(1) << 22;  // polls of a bounded device wait before it gives up
   bamg::Prof prof;
 };
 
@@ -211,6 +212,7 @@ struct Level {
   bamg_bsr* R = nullptr;     // R = P^T (cached, rebuilt when P's version changes)
   int* rmap = nullptr;       // R block -> P block (pattern order)
   uint64_t r_version = ~0ull;
+  uint64_t r_refreshes = 0;  // rebuilds of R (state gate)
   bamg_ptap* plan = nullptr; // Galerkin plan A, P -> next level's A
   int bs = 0;
   int64_t n = 0;             // block rows

@@ -475,6 +475,7 @@ Status mg_refresh_restriction(bamg_mg* mg, int l) {
   }
   L.R->version++;
   L.r_version = L.P->version;
+  L.r_refreshes++;
   return Status{};
 }
 
@@ -881,6 +882,14 @@ bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** A, bamg_b
 bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R) {
   if (!mg || !R || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
   *R = mg->levels[level].R;
+  return BAMG_OK;
+}
+
+bamg_status bamg_mg_get_gate_counts(const bamg_mg* mg, int level, uint64_t* p_refreshes, uint64_t* r_refreshes) {
+  if (!mg || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
+  const Level& L = mg->levels[level];
+  if (p_refreshes) *p_refreshes = L.plan ? L.plan->pblk_refreshes : 0;
+  if (r_refreshes) *r_refreshes = L.r_refreshes;
   return BAMG_OK;
 }
 

@@ -461,6 +461,12 @@ bamg_status bamg_ptap_numeric_prec(bamg_ptap* plan, bamg_bsr* A, bamg_bsr* P, ba
   return s.ok() ? BAMG_OK : fail(plan->ctx, s);
 }
 
+bamg_status bamg_ptap_get_refreshes(const bamg_ptap* plan, uint64_t* p_refreshes) {
+  if (!plan || !p_refreshes) return BAMG_ERR_INVALID;
+  *p_refreshes = plan->pblk_refreshes;
+  return BAMG_OK;
+}
+
 bamg_status bamg_ptap_destroy(bamg_ptap* plan) {
   if (!plan) return BAMG_OK;
   ptap_release(plan);

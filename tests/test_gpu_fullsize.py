@@ -113,3 +113,22 @@ def test_cg_reaches_the_tolerance_with_the_true_residual(big, precision):
     finally:
         if gp is not big:
             gp.close()
+
+
+def test_booked_vcycles_equal_fine_chebyshev_launches(big):
+    """The bench's byte count books bench.vcycles_per_solve(its) V-cycles per
+    solve; each V-cycle launches the fine Chebyshev step three times (two
+    pre-smoothing steps, one post-smoothing step after the residual start)."""
+    import bench
+    b = torch.from_numpy(body_force(big.mesh)).cuda()
+    x = torch.zeros_like(b)
+    B.bamg_mg_update(big.ctx, big.mg)
+    B.bamg_cg_solve(big.ctx, big.mg, b, x, 1e-8, 500)      # captures the graphs
+    B.bamg_ctx_profile_slots(big.ctx, ["cheb_step_l0"])
+    try:
+        out = B.bamg_cg_solve(big.ctx, big.mg, b, x, 1e-8, 500)
+        torch.cuda.synchronize()
+        _, launches = B.bamg_ctx_profile_read(big.ctx, B.PROF_SLOTS["cheb_step_l0"])
+    finally:
+        B.bamg_ctx_profile_slots(big.ctx, [])
+    assert launches == 3 * bench.vcycles_per_solve(out["iterations"])
