@@ -72,7 +72,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the 32-problem batch measurement")
     p.add_argument("--no-large", action="store_true",
                    help="skip the 127^3 FP64-vs-mixed comparison (4 levels, 6.3 M dofs)")
-    p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large"],
+    p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large", "ptap"],
                    help="run only that measurement (its own JSON object; used for profiling)")
     return p.parse_args()
 
@@ -1012,6 +1012,11 @@ def run_only(args):
         build()
     if args.only == "batch":
         return {"only": "batch", "batch": batch_solve(torch, B)}
+    if args.only == "ptap":
+        wl = Workload(B, torch, args.ne, 0.3, "fp64", n_inputs=1)
+        out = {"only": "ptap", "ptap_reuse": ptap_reuse(wl, torch, B)}
+        wl.close()
+        return out
     if args.only in ("peaks", "large"):
         ctx = B.bamg_ctx_create(torch.cuda.current_stream())
         clocks = Clocks(0)

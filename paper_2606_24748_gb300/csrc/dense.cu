@@ -620,8 +620,8 @@ static int64_t half_bandwidth(const bamg_bsr* A) {
   return (b + 1) * A->br - 1;
 }
 
-static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld, int ntl, double* dt,
-                                 double* F2 = nullptr, double* W2 = nullptr, double* dt2 = nullptr) {
+static Status cooperative_factor(bamg_ctx* ctx, cudaStream_t st, double* F, double* W, int64_t ld, int ntl,
+                                 double* dt, double* F2 = nullptr, double* W2 = nullptr, double* dt2 = nullptr) {
   int per_sm = 0;
   BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
   if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
@@ -629,10 +629,10 @@ static Status cooperative_factor(bamg_ctx* ctx, double* F, double* W, int64_t ld
   if (grid / (F2 ? 2 : 1) < 5) return make_status(BAMG_ERR_CUDA, "dense factor needs at least five CTAs per matrix");
   int* err = ctx->d_err;
   unsigned* qctr = ctx->d_counters + kFactorCounters;
-  BAMG_CUDA(cudaMemsetAsync(qctr, 0, 2 * sizeof(unsigned), ctx->stream));
+  BAMG_CUDA(cudaMemsetAsync(qctr, 0, 2 * sizeof(unsigned), st));
   int64_t wait_limit = ctx->wait_limit;
   void* args[] = {&F, &W, &ld, &ntl, &dt, &err, &F2, &W2, &dt2, &qctr, &wait_limit};
-  BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, ctx->stream));
+  BAMG_CUDA(cudaLaunchCooperativeKernel((void*)k_dense_factor, grid, 256, args, 0, st));
   BAMG_COUNT_LAUNCH;
   return Status{};
 }
@@ -665,9 +665,8 @@ static Status gemm_batch(const std::vector<GemmItem>& items, int s, double alpha
 }
 
 // Twisted block factorisation of the banded coarsest operator (see above).
-static Status band_factor(bamg_mg* mg) {
+static Status band_factor(bamg_mg* mg, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
-  cudaStream_t st = ctx->stream;
   Level& C = mg->levels.back();
   CoarseDense& D = mg->coarse;
   const bamg_bsr* A = C.A;
@@ -715,9 +714,9 @@ static Status band_factor(bamg_mg* mg) {
     if (kb >= 0 && kb < nc - 1) syrk.push_back({Dk(kb), BC(kb + 1), BC(kb + 1), kTriNone});
     if (!syrk.empty()) BAMG_TRY(gemm_batch<true>(syrk, s, -1.0, 1.0, 1, st));
     if (kt >= 0 && kb >= 0)
-      BAMG_TRY(cooperative_factor(ctx, Dk(kt), Wk(kt), s, ntl, D.dinv_tiles, Dk(kb), Wk(kb), dt1));
+      BAMG_TRY(cooperative_factor(ctx, st, Dk(kt), Wk(kt), s, ntl, D.dinv_tiles, Dk(kb), Wk(kb), dt1));
     else
-      BAMG_TRY(cooperative_factor(ctx, Dk(kt >= 0 ? kt : kb), Wk(kt >= 0 ? kt : kb), s, ntl, D.dinv_tiles));
+      BAMG_TRY(cooperative_factor(ctx, st, Dk(kt >= 0 ? kt : kb), Wk(kt >= 0 ? kt : kb), s, ntl, D.dinv_tiles));
     for (int k : {kt, kb})
       if (k >= 0) { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(k), Wt(k), s); BAMG_COUNT_LAUNCH; }
     // B_k = A_{k+1,k} W_k^T, C_k = A_{k-1,k} W_k^T (W_k lower triangular)
@@ -731,7 +730,7 @@ static Status band_factor(bamg_mg* mg) {
     if (t > 0) syrk.push_back({Dk(t), BC(t - 1), BC(t - 1), kTriNone});
     if (t + 1 < nc) syrk.push_back({Dk(t), BC(t + 1), BC(t + 1), kTriNone});
     for (auto& it : syrk) BAMG_TRY(gemm_batch<true>({it}, s, -1.0, 1.0, 1, st));  // same output: one at a time
-    BAMG_TRY(cooperative_factor(ctx, Dk(t), Wk(t), s, ntl, D.dinv_tiles));
+    BAMG_TRY(cooperative_factor(ctx, st, Dk(t), Wk(t), s, ntl, D.dinv_tiles));
     { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(t), Wt(t), s); BAMG_COUNT_LAUNCH; }
   }
   // chain matrices, off the critical path: all in two batched launches
@@ -811,9 +810,8 @@ static Status band_apply(bamg_mg* mg, const T* b, T* x, double* y, double* z, co
   return Status{};
 }
 
-static Status dense_factor(bamg_mg* mg) {
+static Status dense_factor(bamg_mg* mg, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
-  cudaStream_t st = ctx->stream;
   Level& C = mg->levels.back();
   CoarseDense& D = mg->coarse;
   const int bs = C.bs;
@@ -849,7 +847,7 @@ static Status dense_factor(bamg_mg* mg) {
   }
   BAMG_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * npad * npad, st));
   if (!D.dinv_tiles) BAMG_TRY(dalloc(&D.dinv_tiles, (int64_t)nt * kT * kT, st));
-  BAMG_TRY(cooperative_factor(ctx, F, W, npad, nt, D.dinv_tiles));
+  BAMG_TRY(cooperative_factor(ctx, st, F, W, npad, nt, D.dinv_tiles));
   // Wt = W^T (the factor in F is no longer needed)
   dim3 tg((unsigned)nt, (unsigned)nt);
   { k_transpose_dense<<<tg, 256, 0, st>>>(W, F, npad); BAMG_COUNT_LAUNCH; }
@@ -858,8 +856,7 @@ static Status dense_factor(bamg_mg* mg) {
   return Status{};
 }
 
-Status coarse_factor(bamg_mg* mg) {
-  cudaStream_t st = mg->ctx->stream;
+Status coarse_factor(bamg_mg* mg, cudaStream_t st) {
   Level& C = mg->levels.back();
   CoarseDense& D = mg->coarse;
   const bamg_bsr* A = C.A;
@@ -886,7 +883,7 @@ Status coarse_factor(bamg_mg* mg) {
     BAMG_TRY(upload(&D.rows, rows, st));
     BAMG_CUDA(cudaStreamSynchronize(st));
   }
-  BAMG_TRY(D.nc > 0 ? band_factor(mg) : dense_factor(mg));
+  BAMG_TRY(D.nc > 0 ? band_factor(mg, st) : dense_factor(mg, st));
   D.factored = true;
   return Status{};
 }

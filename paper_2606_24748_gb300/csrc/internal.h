@@ -294,6 +294,10 @@ struct bamg_mg {
   uint64_t cg_graph_kernels = 0;
   double* power_w[2] = {nullptr, nullptr};
   bamg::MultiWork* multi = nullptr;  // multi-right-hand-side work area
+  // second stream of the reuse update: the coarsest factorisation runs on it,
+  // forked after the last Galerkin product, joined before the update returns
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace bamg {
@@ -376,7 +380,7 @@ Status launch_gather_blocks(const bamg_bsr* A, const double* vals, double* out, 
 // Hierarchy internals shared by the setup, cycle and coarse-solver units.
 Status mg_refresh_level(bamg_mg* mg, int l);            // Dinv, eigen-estimate, Chebyshev coefficients
 Status mg_refresh_restriction(bamg_mg* mg, int l);      // state-gated R = P^T
-Status coarse_factor(bamg_mg* mg);                      // dense Cholesky + inverse of the coarsest level
+Status coarse_factor(bamg_mg* mg, cudaStream_t st);                      // dense Cholesky + inverse of the coarsest level
 template <typename T>
 Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t st);
 // The same solve for kp vectors stored RHS-minor (b, x: n x kp); work holds

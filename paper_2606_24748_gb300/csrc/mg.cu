@@ -535,6 +535,13 @@ static Status alloc_vectors(bamg_mg* mg) {
 
 static void mg_release(bamg_mg* mg) {
   cudaStream_t st = mg->ctx->stream;
+  if (mg->side) {
+    cudaStreamSynchronize(mg->side);
+    cudaStreamDestroy(mg->side);
+    cudaEventDestroy(mg->ev_fork);
+    cudaEventDestroy(mg->ev_join);
+    mg->side = nullptr;
+  }
   mg_release_graphs(mg);
   mg_release_multi(mg);
   for (auto& L : mg->levels) {
@@ -737,27 +744,53 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
   return Status{};
 }
 
+// The coarsest factorisation needs only the last Galerkin product and is a
+// chain of small dependent steps that leaves most of the GPU idle, while the
+// smoother refresh (block inverses, power iterations) keeps the FP64 pipes
+// busy and never reads the coarsest operator: the factor runs on a second
+// stream between the last product and the end of the update.
+static Status update_streams(bamg_mg* mg) {
+  if (mg->side) return Status{};
+  BAMG_CUDA(cudaStreamCreateWithFlags(&mg->side, cudaStreamNonBlocking));
+  BAMG_CUDA(cudaEventCreateWithFlags(&mg->ev_fork, cudaEventDisableTiming));
+  BAMG_CUDA(cudaEventCreateWithFlags(&mg->ev_join, cudaEventDisableTiming));
+  return Status{};
+}
+
 Status mg_update_impl(bamg_mg* mg) {
   const int nl = (int)mg->levels.size();
   const bamg_prec pp = mg->opts.precision == BAMG_FP32 ? BAMG_FP32 : BAMG_FP64;
+  cudaStream_t st = mg->ctx->stream;
   for (int l = 0; l + 1 < nl; ++l) {
     Level& L = mg->levels[l];
     BAMG_TRY(ptap_run(L.plan, L.A, L.P, mg->levels[l + 1].A, pp, true));
   }
-  for (int l = 0; l + 1 < nl; ++l) {
-    BAMG_TRY(mg_refresh_restriction(mg, l));
-    const int pr = prof_begin(mg->ctx, BAMG_PROF_REFRESH, mg->ctx->stream);
-    BAMG_TRY(mg_refresh_level(mg, l));
-    prof_end(mg->ctx, pr, mg->ctx->stream);
-  }
-  if (pp == BAMG_FP32) {
-    BAMG_TRY(bsr_ensure_fp32(mg->levels[0].A));
+  BAMG_TRY(update_streams(mg));
+  BAMG_CUDA(cudaEventRecord(mg->ev_fork, st));
+  BAMG_CUDA(cudaStreamWaitEvent(mg->side, mg->ev_fork, 0));
+  const Status fs = coarse_factor(mg, mg->side);
+  BAMG_CUDA(cudaEventRecord(mg->ev_join, mg->side));
+  auto refresh = [&]() -> Status {
+    BAMG_TRY(fs);
     for (int l = 0; l + 1 < nl; ++l) {
-      BAMG_TRY(bsr_ensure_fp32(mg->levels[l].P));
-      BAMG_TRY(bsr_ensure_fp32(mg->levels[l].R));
+      BAMG_TRY(mg_refresh_restriction(mg, l));
+      const int pr = prof_begin(mg->ctx, BAMG_PROF_REFRESH, st);
+      BAMG_TRY(mg_refresh_level(mg, l));
+      prof_end(mg->ctx, pr, st);
     }
-  }
-  return coarse_factor(mg);
+    if (pp == BAMG_FP32) {
+      BAMG_TRY(bsr_ensure_fp32(mg->levels[0].A));
+      for (int l = 0; l + 1 < nl; ++l) {
+        BAMG_TRY(bsr_ensure_fp32(mg->levels[l].P));
+        BAMG_TRY(bsr_ensure_fp32(mg->levels[l].R));
+      }
+    }
+    return Status{};
+  };
+  const Status rs = refresh();
+  // joined on every path: the caller's stream never runs ahead of the factor
+  BAMG_CUDA(cudaStreamWaitEvent(st, mg->ev_join, 0));
+  return rs;
 }
 
 }  // namespace bamg

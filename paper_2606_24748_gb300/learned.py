@@ -175,6 +175,10 @@ def run(ne: int = 48, n_train: int = 200, n_test: int = 50, epochs: int = 30, se
         "cg_its_plain": agg("plain", "cg_its"), "cg_its_learned": agg("learned", "cg_its"),
         "cg_ms_plain": agg("plain", "cg_ms"), "cg_ms_learned": agg("learned", "cg_ms"),
         "learned_better_fraction": float(np.mean([r["learned"]["rho"] < r["plain"]["rho"] for r in res])),
+        "all_converged": bool(all(r[k]["converged"] for r in res for k in ("plain", "learned"))),
+        "per_instance": [{"rho_plain": r["plain"]["rho"], "rho_learned": r["learned"]["rho"],
+                          "cg_its_plain": r["plain"]["cg_its"], "cg_its_learned": r["learned"]["cg_its"]}
+                         for r in res],
     }
     # the plain smoother stays the fallback unless the learned one converges faster
     out["use_learned"] = out["rho_learned"] < out["rho_plain"] and out["cg_its_learned"] <= out["cg_its_plain"]
