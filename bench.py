@@ -37,9 +37,11 @@ from workloads.elasticity import (Mesh, body_force, coo_indices, coo_values, ele
                                   perturbation)
 
 METRIC = "PtAP+V-cycle HBM GB/s; CG time to rtol 1e-8, FP64 vs mixed/learned"
-# FP64 FMA peak from unit counts and the maximum clock (SMs x DFMA/clk/SM x
-# flop/FMA x 2.07 GHz); the roofline's denominator is the probe's measured
-# rate (bamg_probe_fma_rate), this figure is reported beside it
+# FP64 FMA peak from unit counts and the maximum clock: SMs x DFMA/clk/SM x
+# flop/FMA x 2.07 GHz.  The roofline's denominator for FP64-bound kernels.  A
+# pure-FMA probe (bamg_probe_fma_rate) is measured beside it: it stays below
+# this figure (as does every FP64 kernel measured here), but also below what
+# the fused Chebyshev step sustains at 127^3, so it is not itself the peak.
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 RTOL = 1e-8
 MAXIT = 500
@@ -399,6 +401,8 @@ def run_ours(args):
         result["multi_rhs"] = multi_rhs(wl, torch, B, alu)
     if not args.no_batch and rank == 0 and world == 1:
         result["batch"] = batch_solve(torch, B)
+    if rank == 0 and world == 1:
+        result["mlp_training"] = mlp_training(torch, B)
     if not args.no_compare and args.precision == "fp64" and rank == 0 and world == 1:
         out0 = wl.step(0)
         x64 = wl.x.clone()
@@ -434,14 +438,22 @@ def sources_fingerprint() -> str:
     return h.hexdigest()[:16]
 
 
-def alu_peaks(B, ctx):
-    """Measured FMA rates of the FP64 and FP32 pipes (TFLOP/s) on this GPU."""
-    fp64 = B.bamg_probe_fma_rate(ctx, B.BAMG_FP64)
-    fp32 = B.bamg_probe_fma_rate(ctx, B.BAMG_FP32)
-    return {"fp64_tflops": round(fp64, 4), "fp32_tflops": round(fp32, 2),
-            "fp64_derived_tflops": round(FP64_PEAK_DERIVED_TFLOPS, 4),
-            "how": "bamg_probe_fma_rate: 8 independent FMA chains per thread, full occupancy on every SM, "
-                   "one launch of >= 0.1 s timed with CUDA events after a warm-up"}
+def alu_peaks(B, ctx, reps=1, clocks_index=None):
+    """FMA rates of the FP64 and FP32 pipes (TFLOP/s) from the library's probe
+    (best of `reps` launches of >= 0.1 s), with the SM clock sampled during
+    each when clocks_index is given, and the derived FP64 peak."""
+    out = {}
+    for name, prec in (("fp64", B.BAMG_FP64), ("fp32", B.BAMG_FP32)):
+        clk = Clocks(clocks_index) if clocks_index is not None else None
+        if clk:
+            clk.start()
+        out[f"{name}_probe_tflops"] = round(max(B.bamg_probe_fma_rate(ctx, prec) for _ in range(reps)), 4)
+        if clk:
+            out[f"{name}_probe_clocks"] = clk.stop()
+    out["fp64_peak_tflops"] = round(FP64_PEAK_DERIVED_TFLOPS, 4)
+    out["how"] = ("peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; probe: bamg_probe_fma_rate, 8 independent "
+                  "FMA chains per thread at full occupancy, one launch of >= 0.1 s timed with CUDA events")
+    return out
 
 
 def roofline(wl, prof, B, alu):
@@ -478,15 +490,15 @@ def roofline(wl, prof, B, alu):
         traffic = int(rec[0])
     out = {"kernel": name, "launches": cnt, "avg_ms": round(avg_s * 1e3, 4), "bytes_per_launch": int(bts),
            "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 3), "traffic": traffic}
-    peak64 = alu["fp64_tflops"]
+    peak64 = alu["fp64_peak_tflops"]
     fp64_bound = (not wl.mixed) and fl is not None and (fl / (peak64 * 1e12)) > (bts / (hbm * 1e9))
     if fp64_bound:
         tf = fl / avg_s / 1e12
         out.update({"bound": "alu", "achieved": round(tf, 4), "peak": peak64,
                     "unit": "TFLOP/s", "frac": round(tf / peak64, 3),
-                    "peak_source": "FP64 FMA pipe, measured in this run (bamg_probe_fma_rate)",
-                    "peak_derived": round(FP64_PEAK_DERIVED_TFLOPS, 4),
-                    "frac_of_derived": round(tf / FP64_PEAK_DERIVED_TFLOPS, 3)})
+                    "peak_source": "FP64 FMA pipe from unit counts and the maximum clock (152 x 2 DFMA/clk x "
+                                   "2 flop x 2.07 GHz); no FP64 rate measured on this part exceeds it",
+                    "probe_tflops": alu["fp64_probe_tflops"]})
     else:
         out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(gbs / hbm, 3), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"})
@@ -699,7 +711,7 @@ def multi_rhs(wl, torch, B, alu, k=16):
                                "tflops": round(flops / t_mm / 1e9, 4),
                                "k_spmv_ms": round(t_mv, 4), "speedup_vs_k_spmv": round(t_mv / t_mm, 2)}
         if prec == B.BAMG_FP64:
-            out[f"spmm_{name}"]["frac_fp64_peak"] = round(flops / t_mm / 1e9 / alu["fp64_tflops"], 3)
+            out[f"spmm_{name}"]["frac_fp64_peak"] = round(flops / t_mm / 1e9 / alu["fp64_peak_tflops"], 3)
     # k-column PCG vs k single solves: FP64 hierarchy (the workload's) and a mixed one
     ctx, A = wl.ctx, wl.A
     o = B.bamg_mg_opts_default()
@@ -784,6 +796,25 @@ def batch_solve(torch, B, seed=7, count=32):
         B.bamg_mg_destroy(p["mg"])
         B.bamg_bsr_destroy(p["A"])
         B.bamg_ctx_destroy(p["ctx"])
+    return out
+
+
+def mlp_training(torch, B):
+    """One training step of the learned-weight MLP (fused forward and
+    backward on the tensor cores, gradient reduction, Adam) on 2^20 seeded
+    feature rows: rows/s and its BF16 tensor rate against the measured burst
+    peak (the kernels are timed alone)."""
+    from paper_2606_24748_gb300 import learned
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    mlp = B.bamg_mlp_create(ctx, 12345)
+    try:
+        out = learned.train_step_rate(ctx, mlp)
+    finally:
+        B.bamg_mlp_destroy(mlp)
+        B.bamg_ctx_destroy(ctx)
+    peak = float(measured_peaks().get("bf16_tflops", 1932.6))
+    out["tensor_frac_of_bf16_peak"] = round(out["tflops"] / peak, 4)
+    out["bf16_peak_tflops"] = peak
     return out
 
 
@@ -1019,13 +1050,10 @@ def run_only(args):
         return out
     if args.only in ("peaks", "large"):
         ctx = B.bamg_ctx_create(torch.cuda.current_stream())
-        clocks = Clocks(0)
-        clocks.start()
-        alu = alu_peaks(B, ctx)
-        clk = clocks.stop()
+        alu = alu_peaks(B, ctx, reps=10 if args.only == "peaks" else 1, clocks_index=0)
         B.bamg_ctx_destroy(ctx)
         if args.only == "peaks":
-            return {"only": "peaks", "alu_peaks": alu, "clocks": clk}
+            return {"only": "peaks", "alu_peaks": alu}
         return {"only": "large", "alu_peaks": alu, "large": large_compare(torch, B, alu, ne=args.ne, steps=args.steps)}
     ctx = B.bamg_ctx_create(torch.cuda.current_stream())
     alu = alu_peaks(B, ctx)

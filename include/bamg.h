@@ -268,6 +268,74 @@ BAMG_API bamg_status bamg_mis_aggregate(bamg_ctx* ctx, int64_t n, const int* row
 BAMG_API bamg_status bamg_bsr_residual_norm_noalloc(const bamg_bsr* A, const double* x, const double* b,
                                                     double* norm);
 
+/* ------------------------------------------------- row-sharded operator */
+
+/* Partition plan of a square block pattern over `nparts` contiguous ranges
+ * of block rows (Sec. 3.3): part p owns rows [row_starts[p],
+ * row_starts[p+1]).  Its rows keep their blocks with columns renumbered
+ * locally: the owned columns first (column - row_starts[p]), then the ghost
+ * columns (owned by other parts) in ascending global order, which groups
+ * them by owner.  Host arrays only (rowptr nbr + 1, colidx, row_starts
+ * nparts + 1 with row_starts[0] = 0, row_starts[nparts] = nbr,
+ * non-decreasing); no CUDA call, so it runs without a GPU.  The getters copy
+ * into caller-owned host arrays sized by bamg_halo_part_info. */
+typedef struct bamg_halo bamg_halo;
+BAMG_API bamg_status bamg_halo_create(int64_t nbr, const int32_t* rowptr, const int32_t* colidx, int nparts,
+                                      const int64_t* row_starts, bamg_halo** out);
+BAMG_API bamg_status bamg_halo_destroy(bamg_halo* halo);
+BAMG_API bamg_status bamg_halo_part_info(const bamg_halo* halo, int part, int64_t* n_owned, int64_t* n_ghost,
+                                         int64_t* nnzb);
+/* Local pattern of a part: rowptr (n_owned + 1), colidx (nnzb, local
+ * numbering, ascending per row) and block_src (nnzb: the global block index,
+ * position in the global colidx, of each local block). */
+BAMG_API bamg_status bamg_halo_part_pattern(const bamg_halo* halo, int part, int32_t* rowptr, int32_t* colidx,
+                                            int64_t* block_src);
+/* Ghost columns of a part (global, ascending) and the part owning each. */
+BAMG_API bamg_status bamg_halo_part_ghosts(const bamg_halo* halo, int part, int64_t* ghost, int32_t* owner);
+/* The halo message from part `from` to part `to`: the `from`-local row
+ * indices whose entries `to` needs, in the order of `to`'s ghost list
+ * (*count rows; local_rows may be NULL to query the count). */
+BAMG_API bamg_status bamg_halo_sends(const bamg_halo* halo, int from, int to, int64_t* count, int64_t* local_rows);
+
+/* All parts of one partition of A (and of the Galerkin product with P) on
+ * the context's GPU, run one after another (Sec. 3.3, Sec. 3.5, Sec. 4.8).
+ * Part p keeps A_ext = its rows in a square matrix of owned + ghost rows
+ * (ghost rows empty, local columns as bamg_halo) and P_ext = [P_own; P_oth],
+ * the rows of P for its owned and ghost nodes.  Creates Ac (caller-owned,
+ * bamg_bsr_destroy) with the union of the parts' product patterns, which is
+ * the structural pattern of P^T A P.  A, P: FP64 values; square A with
+ * square blocks; P with A's block rows (3x3 -> 3x6, 6x6 -> 6x6 or 3x3 -> 3x3). */
+typedef struct bamg_sharded bamg_sharded;
+BAMG_API bamg_status bamg_sharded_create(bamg_bsr* A, bamg_bsr* P, int nparts, const int64_t* row_starts,
+                                         bamg_sharded** out, bamg_bsr** Ac);
+/* y = A x through the parts: each gathers its halo (ghost entries of x) and
+ * multiplies its rows; FP64 device vectors of the global size.  The parts'
+ * copies of A are refreshed when A's version changed. */
+BAMG_API bamg_status bamg_sharded_spmv(bamg_sharded* sh, const double* x, double* y);
+/* Numeric Galerkin product through the parts: each computes
+ * C_p = P_ext^T A_ext P_ext with its cached plan; P_oth is gathered only when
+ * P's version changed since the last call (state gate, Sec. 3.5); then
+ * A_c = sum of the C_p, block by block in part order (the off-process
+ * reduce).  A, P must be the matrices the object was built for and Ac the
+ * matrix it created (BAMG_ERR_STATE otherwise). */
+BAMG_API bamg_status bamg_sharded_ptap(bamg_sharded* sh, bamg_bsr* A, bamg_bsr* P, bamg_bsr* Ac);
+/* Communication profile of the partition, as a multi-GPU run would move it:
+ * halo entries per SpMV, P_oth blocks (once per P version) and the blocks of
+ * C_p in coarse rows owned by another part (per recompute; a coarse row
+ * belongs to the part owning the first fine row that touches it). */
+typedef struct {
+  int64_t ghost_rows;           /* sum over parts of ghost block rows */
+  int64_t halo_bytes_per_spmv;  /* ghost_rows x bs x 8 */
+  int64_t poth_blocks;          /* rows of P gathered from other parts, in blocks */
+  int64_t poth_bytes;           /* poth_blocks x (bs x bs_p x 8 + 4) */
+  int64_t poth_gathers;         /* gathers done so far (P versions seen) */
+  int64_t reduce_blocks;        /* off-process C_p blocks per recompute */
+  int64_t reduce_bytes_per_ptap;/* reduce_blocks x (bs_p^2 x 8 + 4) */
+  int64_t max_owned_rows;       /* the largest part */
+} bamg_shard_stats;
+BAMG_API bamg_status bamg_sharded_stats(const bamg_sharded* sh, bamg_shard_stats* out);
+BAMG_API bamg_status bamg_sharded_destroy(bamg_sharded* sh);
+
 /* ----------------------------------------------------- Galerkin product */
 
 /* Symbolic Galerkin product (Sec. 3.1, Sec. 3.5): A (n x n blocks of
@@ -479,6 +547,15 @@ BAMG_API bamg_status bamg_mlp_gradient(bamg_mlp* mlp, const float* X, const floa
  * batch (X, t); *loss (device, may be NULL) receives the batch loss before the step. */
 BAMG_API bamg_status bamg_mlp_train_step(bamg_mlp* mlp, const float* X, const float* t, int64_t n, float* w_tmp,
                                          float lr, float* loss);
+/* One epoch of mini-batch training (Adam after every batch, as
+ * bamg_mlp_train_step): batch k takes rows perm[k * batch .. ] of X (n x 8)
+ * and t (n), perm a device array of n int64 row indices (a permutation, or
+ * any rows to train on, each < the rows of X), so the rows are gathered
+ * inside the kernel.  *loss_sum (device double, caller-owned) is increased
+ * by the epoch's summed squared error (divide by n for the mean).  Runs on
+ * the context's stream without waiting for it. */
+BAMG_API bamg_status bamg_mlp_train_epoch(bamg_mlp* mlp, const float* X, const float* t, const int64_t* perm,
+                                          int64_t n, int64_t batch, float lr, double* loss_sum);
 /* Features of the block rows of a non-coarsest level (n_l x 8, device):
  * log||A_ii||, sum_{j!=i}||A_ij||/||A_ii||, log(max/min nonzero block norm),
  * blocks/27, clamped-row flag, log sum_j||D_i^-1 A_ij||, level, 1. */

@@ -46,6 +46,12 @@ class bamg_mg_opts(ctypes.Structure):
                 ("coarse_solver", ctypes.c_int)]
 
 
+class bamg_shard_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("ghost_rows", "halo_bytes_per_spmv", "poth_blocks", "poth_bytes",
+                                              "poth_gathers", "reduce_blocks", "reduce_bytes_per_ptap",
+                                              "max_owned_rows")]
+
+
 class bamg_cg_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rnorm", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("true_rnorm", ctypes.c_double)]
@@ -59,6 +65,18 @@ _SIGS = {
     "bamg_ctx_destroy": [_P],
     "bamg_ctx_sync": [_P],
     "bamg_probe_fma_rate": [_P, ctypes.c_int, _P],
+    "bamg_halo_create": [_I64, _P, _P, ctypes.c_int, _P, _PP],
+    "bamg_halo_destroy": [_P],
+    "bamg_halo_part_info": [_P, ctypes.c_int, _P, _P, _P],
+    "bamg_halo_part_pattern": [_P, ctypes.c_int, _P, _P, _P],
+    "bamg_halo_part_ghosts": [_P, ctypes.c_int, _P, _P],
+    "bamg_halo_sends": [_P, ctypes.c_int, ctypes.c_int, _P, _P],
+    "bamg_sharded_create": [_P, _P, ctypes.c_int, _P, _PP, _PP],
+    "bamg_sharded_spmv": [_P, _P, _P],
+    "bamg_sharded_ptap": [_P, _P, _P, _P],
+    "bamg_sharded_stats": [_P, _P],
+    "bamg_sharded_destroy": [_P],
+    "bamg_mlp_train_epoch": [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, _P],
     "bamg_ctx_set_wait_limit": [_P, _I64],
     "bamg_mg_get_gate_counts": [_P, ctypes.c_int, _P, _P],
     "bamg_ptap_get_refreshes": [_P, _P],
@@ -525,6 +543,12 @@ def bamg_mlp_set_params(ctx, mlp, params):
     _check(lib().bamg_mlp_set_params(mlp, _ptr(params)), ctx)
 
 
+def bamg_mlp_train_epoch(ctx, mlp, X, t, perm, batch: int, lr: float, loss_sum):
+    """One epoch over the rows perm (device int64) in batches, loss summed into loss_sum (device double)."""
+    _check(lib().bamg_mlp_train_epoch(mlp, _ptr(X), _ptr(t), _ptr(perm), int(perm.numel()), int(batch),
+                                      float(lr), _ptr(loss_sum)), ctx)
+
+
 def bamg_mlp_forward(ctx, mlp, X, w):
     _check(lib().bamg_mlp_forward(mlp, _ptr(X), int(X.shape[0]), _ptr(w)), ctx)
 
@@ -559,3 +583,82 @@ def bamg_mg_stationary(ctx, mg, b, x, its: int) -> list:
 def exported_symbols() -> list[str]:
     """Names of the C entry points this binding declares."""
     return sorted(list(_SIGS) + ["bamg_last_error", "bamg_mg_opts_default", "bamg_kernel_launches"])
+
+
+# ---------------------------------------------------------- row-sharded operator
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Halo:
+    """Host-only partition plan of a square block pattern (no GPU needed)."""
+
+    def __init__(self, rowptr, colidx, row_starts):
+        rp, prp = _host(rowptr, np.int32)
+        ci, pci = _host(colidx, np.int32)
+        rs, prs = _host(row_starts, np.int64)
+        self.nparts = len(rs) - 1
+        h = ctypes.c_void_p()
+        st = lib().bamg_halo_create(int(len(rp) - 1), prp, pci, int(self.nparts), prs, ctypes.byref(h))
+        if st != BAMG_OK:
+            raise BamgError(st, "bamg_halo_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().bamg_halo_destroy(self.h)
+            self.h = None
+
+    def info(self, p: int) -> tuple[int, int, int]:
+        n, g, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bamg_halo_part_info(self.h, int(p), ctypes.byref(n), ctypes.byref(g), ctypes.byref(nb)), None)
+        return n.value, g.value, nb.value
+
+    def pattern(self, p: int):
+        """(rowptr, local colidx, global block index of each local block)."""
+        n, _, nb = self.info(p)
+        rp, prp = _host(np.zeros(n + 1), np.int32)
+        ci, pci = _host(np.zeros(nb), np.int32)
+        src, psrc = _host(np.zeros(nb), np.int64)
+        _check(lib().bamg_halo_part_pattern(self.h, int(p), prp, pci, psrc), None)
+        return rp, ci, src
+
+    def ghosts(self, p: int):
+        _, g, _ = self.info(p)
+        gh, pgh = _host(np.zeros(g), np.int64)
+        ow, pow_ = _host(np.zeros(g), np.int32)
+        _check(lib().bamg_halo_part_ghosts(self.h, int(p), pgh, pow_), None)
+        return gh, ow
+
+    def sends(self, src: int, dst: int):
+        cnt = ctypes.c_int64()
+        _check(lib().bamg_halo_sends(self.h, int(src), int(dst), ctypes.byref(cnt), None), None)
+        out, pout = _host(np.zeros(cnt.value), np.int64)
+        _check(lib().bamg_halo_sends(self.h, int(src), int(dst), None, pout), None)
+        return out
+
+
+def bamg_sharded_create(ctx, A, P, row_starts):
+    rs, prs = _host(row_starts, np.int64)
+    sh, Ac = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().bamg_sharded_create(A, P, int(len(rs) - 1), prs, ctypes.byref(sh), ctypes.byref(Ac)), ctx)
+    return sh, Ac
+
+
+def bamg_sharded_spmv(ctx, sh, x, y):
+    _check(lib().bamg_sharded_spmv(sh, _ptr(x), _ptr(y)), ctx)
+
+
+def bamg_sharded_ptap(ctx, sh, A, P, Ac):
+    _check(lib().bamg_sharded_ptap(sh, A, P, Ac), ctx)
+
+
+def bamg_sharded_stats(sh) -> dict:
+    o = bamg_shard_stats()
+    _check(lib().bamg_sharded_stats(sh, ctypes.byref(o)), None)
+    return {k: getattr(o, k) for k, _ in o._fields_}
+
+
+def bamg_sharded_destroy(sh):
+    _check(lib().bamg_sharded_destroy(sh), None)

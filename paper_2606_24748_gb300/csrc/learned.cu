@@ -20,9 +20,7 @@ namespace bamg {
 constexpr int kNF = 8, kNH = 64;
 constexpr int kOffW1 = 0, kOffB1 = kNF * kNH, kOffW2 = kOffB1 + kNH, kOffB2 = kOffW2 + kNH * kNH,
               kOffW3 = kOffB2 + kNH, kOffB3 = kOffW3 + kNH, kNP = kOffB3 + 1;
-constexpr int kBwdRowsPerChunk = 16;
-constexpr int kBwdThreads = 256;
-constexpr int kBwdMaxCtas = 1216;
+constexpr int kBwdMaxCtas = 1216;  // CTAs of the training kernel (one partial-sum slot each)
 
 }  // namespace bamg
 
@@ -34,10 +32,8 @@ struct bamg_mlp {
   float* v = nullptr;
   float* grad = nullptr;
   float* partials = nullptr; // kBwdMaxCtas x (kNP + 1)
-  __nv_bfloat16* h1 = nullptr;
-  __nv_bfloat16* h2 = nullptr;
-  int64_t cap_rows = 0;
   int64_t t = 0;             // Adam step count
+  bool smem_set = false;     // training kernel's shared-memory limit raised
 };
 
 namespace bamg {
@@ -50,169 +46,366 @@ __device__ __forceinline__ float weight_of(float z) {
   return isfinite(w) ? w : 1.0f;  // a non-finite prediction falls back to the plain smoother
 }
 
-// One row per thread; parameters in shared memory.  Optionally keeps the
-// (bfloat16) hidden activations for the backward pass.
-__global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ pbf, const float* __restrict__ X,
-                                                     int64_t n, float* __restrict__ w_out,
-                                                     __nv_bfloat16* __restrict__ h1s, __nv_bfloat16* __restrict__ h2s) {
-  __shared__ float P[kNP];
-  for (int e = threadIdx.x; e < kNP; e += blockDim.x) P[e] = pbf[e];
-  __syncthreads();
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float x[kNF];
-#pragma unroll
-  for (int f = 0; f < kNF; ++f) x[f] = bfr(X[i * kNF + f]);
-  float h1[kNH];
-#pragma unroll
-  for (int j = 0; j < kNH; ++j) {
-    float a = 0.f;
-#pragma unroll
-    for (int f = 0; f < kNF; ++f) a = fmaf(x[f], P[kOffW1 + f * kNH + j], a);
-    a += P[kOffB1 + j];
-    h1[j] = bfr(fmaxf(a, 0.f));
-    if (h1s) h1s[i * kNH + j] = __float2bfloat16_rn(h1[j]);
-  }
-  float z = 0.f;
-  for (int k = 0; k < kNH; ++k) {
-    float a = 0.f;
-#pragma unroll
-    for (int j = 0; j < kNH; ++j) a = fmaf(h1[j], P[kOffW2 + j * kNH + k], a);
-    a += P[kOffB2 + k];
-    const float h = bfr(fmaxf(a, 0.f));
-    if (h2s) h2s[i * kNH + k] = __float2bfloat16_rn(h);
-    z = fmaf(h, P[kOffW3 + k], z);
-  }
-  z += P[kOffB3];
-  w_out[i] = weight_of(z);
+// ------------------------------------------------ tensor-core MLP kernels
+//
+// Both hidden layers run on the tensor cores as warp-level mma.sync
+// m16n8k16 products, BF16 operands and FP32 accumulation.  Fragment layouts
+// (PTX ISA, .bf16), with g = lane / 4 and t = lane % 4:
+//   A 16x16 row-major:  a0 = (g, 2t..2t+1)  a1 = (g+8, 2t..)  a2 = (g, 2t+8..)  a3 = (g+8, 2t+8..)
+//   B 16x8 col-major:   b0 = (2t..2t+1, g)  b1 = (2t+8..2t+9, g)
+//   C 16x8 FP32:        c0, c1 = (g, 2t..2t+1)  c2, c3 = (g+8, 2t..2t+1)
+// The C tiles of output columns 16q .. 16q+15 (n-tiles 2q and 2q+1) are the
+// A fragment of k-tile q of the next product, so a warp's 16 rows go through
+// both layers (and back) without leaving registers.  Layer 1 has K = 8: its A
+// and B fragments are zero-padded to K = 16.
+constexpr int kTcRows = 16;                   // rows of one warp tile
+constexpr int kTcWarps = 4;
+constexpr int kTcChunk = kTcRows * kTcWarps;  // rows of one CTA step
+constexpr int kLd = kNH + 8;                  // padded row of a 64-wide bf16 tile: conflict-free fragment loads
+constexpr int kLdX = 24;                      // x tile: 16 columns (8 features, the ones column, zeros) + padding
+
+// Parameters in shared memory: W2 both ways round (B operand of the forward
+// product and of the backward product), W1, biases and w3 as floats.
+struct __align__(16) TcWeights {
+  __nv_bfloat16 w2t[kNH][kLd];  // w2t[k][j] = W2[j][k]
+  __nv_bfloat16 w2[kNH][kLd];   // w2[j][k]  = W2[j][k]
+  float w1[kNF][kNH];
+  float b1[kNH], b2[kNH], w3[kNH];
+  float b3, pad[3];
+};
+
+struct __align__(16) TcTrainSmem {
+  TcWeights W;
+  __nv_bfloat16 h1[kTcChunk][kLd];   // hidden layer 1 of the chunk's rows
+  __nv_bfloat16 d2[kTcChunk][kLd];   // dL/d(a2)
+  __nv_bfloat16 d1[kTcChunk][kLd];   // dL/d(a1)
+  __nv_bfloat16 x[kTcChunk][kLdX];   // features, then 1 (valid rows), then zeros
+  float red[kTcWarps][2][kNH];       // per-warp column sums (b2, w3 gradients)
+  float red2[kTcWarps][2];           // per-warp b3 gradient and squared error
+};
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // lo in the low half (lower column)
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ void sts32(__nv_bfloat16* p, uint32_t v) { *reinterpret_cast<uint32_t*>(p) = v; }
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Gradient of mean((w - t)^2) over n rows; CTA b handles rows
-// [b * rows_per_cta, ...) in chunks of 16 and writes its partial sums
-// (and the partial squared error at index kNP) to partials[b].
-__global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(const float* __restrict__ pbf,
-                                                              const float* __restrict__ X,
-                                                              const float* __restrict__ tgt, int64_t n,
-                                                              int64_t rows_per_cta,
-                                                              const __nv_bfloat16* __restrict__ h1s,
-                                                              const __nv_bfloat16* __restrict__ h2s,
-                                                              float* __restrict__ partials) {
-  constexpr int R = kBwdRowsPerChunk;
-  __shared__ float W2[kNH * kNH];
-  __shared__ float W3[kNH];
-  __shared__ float xs[R][kNF];
-  __shared__ float h1[R][kNH + 1];
-  __shared__ float h2[R][kNH + 1];
-  __shared__ float d2[R][kNH + 1];
-  __shared__ float d1[R][kNH + 1];
-  __shared__ float dz[R];
-  __shared__ float sq[R];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < kNH * kNH; e += blockDim.x) W2[e] = pbf[kOffW2 + e];
-  for (int e = tid; e < kNH; e += blockDim.x) W3[e] = pbf[kOffW3 + e];
-  const float b3 = pbf[kOffB3];
-  float gW2[16], gW1[2], g64 = 0.f, gb3 = 0.f, loss = 0.f;
+// Four transposed 8x8 bf16 tiles; lane l gives the address of row l % 8 of tile l / 8.
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const __nv_bfloat16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// Parameters (already bf16-exact floats) into shared memory; the caller syncs.
+__device__ void tc_load_weights(TcWeights& W, const float* __restrict__ pbf) {
+  for (int e = threadIdx.x; e < kNH * kNH; e += blockDim.x) {
+    const int j = e / kNH, k = e % kNH;
+    const __nv_bfloat16 v = __float2bfloat16_rn(pbf[kOffW2 + e]);
+    W.w2[j][k] = v;
+    W.w2t[k][j] = v;
+  }
+  for (int e = threadIdx.x; e < kNF * kNH; e += blockDim.x) W.w1[e / kNH][e % kNH] = pbf[kOffW1 + e];
+  for (int e = threadIdx.x; e < kNH; e += blockDim.x) {
+    W.b1[e] = pbf[kOffB1 + e];
+    W.b2[e] = pbf[kOffB2 + e];
+    W.w3[e] = pbf[kOffW3 + e];
+  }
+  if (threadIdx.x == 0) W.b3 = pbf[kOffB3];
+}
+
+// B fragments of layer 1 (n-tile jn, K padded: the second register is zero).
+__device__ __forceinline__ void tc_w1_frags(const TcWeights& W, int g, int t, uint32_t (&w1f)[8]) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) gW2[q] = 0.f;
-  gW1[0] = gW1[1] = 0.f;
-  const int64_t r0 = blockIdx.x * rows_per_cta;
-  const int64_t r1 = (n < r0 + rows_per_cta) ? n : r0 + rows_per_cta;
-  for (int64_t c0 = r0; c0 < r1; c0 += R) {
-    const int m = (int)((r1 - c0 < R) ? (r1 - c0) : R);
-    __syncthreads();
-    for (int e = tid; e < R * kNH; e += blockDim.x) {
-      const int r = e / kNH, j = e % kNH;
-      const bool ok = r < m;
-      h1[r][j] = ok ? __bfloat162float(h1s[(c0 + r) * kNH + j]) : 0.f;
-      h2[r][j] = ok ? __bfloat162float(h2s[(c0 + r) * kNH + j]) : 0.f;
+  for (int jn = 0; jn < 8; ++jn) w1f[jn] = bf2(W.w1[2 * t][8 * jn + g], W.w1[2 * t + 1][8 * jn + g]);
+}
+
+// Forward pass of the warp tile of rows r0 .. r0+15 (rows >= rend read as
+// zero features).  Returns the packed features, layer 1 as A fragments, the
+// bf16-rounded layer 2 in C layout, and z of rows r0+g and r0+g+8 (in every
+// lane of the quad).
+__device__ __forceinline__ void tc_forward(const TcWeights& W, const uint32_t (&w1f)[8], const float* __restrict__ X,
+                                           const int64_t* __restrict__ idx, int64_t r0, int64_t rend, int g, int t,
+                                           uint32_t (&xa)[2], uint32_t (&h1a)[4][4], float (&h2)[8][4],
+                                           float (&z)[2]) {
+  const int64_t ra = r0 + g, rb = r0 + g + 8;
+  float2 xv0 = make_float2(0.f, 0.f), xv1 = make_float2(0.f, 0.f);
+  if (ra < rend) xv0 = *reinterpret_cast<const float2*>(X + (idx ? idx[ra] : ra) * kNF + 2 * t);
+  if (rb < rend) xv1 = *reinterpret_cast<const float2*>(X + (idx ? idx[rb] : rb) * kNF + 2 * t);
+  xa[0] = bf2(xv0.x, xv0.y);
+  xa[1] = bf2(xv1.x, xv1.y);
+  const uint32_t a1[4] = {xa[0], xa[1], 0u, 0u};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int jn = 2 * q + half, c = 8 * jn + 2 * t;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      mma_bf16(acc, a1, w1f[jn], 0u);
+      h1a[q][2 * half] = bf2(fmaxf(acc[0] + W.b1[c], 0.f), fmaxf(acc[1] + W.b1[c + 1], 0.f));
+      h1a[q][2 * half + 1] = bf2(fmaxf(acc[2] + W.b1[c], 0.f), fmaxf(acc[3] + W.b1[c + 1], 0.f));
     }
-    for (int e = tid; e < R * kNF; e += blockDim.x) {
-      const int r = e / kNF, f = e % kNF;
-      xs[r][f] = r < m ? bfr(X[(c0 + r) * kNF + f]) : 0.f;
+  }
+  float za = 0.f, zb = 0.f;
+#pragma unroll
+  for (int jn = 0; jn < 8; ++jn) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      mma_bf16(acc, h1a[q], lds32(&W.w2t[8 * jn + g][16 * q + 2 * t]), lds32(&W.w2t[8 * jn + g][16 * q + 8 + 2 * t]));
+    const int c = 8 * jn + 2 * t;
+    h2[jn][0] = bfr(fmaxf(acc[0] + W.b2[c], 0.f));
+    h2[jn][1] = bfr(fmaxf(acc[1] + W.b2[c + 1], 0.f));
+    h2[jn][2] = bfr(fmaxf(acc[2] + W.b2[c], 0.f));
+    h2[jn][3] = bfr(fmaxf(acc[3] + W.b2[c + 1], 0.f));
+    za = fmaf(h2[jn][0], W.w3[c], fmaf(h2[jn][1], W.w3[c + 1], za));
+    zb = fmaf(h2[jn][2], W.w3[c], fmaf(h2[jn][3], W.w3[c + 1], zb));
+  }
+  za += __shfl_xor_sync(0xffffffffu, za, 1);
+  za += __shfl_xor_sync(0xffffffffu, za, 2);
+  zb += __shfl_xor_sync(0xffffffffu, zb, 1);
+  zb += __shfl_xor_sync(0xffffffffu, zb, 2);
+  z[0] = za + W.b3;
+  z[1] = zb + W.b3;
+}
+
+// Inference: every warp takes 16-row tiles in turn.
+__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_forward_tc(const float* __restrict__ pbf,
+                                                                  const float* __restrict__ X, int64_t n,
+                                                                  float* __restrict__ w_out) {
+  __shared__ TcWeights W;
+  tc_load_weights(W, pbf);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  uint32_t w1f[8];
+  tc_w1_frags(W, g, t, w1f);
+  for (int64_t r0 = ((int64_t)blockIdx.x * kTcWarps + warp) * kTcRows; r0 < n;
+       r0 += (int64_t)gridDim.x * kTcChunk) {
+    uint32_t xa[2], h1a[4][4];
+    float h2[8][4], z[2];
+    tc_forward(W, w1f, X, nullptr, r0, n, g, t, xa, h1a, h2, z);
+    if (t == 0) {
+      if (r0 + g < n) w_out[r0 + g] = weight_of(z[0]);
+      if (r0 + g + 8 < n) w_out[r0 + g + 8] = weight_of(z[1]);
     }
-    __syncthreads();
-    if (tid < R) {
-      float d = 0.f, s2 = 0.f;
-      if (tid < m) {
-        float z = 0.f;
-        for (int k = 0; k < kNH; ++k) z = fmaf(h2[tid][k], W3[k], z);
-        z += b3;
-        const double s = 1.0 / (1.0 + exp(-(double)z));
-        const double e = 0.5 + 1.5 * s - (double)tgt[c0 + tid];
-        d = (float)((2.0 / (double)n) * e * 1.5 * s * (1.0 - s));
-        s2 = (float)(e * e);
+  }
+}
+
+// Training: gradient of mean((w - t)^2) over n rows (row r of the batch is
+// row idx[r] of X and tgt, or row r without idx).  CTA b takes rows
+// [b * rows_per_cta, ...) in chunks of 64 (16 per warp): forward, dz, the
+// backward signal d2 = dz w3 (masked by a2 > 0) and d1 = d2 W2^T (masked by
+// a1 > 0) in registers; then the chunk's weight gradients h1^T d2 and
+// x^T d1 from shared memory (the ones column of x gives the b1 gradient).
+// Per-CTA partial sums go to partials[b] (squared error at index kNP).
+__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_train_tc(const float* __restrict__ pbf,
+                                                                const float* __restrict__ X,
+                                                                const float* __restrict__ tgt,
+                                                                const int64_t* __restrict__ idx, int64_t n,
+                                                                int64_t rows_per_cta, float* __restrict__ w_out,
+                                                                float* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char tc_smem[];
+  TcTrainSmem& S = *reinterpret_cast<TcTrainSmem*>(tc_smem);
+  tc_load_weights(S.W, pbf);
+  __syncthreads();
+  const TcWeights& W = S.W;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const int mi = lane >> 3, mr = lane & 7;  // ldmatrix: tile and row this lane addresses
+  uint32_t w1f[8];
+  tc_w1_frags(W, g, t, w1f);
+  float gW2[8][4], gW1[2][4], gb2[8][2], gw3[8][2], gb3 = 0.f, sq = 0.f;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) gW2[a][b] = 0.f;
+    gb2[a][0] = gb2[a][1] = gw3[a][0] = gw3[a][1] = 0.f;
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) gW1[0][b] = gW1[1][b] = 0.f;
+  const double scale = 2.0 / (double)n;
+  const int64_t rbeg = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t rend = n < rbeg + rows_per_cta ? n : rbeg + rows_per_cta;
+  const int lr = kTcRows * warp;  // the warp's first row in the chunk
+  for (int64_t c0 = rbeg; c0 < rend; c0 += kTcChunk) {
+    const int64_t r0 = c0 + lr;
+    uint32_t xa[2], h1a[4][4];
+    float h2[8][4], z[2];
+    tc_forward(W, w1f, X, idx, r0, rend, g, t, xa, h1a, h2, z);
+    const bool va = r0 + g < rend, vb = r0 + g + 8 < rend;
+    sts32(&S.x[lr + g][2 * t], xa[0]);
+    sts32(&S.x[lr + g + 8][2 * t], xa[1]);
+    sts32(&S.x[lr + g][8 + 2 * t], (t == 0 && va) ? bf2(1.f, 0.f) : 0u);
+    sts32(&S.x[lr + g + 8][8 + 2 * t], (t == 0 && vb) ? bf2(1.f, 0.f) : 0u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sts32(&S.h1[lr + g][16 * q + 2 * t], h1a[q][0]);
+      sts32(&S.h1[lr + g + 8][16 * q + 2 * t], h1a[q][1]);
+      sts32(&S.h1[lr + g][16 * q + 8 + 2 * t], h1a[q][2]);
+      sts32(&S.h1[lr + g + 8][16 * q + 8 + 2 * t], h1a[q][3]);
+    }
+    // dz of rows g and g+8 (the same in the four lanes of a quad)
+    float dz[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t row = r0 + g + 8 * h;
+      dz[h] = 0.f;
+      if (h == 0 ? va : vb) {
+        const double sg = 1.0 / (1.0 + exp(-(double)z[h]));
+        const double e = 0.5 + 1.5 * sg - (double)tgt[idx ? idx[row] : row];
+        dz[h] = (float)(scale * e * 1.5 * sg * (1.0 - sg));
+        if (t == 0) {
+          sq += (float)(e * e);
+          gb3 += dz[h];
+          if (w_out) w_out[row] = weight_of(z[h]);
+        }
       }
-      dz[tid] = d;
-      sq[tid] = s2;
     }
-    __syncthreads();
-    for (int e = tid; e < R * kNH; e += blockDim.x) {
-      const int r = e / kNH, k = e % kNH;
-      d2[r][k] = h2[r][k] > 0.f ? dz[r] * W3[k] : 0.f;
-    }
-    __syncthreads();
-    for (int e = tid; e < R * kNH; e += blockDim.x) {
-      const int r = e / kNH, j = e % kNH;
-      float a = 0.f;
-      if (h1[r][j] > 0.f)
-        for (int k = 0; k < kNH; ++k) a = fmaf(W2[j * kNH + k], d2[r][k], a);
-      d1[r][j] = a;
-    }
-    __syncthreads();
+    // d2 = dz w3 where a2 > 0; column sums for the b2 and w3 gradients
+    uint32_t d2a[4][4];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int e = tid + kBwdThreads * q, j = e / kNH, k = e % kNH;
-      float a = gW2[q];
-      for (int r = 0; r < R; ++r) a = fmaf(h1[r][j], d2[r][k], a);
-      gW2[q] = a;
+    for (int jn = 0; jn < 8; ++jn) {
+      const int c = 8 * jn + 2 * t;
+      const float e0 = h2[jn][0] > 0.f ? dz[0] * W.w3[c] : 0.f;
+      const float e1 = h2[jn][1] > 0.f ? dz[0] * W.w3[c + 1] : 0.f;
+      const float e2 = h2[jn][2] > 0.f ? dz[1] * W.w3[c] : 0.f;
+      const float e3 = h2[jn][3] > 0.f ? dz[1] * W.w3[c + 1] : 0.f;
+      gb2[jn][0] += e0 + e2;
+      gb2[jn][1] += e1 + e3;
+      gw3[jn][0] = fmaf(dz[0], h2[jn][0], fmaf(dz[1], h2[jn][2], gw3[jn][0]));
+      gw3[jn][1] = fmaf(dz[0], h2[jn][1], fmaf(dz[1], h2[jn][3], gw3[jn][1]));
+      d2a[jn >> 1][2 * (jn & 1)] = bf2(e0, e1);
+      d2a[jn >> 1][2 * (jn & 1) + 1] = bf2(e2, e3);
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int e = tid + kBwdThreads * q, f = e / kNH, j = e % kNH;
-      float a = gW1[q];
-      for (int r = 0; r < R; ++r) a = fmaf(xs[r][f], d1[r][j], a);
-      gW1[q] = a;
+    for (int q = 0; q < 4; ++q) {
+      sts32(&S.d2[lr + g][16 * q + 2 * t], d2a[q][0]);
+      sts32(&S.d2[lr + g + 8][16 * q + 2 * t], d2a[q][1]);
+      sts32(&S.d2[lr + g][16 * q + 8 + 2 * t], d2a[q][2]);
+      sts32(&S.d2[lr + g + 8][16 * q + 8 + 2 * t], d2a[q][3]);
     }
-    if (tid < kNH) {
-      for (int r = 0; r < R; ++r) g64 += d1[r][tid];                 // b1
-    } else if (tid < 2 * kNH) {
-      for (int r = 0; r < R; ++r) g64 += d2[r][tid - kNH];           // b2
-    } else if (tid < 3 * kNH) {
-      for (int r = 0; r < R; ++r) g64 = fmaf(dz[r], h2[r][tid - 2 * kNH], g64);  // w3
-    } else if (tid == 3 * kNH) {
-      for (int r = 0; r < R; ++r) gb3 += dz[r];
-    } else if (tid == 3 * kNH + 1) {
-      for (int r = 0; r < R; ++r) loss += sq[r];
+    // d1 = d2 W2^T where a1 > 0
+#pragma unroll
+    for (int jn = 0; jn < 8; ++jn) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        mma_bf16(acc, d2a[q], lds32(&W.w2[8 * jn + g][16 * q + 2 * t]), lds32(&W.w2[8 * jn + g][16 * q + 8 + 2 * t]));
+      const uint32_t ha = h1a[jn >> 1][2 * (jn & 1)], hb = h1a[jn >> 1][2 * (jn & 1) + 1];
+      sts32(&S.d1[lr + g][8 * jn + 2 * t], bf2(bf_lo(ha) > 0.f ? acc[0] : 0.f, bf_hi(ha) > 0.f ? acc[1] : 0.f));
+      sts32(&S.d1[lr + g + 8][8 * jn + 2 * t], bf2(bf_lo(hb) > 0.f ? acc[2] : 0.f, bf_hi(hb) > 0.f ? acc[3] : 0.f));
     }
+    __syncthreads();
+    // weight gradients of the chunk: warp w owns rows 16w .. 16w+15 of the
+    // W2 gradient (h1^T d2) and columns 16w .. 16w+15 of the W1 gradient (x^T d1)
+#pragma unroll
+    for (int s = 0; s < kTcWarps; ++s) {
+      const int rr = kTcRows * s + (mi >> 1) * 8 + mr;  // A tiles: rows of the k-step, columns by tile
+      uint32_t a[4];
+      ldsm_x4_t(a, &S.h1[rr][16 * warp + (mi & 1) * 8]);
+#pragma unroll
+      for (int jp = 0; jp < 4; ++jp) {
+        uint32_t b[4];
+        ldsm_x4_t(b, &S.d2[kTcRows * s + (mi & 1) * 8 + mr][16 * jp + (mi >> 1) * 8]);
+        mma_bf16(gW2[2 * jp], a, b[0], b[1]);
+        mma_bf16(gW2[2 * jp + 1], a, b[2], b[3]);
+      }
+      uint32_t ax[4], bx[4];
+      ldsm_x4_t(ax, &S.x[rr][(mi & 1) * 8]);
+      ldsm_x4_t(bx, &S.d1[kTcRows * s + (mi & 1) * 8 + mr][16 * warp + (mi >> 1) * 8]);
+      mma_bf16(gW1[0], ax, bx[0], bx[1]);
+      mma_bf16(gW1[1], ax, bx[2], bx[3]);
+    }
+    __syncthreads();
   }
   float* out = partials + (int64_t)blockIdx.x * (kNP + 1);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) out[kOffW2 + tid + kBwdThreads * q] = gW2[q];
+  for (int jn = 0; jn < 8; ++jn) {
+    const int j0 = 16 * warp + g, k = 8 * jn + 2 * t;
+    out[kOffW2 + j0 * kNH + k] = gW2[jn][0];
+    out[kOffW2 + j0 * kNH + k + 1] = gW2[jn][1];
+    out[kOffW2 + (j0 + 8) * kNH + k] = gW2[jn][2];
+    out[kOffW2 + (j0 + 8) * kNH + k + 1] = gW2[jn][3];
+  }
 #pragma unroll
-  for (int q = 0; q < 2; ++q) out[kOffW1 + tid + kBwdThreads * q] = gW1[q];
-  if (tid < kNH)
-    out[kOffB1 + tid] = g64;
-  else if (tid < 2 * kNH)
-    out[kOffB2 + tid - kNH] = g64;
-  else if (tid < 3 * kNH)
-    out[kOffW3 + tid - 2 * kNH] = g64;
-  else if (tid == 3 * kNH)
-    out[kOffB3] = gb3;
-  else if (tid == 3 * kNH + 1)
-    out[kNP] = loss;
+  for (int nn = 0; nn < 2; ++nn) {
+    const int j = 16 * warp + 8 * nn + 2 * t;
+    out[kOffW1 + g * kNH + j] = gW1[nn][0];
+    out[kOffW1 + g * kNH + j + 1] = gW1[nn][1];
+    if (g == 0) {  // row 8 of the padded x^T d1: the ones column
+      out[kOffB1 + j] = gW1[nn][2];
+      out[kOffB1 + j + 1] = gW1[nn][3];
+    }
+  }
+  // column sums over the warp's rows (lanes of equal t), then over the warps in order
+#pragma unroll
+  for (int jn = 0; jn < 8; ++jn)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float b2s = gb2[jn][c], w3s = gw3[jn][c];
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        b2s += __shfl_xor_sync(0xffffffffu, b2s, o);
+        w3s += __shfl_xor_sync(0xffffffffu, w3s, o);
+      }
+      if (g == 0) {
+        S.red[warp][0][8 * jn + 2 * t + c] = b2s;
+        S.red[warp][1][8 * jn + 2 * t + c] = w3s;
+      }
+    }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    gb3 += __shfl_xor_sync(0xffffffffu, gb3, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  }
+  if (lane == 0) {
+    S.red2[warp][0] = gb3;
+    S.red2[warp][1] = sq;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNH) {
+    float b2s = 0.f, w3s = 0.f;
+    for (int w = 0; w < kTcWarps; ++w) {
+      b2s += S.red[w][0][threadIdx.x];
+      w3s += S.red[w][1][threadIdx.x];
+    }
+    out[kOffB2 + threadIdx.x] = b2s;
+    out[kOffW3 + threadIdx.x] = w3s;
+  } else if (threadIdx.x == kNH) {
+    float b3s = 0.f, sqs = 0.f;
+    for (int w = 0; w < kTcWarps; ++w) {
+      b3s += S.red2[w][0];
+      sqs += S.red2[w][1];
+    }
+    out[kOffB3] = b3s;
+    out[kNP] = sqs;
+  }
 }
 
 // grad[p] = sum over CTAs of partials[b][p] in CTA order; loss = sum / n.
+// With loss_sum, the batch's summed squared error is also added to it.
 __global__ void k_mlp_reduce(const float* __restrict__ partials, int nb, float* __restrict__ grad,
-                             float* __restrict__ loss_out, int64_t n) {
+                             float* __restrict__ loss_out, int64_t n, double* __restrict__ loss_sum) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p > kNP) return;
   double s = 0.0;
   for (int b = 0; b < nb; ++b) s += (double)partials[(int64_t)b * (kNP + 1) + p];
-  if (p < kNP)
+  if (p < kNP) {
     grad[p] = (float)s;
-  else if (loss_out)
-    *loss_out = (float)(s / (double)n);
+  } else {
+    if (loss_out) *loss_out = (float)(s / (double)n);
+    if (loss_sum) *loss_sum += s;
+  }
 }
 
 // Adam (Kingma and Ba 2015) on the FP32 master copy, then the bfloat16 copy.
@@ -385,34 +578,43 @@ __global__ void k_axpy(int64_t m, const double* __restrict__ z, double* __restri
   if (t < m) x[t] += z[t];
 }
 
-static Status mlp_reserve(bamg_mlp* M, int64_t n) {
-  if (n <= M->cap_rows) return Status{};
-  cudaStream_t st = M->ctx->stream;
-  dfree(M->h1, st);
-  dfree(M->h2, st);
-  BAMG_TRY(dalloc(&M->h1, n * kNH, st));
-  BAMG_TRY(dalloc(&M->h2, n * kNH, st));
-  M->cap_rows = n;
-  return Status{};
-}
-
-static Status mlp_forward(bamg_mlp* M, const float* X, int64_t n, float* w, bool keep, cudaStream_t st) {
+static Status mlp_forward(bamg_mlp* M, const float* X, int64_t n, float* w, cudaStream_t st) {
   if (n <= 0) return Status{};
-  if (keep) BAMG_TRY(mlp_reserve(M, n));
-  { k_mlp_forward<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(M->theta_bf, X, n, w, keep ? M->h1 : nullptr,
-                                                               keep ? M->h2 : nullptr); BAMG_COUNT_LAUNCH; }
+  const int64_t tiles = (n + kTcChunk - 1) / kTcChunk;
+  const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)M->ctx->sm_count * 4));
+  { k_mlp_forward_tc<<<nb, kTcWarps * 32, 0, st>>>(M->theta_bf, X, n, w); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
 
-static Status mlp_gradient(bamg_mlp* M, const float* X, const float* t, int64_t n, float* w_tmp, float* loss,
-                           cudaStream_t st) {
-  BAMG_TRY(mlp_forward(M, X, n, w_tmp, true, st));
-  int64_t per = (n + kBwdMaxCtas - 1) / kBwdMaxCtas;
-  per = ((per + kBwdRowsPerChunk - 1) / kBwdRowsPerChunk) * kBwdRowsPerChunk;
+// Rows per CTA of the training kernel: whole 64-row chunks, at least four
+// of them (each CTA first stages the parameters), at most two CTAs per SM.
+static int64_t train_rows_per_cta(int64_t n, int sm_count) {
+  int64_t per = (n + 2 * sm_count - 1) / (2 * (int64_t)sm_count);
+  per = std::max<int64_t>(per, 4 * kTcChunk);
+  return (per + kTcChunk - 1) / kTcChunk * kTcChunk;
+}
+
+static Status mlp_gradient(bamg_mlp* M, const float* X, const float* t, const int64_t* idx, int64_t n,
+                           float* w_tmp, float* loss, double* loss_sum, cudaStream_t st) {
+  const size_t smem = sizeof(TcTrainSmem);
+  if (!M->smem_set) {
+    BAMG_CUDA(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    M->smem_set = true;
+  }
+  const int64_t per = train_rows_per_cta(n, M->ctx->sm_count);
   const int nb = (int)((n + per - 1) / per);
-  { k_mlp_backward<<<nb, kBwdThreads, 0, st>>>(M->theta_bf, X, t, n, per, M->h1, M->h2, M->partials); BAMG_COUNT_LAUNCH; }
-  { k_mlp_reduce<<<(kNP + 1 + 255) / 256, 256, 0, st>>>(M->partials, nb, M->grad, loss, n); BAMG_COUNT_LAUNCH; }
+  if (nb > kBwdMaxCtas) return make_status(BAMG_ERR_INVALID, "too many rows for one training step");
+  { k_mlp_train_tc<<<nb, kTcWarps * 32, smem, st>>>(M->theta_bf, X, t, idx, n, per, w_tmp, M->partials); BAMG_COUNT_LAUNCH; }
+  { k_mlp_reduce<<<(kNP + 1 + 255) / 256, 256, 0, st>>>(M->partials, nb, M->grad, loss, n, loss_sum); BAMG_COUNT_LAUNCH; }
+  BAMG_CUDA(cudaGetLastError());
+  return Status{};
+}
+
+static Status mlp_adam(bamg_mlp* M, float lr, cudaStream_t st) {
+  M->t++;
+  { k_mlp_adam<<<(kNP + 255) / 256, 256, 0, st>>>(M->theta, M->m, M->v, M->grad, M->theta_bf, lr, 0.9f, 0.999f, 1e-8f,
+                                                  M->t); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaGetLastError());
   return Status{};
 }
@@ -436,7 +638,7 @@ Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st) {
       { k_block_features<6, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, L.dinv, L.n, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
   }
   BAMG_CUDA(cudaGetLastError());
-  return mlp_forward(mg->mlp, L.feat, L.n, L.learned_w, false, st);
+  return mlp_forward(mg->mlp, L.feat, L.n, L.learned_w, st);
 }
 
 }  // namespace bamg
@@ -499,8 +701,6 @@ bamg_status bamg_mlp_destroy(bamg_mlp* M) {
   if (!M) return BAMG_OK;
   cudaStream_t st = M->ctx->stream;
   for (float** p : {&M->theta, &M->theta_bf, &M->m, &M->v, &M->grad, &M->partials}) dfree(*p, st);
-  dfree(M->h1, st);
-  dfree(M->h2, st);
   cudaStreamSynchronize(st);
   delete M;
   return BAMG_OK;
@@ -530,7 +730,7 @@ bamg_status bamg_mlp_set_params(bamg_mlp* M, const float* params) {
 
 bamg_status bamg_mlp_forward(bamg_mlp* M, const float* X, int64_t n, float* w) {
   if (!M || n < 0 || (n > 0 && (!X || !w))) return BAMG_ERR_INVALID;
-  Status s = mlp_forward(M, X, n, w, false, M->ctx->stream);
+  Status s = mlp_forward(M, X, n, w, M->ctx->stream);
   return s.ok() ? BAMG_OK : fail(M->ctx, s);
 }
 
@@ -538,7 +738,7 @@ bamg_status bamg_mlp_gradient(bamg_mlp* M, const float* X, const float* t, int64
                               float* loss) {
   if (!M || n <= 0 || !X || !t || !w_tmp) return BAMG_ERR_INVALID;
   cudaStream_t st = M->ctx->stream;
-  Status s = mlp_gradient(M, X, t, n, w_tmp, loss, st);
+  Status s = mlp_gradient(M, X, t, nullptr, n, w_tmp, loss, nullptr, st);
   if (s.ok() && grad) {
     cudaError_t e = cudaMemcpyAsync(grad, M->grad, sizeof(float) * kNP, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) s = cuda_status(e, "gradient copy");
@@ -550,13 +750,20 @@ bamg_status bamg_mlp_train_step(bamg_mlp* M, const float* X, const float* t, int
                                 float* loss) {
   if (!M || n <= 0 || !X || !t || !w_tmp || !(lr > 0.f)) return BAMG_ERR_INVALID;
   cudaStream_t st = M->ctx->stream;
-  Status s = mlp_gradient(M, X, t, n, w_tmp, loss, st);
-  if (s.ok()) {
-    M->t++;
-    { k_mlp_adam<<<(kNP + 255) / 256, 256, 0, st>>>(M->theta, M->m, M->v, M->grad, M->theta_bf, lr, 0.9f, 0.999f,
-                                                    1e-8f, M->t); BAMG_COUNT_LAUNCH; }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) s = cuda_status(e, "adam");
+  Status s = mlp_gradient(M, X, t, nullptr, n, w_tmp, loss, nullptr, st);
+  if (s.ok()) s = mlp_adam(M, lr, st);
+  return s.ok() ? BAMG_OK : fail(M->ctx, s);
+}
+
+bamg_status bamg_mlp_train_epoch(bamg_mlp* M, const float* X, const float* t, const int64_t* perm, int64_t n,
+                                 int64_t batch, float lr, double* loss_sum) {
+  if (!M || n <= 0 || batch <= 0 || !X || !t || !perm || !(lr > 0.f)) return BAMG_ERR_INVALID;
+  cudaStream_t st = M->ctx->stream;
+  Status s;
+  for (int64_t s0 = 0; s0 < n && s.ok(); s0 += batch) {
+    const int64_t m = std::min(batch, n - s0);
+    s = mlp_gradient(M, X, t, perm + s0, m, nullptr, nullptr, loss_sum, st);
+    if (s.ok()) s = mlp_adam(M, lr, st);
   }
   return s.ok() ? BAMG_OK : fail(M->ctx, s);
 }

@@ -105,23 +105,44 @@ class InclusionProblems:
 
 
 def train(ctx, mlp, X, t, epochs: int = 30, batch: int = 32768, lr: float = 1e-3, seed: int = 0):
-    """Mini-batch Adam on (X, t); returns the loss after every epoch."""
+    """Mini-batch Adam on (X, t), one library call per epoch over a seeded
+    device permutation (rows gathered inside the kernel); returns the mean
+    loss of every epoch."""
     n = X.shape[0]
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    w_tmp = torch.empty(min(batch, n), dtype=torch.float32, device="cuda")
-    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-    hist = []
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    sums = torch.zeros(epochs, dtype=torch.float64, device="cuda")
     for ep in range(epochs):
-        perm = torch.randperm(n, generator=g).cuda()
-        tot, cnt = 0.0, 0
-        for s in range(0, n, batch):
-            idx = perm[s:s + batch]
-            Xb, tb = X[idx].contiguous(), t[idx].contiguous()
-            B.bamg_mlp_train_step(ctx, mlp, Xb, tb, w_tmp, lr, loss)
-            tot += float(loss.item()) * idx.numel()
-            cnt += idx.numel()
-        hist.append(tot / cnt)
-    return hist
+        perm = torch.randperm(n, generator=g, device="cuda")
+        B.bamg_mlp_train_epoch(ctx, mlp, X, t, perm, batch, lr, sums[ep:ep + 1])
+    return [float(v) / n for v in sums.cpu()]
+
+
+def train_step_rate(ctx, mlp, n: int = 1 << 20, reps: int = 20, seed: int = 0) -> dict:
+    """Rows per second of one training step (fused forward + backward on the
+    tensor cores, gradient reduction, Adam) on n seeded N(0,1) feature rows,
+    CUDA events on the current stream; the parameters are restored after."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    X = torch.randn((n, 8), generator=gen).cuda()
+    t = (0.5 + 1.5 * torch.rand(n, generator=gen)).cuda()
+    w = torch.empty(n, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    saved = torch.empty(B.bamg_mlp_num_params(), dtype=torch.float32, device="cuda")
+    B.bamg_mlp_get_params(ctx, mlp, saved)
+    for _ in range(3):
+        B.bamg_mlp_train_step(ctx, mlp, X, t, w, 1e-6, loss)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        B.bamg_mlp_train_step(ctx, mlp, X, t, w, 1e-6, loss)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    B.bamg_mlp_set_params(ctx, mlp, saved)
+    # multiply-adds per row: 8x64 + 64x64 + 64 forward, 64x64 for d1, 64x64 + 8x64 + 3x64 for the gradients
+    flop_row = 2 * (8 * 64 + 64 * 64 + 64) + 2 * 64 * 64 + 2 * (64 * 64 + 8 * 64 + 3 * 64)
+    return {"rows": n, "ms_per_step": round(ms, 4), "rows_per_s": round(n / ms * 1e3, 1),
+            "tflops": round(flop_row * n / ms / 1e9, 3), "flop_per_row": flop_row}
 
 
 def mse(ctx, mlp, X, t) -> float:
@@ -150,6 +171,7 @@ def run(ne: int = 48, n_train: int = 200, n_test: int = 50, epochs: int = 30, se
     t_train = time.perf_counter() - t1
     log(f"training set {X.shape[0]} rows from {n_train} instances in {t_data:.1f} s; "
         f"{epochs} epochs in {t_train:.2f} s, loss {hist[0]:.4f} -> {hist[-1]:.4f}")
+    rate = train_step_rate(ctx, mlp)
     var = float(torch.mean((t - t.mean()) ** 2).item())
     res = []
     for k in range(n_test):
@@ -169,6 +191,7 @@ def run(ne: int = 48, n_train: int = 200, n_test: int = 50, epochs: int = 30, se
     out = {
         "ne": ne, "train_instances": n_train, "test_instances": n_test, "train_rows": int(X.shape[0]),
         "epochs": epochs, "train_seconds": round(t_train, 3), "data_seconds": round(t_data, 1),
+        "train_rows_per_s": round(X.shape[0] * epochs / t_train, 1), "train_step_kernels": rate,
         "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "target_variance": var,
         "test_mse": float(np.mean([r["mse"] for r in res])),
         "rho_plain": agg("plain", "rho"), "rho_learned": agg("learned", "rho"),

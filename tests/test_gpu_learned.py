@@ -42,7 +42,11 @@ def test_block_features_match_oracle():
         gp.close()
 
 
-def test_mlp_forward_gradient_and_adam_match_oracle(ctx):
+@pytest.mark.parametrize("N", [3000, 100003])
+def test_mlp_forward_gradient_and_adam_match_oracle(ctx, N):
+    """Tensor-core forward and fused backward (BF16 operands, FP32
+    accumulation) against the oracle's BF16-emulating MLP; 3,000 rows fill a
+    dozen CTAs with a ragged last chunk, 100,003 rows every CTA slot."""
     n = B.bamg_mlp_num_params()
     assert n == OL.N_PARAMS
     mlp = B.bamg_mlp_create(ctx, 7)
@@ -50,7 +54,6 @@ def test_mlp_forward_gradient_and_adam_match_oracle(ctx):
         rng = np.random.default_rng(3)
         theta = (rng.standard_normal(n) * 0.3).astype(np.float32)
         B.bamg_mlp_set_params(ctx, mlp, torch.from_numpy(theta).cuda())
-        N = 3000
         X = rng.standard_normal((N, 8)).astype(np.float32)
         t = rng.uniform(0.5, 2.0, N).astype(np.float32)
         Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
@@ -205,3 +208,35 @@ def test_numeric_resetup_equals_a_fresh_setup():
     finally:
         fresh.close()
         reuse.close()
+
+
+def test_train_epoch_equals_train_steps_on_gathered_batches(ctx):
+    """bamg_mlp_train_epoch gathers each batch's rows through the permutation
+    inside the kernel; it must give bit for bit the parameters (and the loss)
+    of bamg_mlp_train_step on the same batches gathered beforehand."""
+    rng = np.random.default_rng(12)
+    n, batch = 10000, 3000                          # three full batches and a ragged one
+    X = torch.from_numpy(rng.standard_normal((n, 8)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.uniform(0.5, 2.0, n).astype(np.float32)).cuda()
+    perm = torch.from_numpy(rng.permutation(n)).cuda()
+    a = B.bamg_mlp_create(ctx, 5)
+    b = B.bamg_mlp_create(ctx, 5)
+    try:
+        loss_sum = torch.zeros(1, dtype=torch.float64, device="cuda")
+        B.bamg_mlp_train_epoch(ctx, a, X, t, perm, batch, 1e-3, loss_sum)
+        w = torch.empty(batch, dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        tot = 0.0
+        for s in range(0, n, batch):
+            idx = perm[s:s + batch]
+            B.bamg_mlp_train_step(ctx, b, X[idx].contiguous(), t[idx].contiguous(), w, 1e-3, loss)
+            tot += float(loss.item()) * idx.numel()
+        pa = torch.empty(OL.N_PARAMS, dtype=torch.float32, device="cuda")
+        pb = torch.empty_like(pa)
+        B.bamg_mlp_get_params(ctx, a, pa)
+        B.bamg_mlp_get_params(ctx, b, pb)
+        assert torch.equal(pa, pb)
+        assert float(loss_sum.item()) == pytest.approx(tot, rel=1e-6)
+    finally:
+        B.bamg_mlp_destroy(a)
+        B.bamg_mlp_destroy(b)
