@@ -395,6 +395,7 @@ def run_ours(args):
     result["ptap_reuse"] = ptap_reuse(wl, torch, B)
     result["aggregation_graph"] = aggregation_graph(wl, torch, B)
     result["assembly"] = assembly_compare(wl, torch, B)
+    result["sharded"] = sharded_compare(wl, torch, B)
     if not args.no_e2e:
         result["e2e"] = e2e(wl, torch, B, dist, K, W, world, per_step)
     if not args.no_multi and args.precision == "fp64" and rank == 0 and world == 1:
@@ -530,6 +531,46 @@ def ptap_reuse(wl, torch, B):
     return {"level": 0, "symbolic_plus_numeric_ms": round(both, 2), "numeric_ms": round(num, 3),
             "ratio": round(both / num, 1),
             "timing": "symbolic + first numeric: host clock around synchronised calls; numeric: CUDA events, median of 5"}
+
+
+def sharded_compare(wl, torch, B, nparts=4):
+    """The finest level as a row-sharded operator of `nparts` contiguous parts
+    run in turn on this GPU: SpMV and numeric Galerkin product through the
+    parts (halo gathers, cached P_oth, per-part products, reduce) against the
+    unsharded kernels, CUDA events, median of 5, and the partition's
+    communication profile (what a multi-GPU run would move)."""
+    A0, P0 = B.bamg_mg_get_level(wl.mg, 0)
+    n = B.bamg_bsr_info(A0)["nbr"]
+    starts = np.array([round(k * n / nparts) for k in range(nparts + 1)], dtype=np.int64)
+    t0 = time.perf_counter()
+    sh, Ac = B.bamg_sharded_create(wl.ctx, A0, P0, starts)
+    build_s = time.perf_counter() - t0
+    plan, Ac1 = B.bamg_ptap_symbolic(wl.ctx, A0, P0)
+    x = torch.randn(n * 3, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    try:
+        B.bamg_sharded_ptap(wl.ctx, sh, A0, P0, Ac)
+        B.bamg_ptap_numeric(wl.ctx, plan, A0, P0, Ac1)
+
+        def med(fn):
+            return sorted(event_ms(torch, fn, 1) for _ in range(5))[2]
+        out = {"parts": nparts, "build_s": round(build_s, 2),
+               "spmv_ms": round(med(lambda: B.bamg_sharded_spmv(wl.ctx, sh, x, y)), 4),
+               "spmv_unsharded_ms": round(med(lambda: B.bamg_bsr_spmv(wl.ctx, A0, x, y)), 4),
+               "ptap_ms": round(med(lambda: B.bamg_sharded_ptap(wl.ctx, sh, A0, P0, Ac)), 4),
+               "ptap_unsharded_ms": round(med(lambda: B.bamg_ptap_numeric(wl.ctx, plan, A0, P0, Ac1)), 4)}
+        v1 = torch.empty(B.bamg_bsr_info(Ac)["nnzb"] * 36, dtype=torch.float64, device="cuda")
+        v2 = torch.empty_like(v1)
+        B.bamg_bsr_get_values(wl.ctx, Ac, v1)
+        B.bamg_bsr_get_values(wl.ctx, Ac1, v2)
+        out["ptap_rel_diff"] = float(torch.linalg.norm(v1 - v2) / torch.linalg.norm(v2))
+        out.update(B.bamg_sharded_stats(sh))
+        return out
+    finally:
+        B.bamg_ptap_destroy(plan)
+        B.bamg_bsr_destroy(Ac1)
+        B.bamg_sharded_destroy(sh)
+        B.bamg_bsr_destroy(Ac)
 
 
 def assembly_compare(wl, torch, B):
