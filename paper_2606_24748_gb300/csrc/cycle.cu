@@ -281,13 +281,19 @@ LevelPtrs<double> level_ptrs<double>(Level& L) { return ptrs64(L); }
 template <>
 LevelPtrs<float> level_ptrs<float>(Level& L) { return ptrs32(L); }
 
+// CTA size of the fused Chebyshev row kernels.  A level's rows fill about one
+// wave of the GPU at the workload sizes (64^3: 8,582 slices for 152 SMs x 64
+// warps), so the last CTA of the busier SMs is the kernel's tail: 64-thread
+// CTAs (two slices) halve it against 128-thread ones.
+constexpr int kChebThreads = 64;
+
 template <int BS, typename T>
 static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
   const int64_t rows = row_threads_for<T>(A);
-  const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
+  const unsigned gr = (unsigned)((rows + kChebThreads - 1) / kChebThreads);
   const unsigned gn = (unsigned)((L.n + kRowThreads - 1) / kRowThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
@@ -305,7 +311,7 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
             k + 1 < m ? 1 : 0, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
                                                      k + 1 < m ? 1 : 0, done)); BAMG_COUNT_LAUNCH; })
     }
@@ -322,7 +328,7 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
   const int64_t rows = row_threads_for<T>(A);
-  const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
+  const unsigned gr = (unsigned)((rows + kChebThreads - 1) / kChebThreads);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
   const int split = BS == 6 ? split_for<T>(A) : 0;
@@ -335,7 +341,7 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
                                                                  p.r, p.d0, p.dinv, L.weights, sc, done));
       BAMG_COUNT_LAUNCH; })
   } else {
-    BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_rinit<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+    BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_rinit<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
                                                     p.d0, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; })
   }
   prof_end(mg->ctx, pr, st);
@@ -349,7 +355,7 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
                                                                   1, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kRowThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done)); BAMG_COUNT_LAUNCH; })
     }
     prof_end(mg->ctx, pm, st);
