@@ -384,7 +384,14 @@ typedef struct {
                                half-bandwidth splits it into >= 3 chunks, else
                                dense; 1 = always dense; 2 = banded whenever
                                it splits into >= 2 chunks */
+  int aggregation;          /* BAMG_AGG_GEOMETRIC (default): 3x3x3 node cubes
+                               on opts.grid; BAMG_AGG_MIS: on every level, MIS
+                               aggregates of the block strength graph (see
+                               bamg_mg_setup) */
+  double mis_eps;           /* strength threshold eps of BAMG_AGG_MIS (0.08) */
+  uint64_t mis_seed;        /* vertex-weight seed of level l: mis_seed + l (1) */
 } bamg_mg_opts;
+typedef enum { BAMG_AGG_GEOMETRIC = 0, BAMG_AGG_MIS = 1 } bamg_aggregation;
 
 typedef struct {
   int iterations;     /* CG iterations taken */
@@ -400,6 +407,14 @@ BAMG_API void bamg_mg_opts_default(bamg_mg_opts* opts);
  * blocks); coords (host, nbr x 3 doubles) and dirichlet (host, nbr bytes,
  * 1 = clamped node) give the rigid-body near-null space.  Aggregates are
  * cubes of 3x3x3 nodes of opts->grid (a remainder joins the last aggregate),
+ * or, with opts->aggregation = BAMG_AGG_MIS (Sec. 3.2, Sec. 6), on every level
+ * the device MIS aggregates of the block strength graph (bamg_strength_graph
+ * with opts->mis_eps, bamg_mis_aggregate with seed mis_seed + level), where a
+ * vertex without strong neighbours (a clamped node) joins no aggregate (its
+ * prolongator row is empty) and an aggregate whose near-null block is rank
+ * deficient (fewer than three non-collinear fine nodes) is dissolved, each of
+ * its vertices joining the surviving aggregate of a strong neighbour whose
+ * root has the largest (weight, root), survivors renumbered in root order;
  * the tentative prolongator is the per-aggregate QR of the rigid-body modes,
  * the prolongator is smoothed by one damped-Jacobi step with
  * omega = 4 / (3 lambda_max(D^-1 A)), coarse operators are Galerkin
@@ -471,6 +486,10 @@ BAMG_API bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** 
 /* The cached restriction R = P^T of a level (NULL on the coarsest level);
  * owned by the hierarchy, refreshed when P changes. */
 BAMG_API bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R);
+/* Aggregate of every block row of a non-coarsest level (the column of its
+ * tentative-prolongator block), -1 for a row in no aggregate: nbr ints
+ * into a caller-owned device array, on the context's stream. */
+BAMG_API bamg_status bamg_mg_get_aggregates(const bamg_mg* mg, int level, int32_t* agg);
 /* State gate (Sec. 3.5): how many times the level's prolongator-side caches
  * were rebuilt since setup: the block-ordered copy of P inside the level's
  * Galerkin plan (*p_refreshes) and R = P^T (*r_refreshes).  Both are

@@ -60,14 +60,32 @@ class Hierarchy:
 
 def setup(A: BlockMatrix, coords: np.ndarray, dirichlet: np.ndarray,
           grid: tuple[int, int, int], max_coarse_dofs: int = MAX_COARSE_DOFS,
-          max_levels: int = 10, degree: int = 2) -> Hierarchy:
+          max_levels: int = 10, degree: int = 2, aggregation: str = "geometric",
+          eps: float = 0.08, seed: int = 1) -> Hierarchy:
+    """aggregation: "geometric" (3x3x3 node cubes on the structured grid) or
+    "mis" (MIS aggregates of each level's block strength graph, Sec. 3.2 and
+    Sec. 6, with the readings of strength.hierarchy_aggregates; seed + level
+    seeds the vertex weights of level l)."""
     levels = [Level(A=A, grid=grid)]
     Bn = None
     while (levels[-1].A.nbr * levels[-1].A.bs_r > max_coarse_dofs
            and len(levels) < max_levels):
         L = levels[-1]
-        agg, cgrid = aggregates(L.grid)
-        n_agg = int(np.prod(cgrid))
+        if aggregation == "mis":
+            from .strength import hierarchy_aggregates
+            l = len(levels) - 1
+            if Bn is None:
+                def near_null(m):  # rigid-body rows of the members about their centroid
+                    sub = rigid_body_modes(coords[m], np.zeros(len(m), dtype=np.int64), 1, dirichlet[m])
+                    return sub.reshape(-1, 6)
+            else:
+                Bprev = Bn
+                near_null = lambda m: Bprev[m].reshape(-1, 6)  # noqa: E731
+            agg, n_agg = hierarchy_aggregates(L.A, eps, seed + l, near_null)
+            cgrid = None
+        else:
+            agg, cgrid = aggregates(L.grid)
+            n_agg = int(np.prod(cgrid))
         if Bn is None:
             Bn = rigid_body_modes(coords, agg, n_agg, dirichlet)
         Pt, Bc = tentative_prolongator(Bn, agg, n_agg)

@@ -28,11 +28,14 @@ OMEGA_NUMERATOR = 4.0 / 3.0
 
 def rigid_body_modes(coords: np.ndarray, agg: np.ndarray, n_agg: int,
                      dirichlet: np.ndarray) -> np.ndarray:
-    """(n_nodes, 3, 6) rigid-body blocks centred on each aggregate's centroid."""
-    counts = np.bincount(agg, minlength=n_agg).astype(np.float64)
-    cen = np.stack([np.bincount(agg, weights=coords[:, d], minlength=n_agg) for d in range(3)], 1)
-    cen /= counts[:, None]
-    rel = coords - cen[agg]
+    """(n_nodes, 3, 6) rigid-body blocks centred on each aggregate's centroid
+    (nodes outside every aggregate, agg = -1, get zero blocks)."""
+    inside = agg >= 0
+    a = np.where(inside, agg, 0)
+    counts = np.bincount(agg[inside], minlength=n_agg).astype(np.float64)
+    cen = np.stack([np.bincount(agg[inside], weights=coords[inside, d], minlength=n_agg) for d in range(3)], 1)
+    cen /= np.maximum(counts, 1.0)[:, None]
+    rel = coords - cen[a]
     x, y, z = rel[:, 0], rel[:, 1], rel[:, 2]
     B = np.zeros((coords.shape[0], 3, 6))
     B[:, 0, 0] = B[:, 1, 1] = B[:, 2, 2] = 1.0
@@ -40,15 +43,18 @@ def rigid_body_modes(coords: np.ndarray, agg: np.ndarray, n_agg: int,
     B[:, 1, 4], B[:, 2, 4] = -z, y
     B[:, 0, 5], B[:, 2, 5] = z, -x
     B[np.asarray(dirichlet).astype(bool)] = 0.0
+    B[~inside] = 0.0
     return B
 
 
 def tentative_prolongator(Bn: np.ndarray, agg: np.ndarray, n_agg: int) -> tuple[BlockMatrix, np.ndarray]:
-    """P~ (one bs x 6 block per node, column = its aggregate) and coarse blocks R."""
+    """P~ (one bs x 6 block per aggregated node, column = its aggregate; no
+    block for a node outside every aggregate, agg = -1) and coarse blocks R."""
     n_nodes, bs, k = Bn.shape
     Q_nodes = np.zeros((n_nodes, bs, k))
     Bc = np.zeros((n_agg, k, k))
     order = np.argsort(agg, kind="stable")
+    order = order[agg[order] >= 0]
     starts = np.searchsorted(agg[order], np.arange(n_agg + 1))
     for a in range(n_agg):
         nodes = order[starts[a]:starts[a + 1]]
@@ -65,8 +71,10 @@ def tentative_prolongator(Bn: np.ndarray, agg: np.ndarray, n_agg: int) -> tuple[
         Q[zero_rows] = 0.0
         Q_nodes[nodes] = Q.reshape(-1, bs, k)
         Bc[a] = R
-    rowptr = np.arange(n_nodes + 1, dtype=np.int64)
-    P = BlockMatrix(n_nodes, n_agg, bs, k, rowptr, agg.astype(np.int64), Q_nodes)
+    inside = agg >= 0
+    rowptr = np.zeros(n_nodes + 1, dtype=np.int64)
+    np.cumsum(inside, out=rowptr[1:])
+    P = BlockMatrix(n_nodes, n_agg, bs, k, rowptr, agg[inside].astype(np.int64), Q_nodes[inside])
     return P, Bc
 
 

@@ -137,3 +137,57 @@ def mis_aggregates(rowptr: np.ndarray, col: np.ndarray, w: np.ndarray, in_set: n
             raise ValueError(f"vertex {i} has no neighbour in the set: the set is not maximal")
         agg[i] = root_id[best]
     return agg
+
+
+def _rank_ok(Bagg: np.ndarray) -> bool:
+    """Full column rank by the QR test the tentative prolongator applies."""
+    if Bagg.shape[0] < Bagg.shape[1]:
+        return False
+    R = np.linalg.qr(Bagg, mode="r")
+    d = np.abs(np.diag(R))
+    return bool(d.min() >= 1e-12 * d.max())
+
+
+def hierarchy_aggregates(A: BlockMatrix, eps: float, seed: int, near_null) -> tuple[np.ndarray, int]:
+    """Aggregates of one level of the MIS-driven hierarchy (readings of Sec. 3.2
+    and Sec. 6 where the paper is silent):
+
+    1. MIS aggregates of the strength graph with weights splitmix64(i, seed).
+    2. A vertex with no strong neighbour (a clamped node, or one decoupled by
+       eps) is left out of every aggregate (-1): its prolongator row is empty.
+    3. An aggregate whose near-null block (its members' rows, in vertex order,
+       centred on the members' centroid at the fine level) is rank deficient
+       is dissolved: each of its vertices joins, among the surviving
+       aggregates of its strong neighbours, the one whose root has the largest
+       (weight, root); a vertex with no such neighbour is left out.
+    4. The surviving aggregates are renumbered in root order.
+
+    near_null(members) returns the stacked near-null rows of those vertices.
+    Returns (aggregate of every vertex or -1, number of aggregates)."""
+    rowptr, col = strength_graph(A, eps)
+    w = weights(A.nbr, seed)
+    in_set = mis_greedy(rowptr, col, w)
+    agg = mis_aggregates(rowptr, col, w, in_set)
+    roots = np.flatnonzero(in_set)
+    deg = np.diff(rowptr)
+    agg[deg == 0] = -1
+    n_agg = roots.size
+    members = [[] for _ in range(n_agg)]
+    for v in range(A.nbr):
+        if agg[v] >= 0:
+            members[agg[v]].append(v)
+    dissolved = np.array([len(m) > 0 and not _rank_ok(near_null(np.array(m))) for m in members], dtype=bool)
+    out = agg.copy()
+    for v in range(A.nbr):
+        if agg[v] < 0 or not dissolved[agg[v]]:
+            continue
+        best = -1
+        for j in col[rowptr[v]:rowptr[v + 1]]:
+            a = agg[j]
+            if a >= 0 and not dissolved[a] and (best < 0 or _key(w, roots[a]) > _key(w, roots[best])):
+                best = a
+        out[v] = best
+    keep = np.array([len(m) > 0 and not d for m, d in zip(members, dissolved)], dtype=bool)
+    renum = np.cumsum(keep) - 1
+    out = np.where(out >= 0, renum[np.maximum(out, 0)], -1)
+    return out.astype(np.int64), int(keep.sum())

@@ -25,6 +25,8 @@ STATUS_NAMES = {0: "BAMG_OK", 1: "BAMG_ERR_INVALID", 2: "BAMG_ERR_OOM", 3: "BAMG
  BAMG_ERR_NOT_CONVERGED, BAMG_ERR_TIMEOUT) = range(1, 9)
 BAMG_FP64 = 0
 BAMG_FP32 = 1
+BAMG_AGG_GEOMETRIC = 0
+BAMG_AGG_MIS = 1
 BAMG_NORM_FROBENIUS = 0
 BAMG_NORM_INFINITY = 1
 PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
@@ -43,7 +45,8 @@ class bamg_mg_opts(ctypes.Structure):
                 ("grid", ctypes.c_int * 3), ("cheb_degree", ctypes.c_int),
                 ("cheb_lower", ctypes.c_double), ("cheb_upper", ctypes.c_double),
                 ("power_its", ctypes.c_int), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("coarse_solver", ctypes.c_int)]
+                ("coarse_solver", ctypes.c_int), ("aggregation", ctypes.c_int), ("mis_eps", ctypes.c_double),
+                ("mis_seed", ctypes.c_uint64)]
 
 
 class bamg_shard_stats(ctypes.Structure):
@@ -78,6 +81,7 @@ _SIGS = {
     "bamg_sharded_destroy": [_P],
     "bamg_mlp_train_epoch": [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, _P],
     "bamg_ctx_set_wait_limit": [_P, _I64],
+    "bamg_mg_get_aggregates": [_P, ctypes.c_int, _P],
     "bamg_mg_get_gate_counts": [_P, ctypes.c_int, _P, _P],
     "bamg_ptap_get_refreshes": [_P, _P],
     "bamg_ctx_profile": [_P, ctypes.c_int],
@@ -230,6 +234,11 @@ def bamg_device_memory(ctx, reset_peak: bool = False) -> tuple[int, int]:
 
 def bamg_kernel_launches() -> int:
     return int(lib().bamg_kernel_launches())
+
+
+def bamg_mg_get_aggregates(ctx, mg, level: int, out):
+    """Aggregate of every block row of a level (-1: in none) into a device int32 tensor."""
+    _check(lib().bamg_mg_get_aggregates(mg, int(level), _ptr(out)), ctx)
 
 
 def bamg_ctx_set_wait_limit(ctx, polls: int):

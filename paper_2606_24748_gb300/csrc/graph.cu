@@ -144,6 +144,13 @@ __global__ void k_mis_exclude(int64_t n, const int* __restrict__ rp, const int* 
   atomicAdd(undecided, 1u);
 }
 
+// root_vertex[a] = the set vertex numbered a
+__global__ void k_root_vertex(int64_t n, const int8_t* __restrict__ st, const int* __restrict__ root_id,
+                              int* __restrict__ root_vertex) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && st[i] == kIn) root_vertex[root_id[i]] = (int)i;
+}
+
 __global__ void k_root_flags(int64_t n, const int8_t* __restrict__ st, int* __restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) flag[i] = st[i] == kIn ? 1 : 0;
@@ -205,7 +212,7 @@ static Status block_sumsq_all(const bamg_bsr* A, double* out, cudaStream_t st) {
   return Status{};
 }
 
-static Status strength_graph(bamg_bsr* A, double eps, int* grow, int* gcol, int64_t cap, int64_t* nedges) {
+Status strength_graph(bamg_bsr* A, double eps, int* grow, int* gcol, int64_t cap, int64_t* nedges) {
   if (!A->has_pattern) return make_status(BAMG_ERR_STATE, "the matrix has no pattern");
   if (A->br != A->bc || A->nbr != A->nbc) return make_status(BAMG_ERR_INVALID, "the strength graph needs a square operator");
   if (!(eps >= 0.0)) return make_status(BAMG_ERR_INVALID, "eps must be >= 0");
@@ -243,8 +250,9 @@ static Status strength_graph(bamg_bsr* A, double eps, int* grow, int* gcol, int6
   return s;
 }
 
-static Status mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rp, const int* col, uint64_t seed, int* agg,
-                            int64_t* n_agg, int* rounds) {
+// root_vertex (device, optional, capacity n): the root vertex of every aggregate.
+Status mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rp, const int* col, uint64_t seed, int* agg,
+                     int64_t* n_agg, int* rounds, int* root_vertex) {
   if (n < 0 || n > INT_MAX - 1) return make_status(BAMG_ERR_INVALID, "vertex count out of range");
   cudaStream_t st = ctx->stream;
   int8_t* state = nullptr;
@@ -280,6 +288,10 @@ static Status mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rp, const int* 
     if (s.ok()) {
       k_mis_assign<<<grid_of(n), 256, 0, st>>>(n, rp, col, (unsigned long long)seed, state, root_id, agg, ctx->d_err);
       BAMG_COUNT_LAUNCH;
+      if (root_vertex) {
+        k_root_vertex<<<grid_of(n), 256, 0, st>>>(n, state, root_id, root_vertex);
+        BAMG_COUNT_LAUNCH;
+      }
       if (cudaMemcpyAsync(&roots, root_id + n, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         s = make_status(BAMG_ERR_CUDA, "root count");
     }
@@ -374,7 +386,7 @@ bamg_status bamg_strength_graph(bamg_bsr* A, double eps, int* rowptr, int* col, 
 bamg_status bamg_mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rowptr, const int* col, uint64_t seed, int* agg,
                                int64_t* n_agg, int* rounds) {
   if (!ctx || n < 0 || (n > 0 && (!rowptr || !agg))) return BAMG_ERR_INVALID;
-  Status s = mis_aggregate(ctx, n, rowptr, col, seed, agg, n_agg, rounds);
+  Status s = mis_aggregate(ctx, n, rowptr, col, seed, agg, n_agg, rounds, nullptr);
   return s.ok() ? BAMG_OK : fail(ctx, s);
 }
 

@@ -396,7 +396,13 @@ Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st);  // features -> 
 Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st);  // FP64 pre-smoothing of level l (b -> x, r)
 Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st);     // levels[l+1].b = R_l r_l
 Status mg_precond(bamg_mg* mg, const double* r, double* z, cudaStream_t st);  // one V-cycle
-Status mg_tune_smoothers(bamg_mg* mg);  // warps per component of the coarse smoothers, by timing them
+Status mg_tune_smoothers(bamg_mg* mg);
+// Block strength graph (see bamg_strength_graph) into device rowptr / col.
+Status strength_graph(bamg_bsr* A, double eps, int* rowptr, int* col, int64_t cap, int64_t* nedges);
+// Device MIS aggregation of a CSR graph (see bamg_mis_aggregate); root_vertex
+// (device, optional) receives the root vertex of every aggregate.
+Status mis_aggregate(bamg_ctx* ctx, int64_t n, const int* rp, const int* col, uint64_t seed, int* agg,
+                     int64_t* n_agg, int* rounds, int* root_vertex);  // warps per component of the coarse smoothers, by timing them
 // The phases of one PCG solve on stream st (the batch solver captures them):
 // setup, r = b, z = M r, p = z; one iteration (every kernel returns at once
 // when the solve is done); x = the iterate, ||b - A x||^2 into *true_r2.

@@ -33,19 +33,21 @@ static void aggregates(const int grid[3], std::vector<int>& agg, int cgrid[3]) {
 
 // Rigid-body modes of fine nodes relative to their aggregate's centroid:
 // columns translations x, y, z, then rotations (-y, x, 0), (0, -z, y), (z, 0, -x);
-// clamped nodes get zero rows.  Layout: node-major 3 x 6 row-major.
+// clamped nodes and nodes outside every aggregate (agg -1) get zero rows.
+// Layout: node-major 3 x 6 row-major.
 static std::vector<double> rigid_modes(const double* coords, const uint8_t* dir, const std::vector<int>& agg,
                                        int64_t nagg) {
   const int64_t n = (int64_t)agg.size();
   std::vector<double> cen(nagg * 3, 0.0), cnt(nagg, 0.0), B(n * 18, 0.0);
   for (int64_t v = 0; v < n; ++v) {
+    if (agg[v] < 0) continue;
     for (int d = 0; d < 3; ++d) cen[agg[v] * 3 + d] += coords[v * 3 + d];
     cnt[agg[v]] += 1.0;
   }
   for (int64_t a = 0; a < nagg; ++a)
-    for (int d = 0; d < 3; ++d) cen[a * 3 + d] /= cnt[a];
+    for (int d = 0; d < 3; ++d) cen[a * 3 + d] /= std::max(cnt[a], 1.0);
   for (int64_t v = 0; v < n; ++v) {
-    if (dir && dir[v]) continue;
+    if ((dir && dir[v]) || agg[v] < 0) continue;
     const double x = coords[v * 3] - cen[agg[v] * 3], y = coords[v * 3 + 1] - cen[agg[v] * 3 + 1],
                  z = coords[v * 3 + 2] - cen[agg[v] * 3 + 2];
     double* b = &B[v * 18];
@@ -108,6 +110,48 @@ static bool thin_qr(int m, const double* Bm, double* Q, double* R) {
   }
   std::copy(q.begin(), q.end(), Q);
   return true;
+}
+
+static uint64_t splitmix64_host(uint64_t d, uint64_t seed) {
+  uint64_t z = seed + (d + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Stacked near-null rows of the vertices `mem` of level l: at the fine level
+// the rigid-body modes about the vertices' centroid (clamped nodes zero), on
+// coarse levels the vertices' 6 x 6 blocks of B.  True if they have full
+// column rank (the thin QR of the tentative prolongator succeeds).
+static bool near_null_full_rank(int l, const std::vector<int>& mem, const double* coords, const uint8_t* dir,
+                                const std::vector<double>& B) {
+  const int bs = l == 0 ? 3 : 6;
+  const int m = (int)mem.size() * bs;
+  if (m < 6) return false;
+  std::vector<double> Bm((size_t)m * 6, 0.0), Q((size_t)m * 6), R(36);
+  if (l == 0) {
+    double c[3] = {0, 0, 0};
+    for (int v : mem)
+      for (int d = 0; d < 3; ++d) c[d] += coords[(int64_t)v * 3 + d];
+    for (int d = 0; d < 3; ++d) c[d] /= (double)mem.size();
+    for (size_t u = 0; u < mem.size(); ++u) {
+      const int64_t v = mem[u];
+      if (dir && dir[v]) continue;
+      const double x = coords[v * 3] - c[0], y = coords[v * 3 + 1] - c[1], z = coords[v * 3 + 2] - c[2];
+      double* b = &Bm[u * 18];
+      b[0 * 6 + 0] = b[1 * 6 + 1] = b[2 * 6 + 2] = 1.0;
+      b[0 * 6 + 3] = -y;
+      b[1 * 6 + 3] = x;
+      b[1 * 6 + 4] = -z;
+      b[2 * 6 + 4] = y;
+      b[0 * 6 + 5] = z;
+      b[2 * 6 + 5] = -x;
+    }
+  } else {
+    for (size_t u = 0; u < mem.size(); ++u)
+      std::copy(&B[(size_t)mem[u] * 36], &B[(size_t)mem[u] * 36] + 36, &Bm[u * 36]);
+  }
+  return thin_qr(m, Bm.data(), Q.data(), R.data());
 }
 
 // --------------------------------------------------------------- device kernels
@@ -609,6 +653,69 @@ static Status smooth_level(bamg_mg* mg, int l) {
   return Status{};
 }
 
+// Aggregates of level l from the device strength graph and MIS (Sec. 3.2,
+// Sec. 6), then the two host rules: vertices without strong neighbours join
+// no aggregate, and rank-deficient aggregates are dissolved into their
+// neighbours' surviving aggregates (the vertex's strong neighbour whose
+// aggregate root has the largest (weight, root)); survivors are renumbered
+// in root order.
+static Status mis_level_aggregates(bamg_mg* mg, int l, const double* coords, const uint8_t* dir,
+                                   const std::vector<double>& B, std::vector<int>& agg, int64_t& nagg) {
+  bamg_ctx* ctx = mg->ctx;
+  cudaStream_t st = ctx->stream;
+  Level& L = mg->levels[l];
+  const int64_t n = L.n;
+  const uint64_t seed = mg->opts.mis_seed + (uint64_t)l;
+  int *rp = nullptr, *col = nullptr, *dagg = nullptr, *droot = nullptr;
+  std::vector<int> hrp, hcol, hroot;
+  int64_t ne = 0, na = 0;
+  int rounds = 0;
+  Status s = dalloc(&rp, n + 1, st);
+  if (s.ok()) s = dalloc(&col, std::max<int64_t>(L.A->nnzb, 1), st);
+  if (s.ok()) s = dalloc(&dagg, std::max<int64_t>(n, 1), st);
+  if (s.ok()) s = dalloc(&droot, std::max<int64_t>(n, 1), st);
+  if (s.ok()) s = strength_graph(L.A, mg->opts.mis_eps, rp, col, L.A->nnzb, &ne);
+  if (s.ok()) s = mis_aggregate(ctx, n, rp, col, seed, dagg, &na, &rounds, droot);
+  if (s.ok()) s = download(hrp, rp, n + 1, st);
+  if (s.ok()) s = download(hcol, col, ne, st);
+  if (s.ok()) s = download(agg, dagg, n, st);
+  if (s.ok()) s = download(hroot, droot, na, st);
+  dfree(rp, st);
+  dfree(col, st);
+  dfree(dagg, st);
+  dfree(droot, st);
+  if (!s.ok()) return s;
+  std::vector<std::vector<int>> mem(na);
+  for (int64_t v = 0; v < n; ++v) {
+    if (hrp[v + 1] == hrp[v]) agg[v] = -1;  // no strong neighbour
+    if (agg[v] >= 0) mem[agg[v]].push_back((int)v);
+  }
+  std::vector<char> dissolved(na, 0);
+  for (int64_t a = 0; a < na; ++a)
+    dissolved[a] = !mem[a].empty() && !near_null_full_rank(l, mem[a], coords, dir, B);
+  auto better = [&](int a, int b) {  // root of aggregate a beats root of aggregate b in (weight, root)
+    const uint64_t wa = splitmix64_host((uint64_t)hroot[a], seed), wb = splitmix64_host((uint64_t)hroot[b], seed);
+    return wa > wb || (wa == wb && hroot[a] > hroot[b]);
+  };
+  std::vector<int> out(agg);
+  for (int64_t v = 0; v < n; ++v) {
+    if (agg[v] < 0 || !dissolved[agg[v]]) continue;
+    int best = -1;
+    for (int k = hrp[v]; k < hrp[v + 1]; ++k) {
+      const int a = agg[hcol[k]];
+      if (a >= 0 && !dissolved[a] && (best < 0 || better(a, best))) best = a;
+    }
+    out[v] = best;
+  }
+  std::vector<int> renum(na, -1);
+  nagg = 0;
+  for (int64_t a = 0; a < na; ++a)
+    if (!mem[a].empty() && !dissolved[a]) renum[a] = (int)nagg++;
+  for (int64_t v = 0; v < n; ++v) agg[v] = out[v] >= 0 ? renum[out[v]] : -1;
+  if (nagg == 0) return make_status(BAMG_ERR_INVALID, "level %d: no aggregate survives", l);
+  return Status{};
+}
+
 static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, const uint8_t* dir) {
   bamg_ctx* ctx = mg->ctx;
   cudaStream_t st = ctx->stream;
@@ -630,19 +737,26 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
     const int l = (int)mg->levels.size() - 1;
     Level& L = mg->levels[l];
     std::vector<int> agg;
-    int cgrid[3];
-    aggregates(grid, agg, cgrid);
-    const int64_t nagg = (int64_t)cgrid[0] * cgrid[1] * cgrid[2];
+    int cgrid[3] = {0, 0, 0};
+    int64_t nagg = 0;
     const int bs = L.bs;
+    if (o.aggregation == BAMG_AGG_MIS) {
+      BAMG_TRY(mis_level_aggregates(mg, l, coords, dir, B, agg, nagg));
+    } else {
+      aggregates(grid, agg, cgrid);
+      nagg = (int64_t)cgrid[0] * cgrid[1] * cgrid[2];
+    }
     if (l == 0) B = rigid_modes(coords, dir, agg, nagg);
-    // tentative prolongator by per-aggregate QR
+    // tentative prolongator by per-aggregate QR (nodes outside every aggregate get no block)
     std::vector<int64_t> start(nagg + 1, 0);
-    for (int64_t v = 0; v < L.n; ++v) start[agg[v] + 1]++;
+    for (int64_t v = 0; v < L.n; ++v)
+      if (agg[v] >= 0) start[agg[v] + 1]++;
     for (int64_t a = 0; a < nagg; ++a) start[a + 1] += start[a];
-    std::vector<int64_t> members(L.n);
+    std::vector<int64_t> members(start[nagg]);
     {
       std::vector<int64_t> fill(start.begin(), start.end() - 1);
-      for (int64_t v = 0; v < L.n; ++v) members[fill[agg[v]]++] = v;
+      for (int64_t v = 0; v < L.n; ++v)
+        if (agg[v] >= 0) members[fill[agg[v]]++] = v;
     }
     std::vector<double> Q((size_t)L.n * bs * 6, 0.0), Bc((size_t)nagg * 36, 0.0);
     for (int64_t a = 0; a < nagg; ++a) {
@@ -671,10 +785,17 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
     if (bamg_bsr_create(ctx, bs, 6, L.n, nagg, &Pt) != BAMG_OK) return make_status(BAMG_ERR_OOM, "P~");
     std::unique_ptr<bamg_bsr, bamg_status (*)(bamg_bsr*)> Pt_guard(Pt, bamg_bsr_destroy);
     {
-      std::vector<int> rp(L.n + 1), ci(agg.begin(), agg.end());
-      for (int64_t v = 0; v <= L.n; ++v) rp[v] = (int)v;
+      std::vector<int> rp(L.n + 1, 0), ci;
+      std::vector<double> Qb;
+      for (int64_t v = 0; v < L.n; ++v) {
+        if (agg[v] >= 0) {
+          ci.push_back(agg[v]);
+          Qb.insert(Qb.end(), &Q[(size_t)v * bs * 6], &Q[(size_t)v * bs * 6] + bs * 6);
+        }
+        rp[v + 1] = (int)ci.size();
+      }
       BAMG_TRY(bsr_set_pattern(Pt, std::move(rp), std::move(ci)));
-      BAMG_TRY(bsr_upload_values(Pt, Q));
+      BAMG_TRY(bsr_upload_values(Pt, Qb));
     }
     // P = P~ - omega D_s^-1 A P~ on the pattern of A P~ (values by smooth_level)
     bamg_ptap* ap = nullptr;
@@ -811,6 +932,9 @@ void bamg_mg_opts_default(bamg_mg_opts* o) {
   o->precision = BAMG_FP64;
   o->autotune = 1;
   o->coarse_solver = 0;
+  o->aggregation = BAMG_AGG_GEOMETRIC;
+  o->mis_eps = 0.08;
+  o->mis_seed = 1;
 }
 
 bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, const uint8_t* dirichlet,
@@ -824,7 +948,12 @@ bamg_status bamg_mg_setup(bamg_ctx* ctx, bamg_bsr* A, const double* coords, cons
     bamg_mg_opts_default(&o);
   if (!A->has_pattern || A->br != 3 || A->bc != 3 || A->nbr != A->nbc)
     return fail(ctx, make_status(BAMG_ERR_INVALID, "mg_setup needs an assembled square 3x3-block operator"));
-  if ((int64_t)o.grid[0] * o.grid[1] * o.grid[2] != A->nbr || o.grid[0] <= 0)
+  if (o.aggregation != BAMG_AGG_GEOMETRIC && o.aggregation != BAMG_AGG_MIS)
+    return fail(ctx, make_status(BAMG_ERR_INVALID, "unknown aggregation %d", o.aggregation));
+  if (o.aggregation == BAMG_AGG_MIS && !(o.mis_eps >= 0))
+    return fail(ctx, make_status(BAMG_ERR_INVALID, "mis_eps must be >= 0"));
+  if (o.aggregation == BAMG_AGG_GEOMETRIC &&
+      ((int64_t)o.grid[0] * o.grid[1] * o.grid[2] != A->nbr || o.grid[0] <= 0))
     return fail(ctx, make_status(BAMG_ERR_INVALID, "opts.grid %dx%dx%d does not match %lld block rows", o.grid[0],
                                  o.grid[1], o.grid[2], (long long)A->nbr));
   if (o.max_levels < 1 || o.max_levels > 16 || o.cheb_degree < 1 || o.cheb_degree > 12 || o.power_its < 1 ||
@@ -915,6 +1044,14 @@ bamg_status bamg_mg_get_level(const bamg_mg* mg, int level, bamg_bsr** A, bamg_b
 bamg_status bamg_mg_get_restriction(const bamg_mg* mg, int level, bamg_bsr** R) {
   if (!mg || !R || level < 0 || level >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
   *R = mg->levels[level].R;
+  return BAMG_OK;
+}
+
+bamg_status bamg_mg_get_aggregates(const bamg_mg* mg, int level, int32_t* agg) {
+  if (!mg || !agg || level < 0 || level + 1 >= (int)mg->levels.size()) return BAMG_ERR_INVALID;
+  const Level& L = mg->levels[level];
+  if (L.n > 0 && cudaMemcpyAsync(agg, L.agg, sizeof(int) * L.n, cudaMemcpyDeviceToDevice, mg->ctx->stream) != cudaSuccess)
+    return fail(mg->ctx, cuda_status(cudaGetLastError(), "aggregates"));
   return BAMG_OK;
 }
 
