@@ -48,7 +48,7 @@ MAXIT = 500
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/traffic_cheb_step_l0_64cubed_fp64.md), with a fingerprint of the
 # kernel's sources at capture time; reported as null once they change.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.5e6, "2afcb46c5b2bd38c")}
+TRAFFIC = {("cheb_step_l0", 64, False): (589.7e6, "f9e4265b83513b2a")}
 TRAFFIC_SOURCES = ("paper_2606_24748_gb300/csrc/device.cuh", "paper_2606_24748_gb300/csrc/cycle.cu")
 
 
@@ -72,6 +72,8 @@ def parse():
                         "else written after tuning; makes a run under a profiler use the timed run's choices")
     p.add_argument("--no-multi", action="store_true", help="skip the 16-right-hand-side measurement")
     p.add_argument("--no-batch", action="store_true", help="skip the 32-problem batch measurement")
+    p.add_argument("--step-only", action="store_true",
+                   help="only the timed reuse steps and their per-kernel table (for runs under a profiler)")
     p.add_argument("--no-large", action="store_true",
                    help="skip the 127^3 FP64-vs-mixed comparison (4 levels, 6.3 M dofs)")
     p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large", "ptap"],
@@ -333,17 +335,21 @@ def run_ours(args):
         dist = tdist
     K, W = args.steps, args.warmup
     pctx = B.bamg_ctx_create(torch.cuda.current_stream())
-    alu = alu_peaks(B, pctx)
+    alu = alu_peaks(B, pctx) if not args.step_only else {"fp64_peak_tflops": round(FP64_PEAK_DERIVED_TFLOPS, 4),
+                                                          "fp64_probe_tflops": None}
     B.bamg_ctx_destroy(pctx)
     stream_bytes = 72 * Mesh(args.ne, args.order).nodes_per_element ** 2 * args.ne ** 3
     wl = Workload(B, torch, args.ne, 0.3, args.precision, order=args.order,
                   n_inputs=min(K + W, 8, max(2, int(16e9 // stream_bytes))), autotune=args.autotune,
                   tune_cache=args.tune_cache)
+    # inside the timed region only the roofline candidates are bracketed by
+    # events (each bracket costs the kernel its overlap with its neighbours);
+    # enabled before the warm-up, so that the CG graphs are captured with
+    # them outside the timed region, and re-enabled after it (resets totals)
+    B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
     for k in range(W):
         wl.step(k)
     clocks = Clocks(local)
-    # inside the timed region only the roofline candidates are bracketed by
-    # events (each bracket costs the kernel its overlap with its neighbours)
     B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
     lib_setup_bytes, _ = B.bamg_device_memory(wl.ctx, reset_peak=True)
     launches0 = B.bamg_kernel_launches()
@@ -390,6 +396,11 @@ def run_ours(args):
         "device_used": round((total_b - free_b) / 1e9, 3),
         "note": "library = its stream-ordered pool allocations (hierarchy, plans, vectors); "
                 "inputs = the value streams and vectors bench.py keeps resident through torch"}
+    if args.step_only:
+        wl.close()
+        if dist:
+            dist.destroy_process_group()
+        return result if rank == 0 else None
     # phases (separate, untimed pass for the breakdown)
     result["phases_ms"] = phases(wl, torch, B)
     result["ptap_reuse"] = ptap_reuse(wl, torch, B)
@@ -904,6 +915,7 @@ def compare_mixed(args, torch, B, x64, alu, ne=None, steps=None):
     stream_bytes = 72 * Mesh(ne, args.order).nodes_per_element ** 2 * ne ** 3
     wl = Workload(B, torch, ne, 0.3, "mixed", n_inputs=min(K, max(2, int(16e9 // stream_bytes))),
                   order=args.order)
+    B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)   # CG graphs captured with the slots in the warm-up
     for k in range(3):
         wl.step(k)
     B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)
@@ -936,6 +948,7 @@ def large_compare(torch, B, alu, ne=127, steps=5, warmup=3):
     args = parse_args_for_test(["--ne", str(ne), "--steps", str(steps)])
     stream_bytes = 72 * 64 * ne ** 3
     wl = Workload(B, torch, ne, 0.3, "fp64", n_inputs=min(steps, max(2, int(16e9 // stream_bytes))))
+    B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)   # CG graphs captured with the slots in the warm-up
     for k in range(warmup):
         wl.step(k)
     B.bamg_ctx_profile_slots(wl.ctx, ROOFLINE_SLOTS)

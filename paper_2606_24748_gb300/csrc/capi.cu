@@ -330,9 +330,11 @@ bamg_status bamg_ctx_profile_slots(bamg_ctx* c, unsigned mask) {
   if (!c) return BAMG_ERR_INVALID;
   Prof& p = c->prof;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, cuda_status(cudaGetLastError(), "profile"));
+  // graphs captured under another mask hold other event nodes: re-capture
+  // only when the mask changes (re-enabling the same slots just resets)
+  if ((mask != 0) != p.on || mask != p.mask) p.epoch++;
   p.on = mask != 0;
   p.mask = mask;
-  p.epoch++;
   p.eager_used = 0;
   for (int k = 0; k < BAMG_PROF_COUNT; ++k) {
     p.ms[k] = 0.0;

@@ -625,7 +625,11 @@ static Status cooperative_factor(bamg_ctx* ctx, cudaStream_t st, double* F, doub
   int per_sm = 0;
   BAMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_factor, 256, 0));
   if (per_sm < 1) return make_status(BAMG_ERR_CUDA, "dense factor kernel cannot be resident");
-  const int grid = std::max(1, std::min(per_sm, 2)) * ctx->sm_count;
+  // one CTA per SM: a factor step has at most a few tile items per CTA of
+  // this grid, and the launch must fit beside the smoother refresh that runs
+  // concurrently on the other stream (all its CTAs resident at once)
+  const int grid = ctx->sm_count;
+  (void)per_sm;
   if (grid / (F2 ? 2 : 1) < 5) return make_status(BAMG_ERR_CUDA, "dense factor needs at least five CTAs per matrix");
   int* err = ctx->d_err;
   unsigned* qctr = ctx->d_counters + kFactorCounters;

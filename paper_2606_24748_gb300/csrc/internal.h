@@ -298,6 +298,10 @@ struct bamg_mg {
   // forked after the last Galerkin product, joined before the update returns
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // mixed form: the finest level's (FP64) smoother refresh runs on a third
+  // stream under the FP32 Galerkin products
+  cudaStream_t side0 = nullptr;
+  cudaEvent_t ev_join0 = nullptr;
 };
 
 namespace bamg {
@@ -378,8 +382,8 @@ void ptap_release(bamg_ptap* plan);
 Status launch_gather_blocks(const bamg_bsr* A, const double* vals, double* out, cudaStream_t st);
 
 // Hierarchy internals shared by the setup, cycle and coarse-solver units.
-Status mg_refresh_level(bamg_mg* mg, int l);            // Dinv, eigen-estimate, Chebyshev coefficients
-Status mg_refresh_restriction(bamg_mg* mg, int l);      // state-gated R = P^T
+Status mg_refresh_level(bamg_mg* mg, int l, cudaStream_t st);        // Dinv, eigen-estimate, Chebyshev coefficients
+Status mg_refresh_restriction(bamg_mg* mg, int l, cudaStream_t st);  // state-gated R = P^T
 Status coarse_factor(bamg_mg* mg, cudaStream_t st);                      // dense Cholesky + inverse of the coarsest level
 template <typename T>
 Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t st);
@@ -389,7 +393,7 @@ template <typename T>
 Status coarse_apply_multi(bamg_mg* mg, int kp, const T* b, T* x, double* work, const int* done, cudaStream_t st);
 template <typename T>
 Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
-Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot);
+Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot, cudaStream_t st);
 void mg_release_graphs(bamg_mg* mg);
 void mg_release_multi(bamg_mg* mg);               // multi-right-hand-side work area
 Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st);  // features -> MLP -> level weights

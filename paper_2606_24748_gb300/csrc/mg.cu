@@ -429,9 +429,9 @@ __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_
 
 template <int BS, typename TM>
 static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const double* dinv, const float* wts,
-                         bool scalar_diag, double* out_scal) {
+                         bool scalar_diag, double* out_scal, cudaStream_t st) {
   bamg_ctx* ctx = mg->ctx;
-  cudaStream_t st = ctx->stream;
+  
   const int64_t n = A->nbr, rows = row_threads_for<TM>(A);
   double* w[2] = {mg->power_w[0], mg->power_w[1]};
   double* norms = mg->scal + (int64_t)mg->levels.size() * kScalarsPerLevel;  // 2 scratch slots
@@ -460,7 +460,7 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
   return Status{};
 }
 
-Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal) {
+Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal, cudaStream_t st) {
   Level& L = mg->levels[l];
   bamg_bsr* A = L.A;
   // FP64 arithmetic on the FP64 values when they are current (the fine level
@@ -471,18 +471,17 @@ Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scal) {
   if (f32) BAMG_TRY(bsr_ensure_fp32(A));
   const float* wts = L.weights;
   if (L.bs == 3)
-    return f32 ? power_impl<3, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal)
-               : power_impl<3, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal);
+    return f32 ? power_impl<3, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal, st)
+               : power_impl<3, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal, st);
   if (L.bs == 6)
-    return f32 ? power_impl<6, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal)
-               : power_impl<6, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal);
+    return f32 ? power_impl<6, float>(mg, A, A->vals32, L.dinv, wts, scalar_diag, out_scal, st)
+               : power_impl<6, double>(mg, A, A->vals, L.dinv, wts, scalar_diag, out_scal, st);
   return make_status(BAMG_ERR_INVALID, "block size %d", L.bs);
 }
 
-Status mg_refresh_level(bamg_mg* mg, int l) {
+Status mg_refresh_level(bamg_mg* mg, int l, cudaStream_t st) {
   Level& L = mg->levels[l];
   bamg_ctx* ctx = mg->ctx;
-  cudaStream_t st = ctx->stream;
   const bamg_bsr* A = L.A;
   const unsigned b = (unsigned)((L.n + 127) / 128);
   float* d32 = mg->opts.precision == BAMG_FP32 ? L.dinv32 : nullptr;
@@ -501,13 +500,12 @@ Status mg_refresh_level(bamg_mg* mg, int l) {
     BAMG_CUDA(cudaGetLastError());
   }
   BAMG_TRY(mg_learned_weights(mg, l, st));
-  return power_lambda(mg, l, false, mg->scal + (int64_t)l * kScalarsPerLevel);
+  return power_lambda(mg, l, false, mg->scal + (int64_t)l * kScalarsPerLevel, st);
 }
 
-Status mg_refresh_restriction(bamg_mg* mg, int l) {
+Status mg_refresh_restriction(bamg_mg* mg, int l, cudaStream_t st) {
   Level& L = mg->levels[l];
   if (!L.P || L.r_version == L.P->version) return Status{};
-  cudaStream_t st = mg->ctx->stream;
   const int64_t nt = L.R->nnzb * L.R->block_elems();
   if (nt > 0) {
     const unsigned b = (unsigned)((nt + 255) / 256);
@@ -581,9 +579,12 @@ static void mg_release(bamg_mg* mg) {
   cudaStream_t st = mg->ctx->stream;
   if (mg->side) {
     cudaStreamSynchronize(mg->side);
+    cudaStreamSynchronize(mg->side0);
     cudaStreamDestroy(mg->side);
+    cudaStreamDestroy(mg->side0);
     cudaEventDestroy(mg->ev_fork);
     cudaEventDestroy(mg->ev_join);
+    cudaEventDestroy(mg->ev_join0);
     mg->side = nullptr;
   }
   mg_release_graphs(mg);
@@ -628,7 +629,7 @@ static Status smooth_level(bamg_mg* mg, int l) {
   const int bs = L.bs;
   // scratch slot in the last (spare) block of scalars
   double* lam_slot = mg->scal + (int64_t)mg->scal_blocks_minus1 * kScalarsPerLevel + 4;
-  BAMG_TRY(power_lambda(mg, l, true, lam_slot));
+  BAMG_TRY(power_lambda(mg, l, true, lam_slot, st));
   double lam_s = 0.0;
   BAMG_CUDA(cudaMemcpyAsync(&lam_s, lam_slot + kLam, sizeof(double), cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaStreamSynchronize(st));
@@ -873,32 +874,65 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
 static Status update_streams(bamg_mg* mg) {
   if (mg->side) return Status{};
   BAMG_CUDA(cudaStreamCreateWithFlags(&mg->side, cudaStreamNonBlocking));
+  BAMG_CUDA(cudaStreamCreateWithFlags(&mg->side0, cudaStreamNonBlocking));
   BAMG_CUDA(cudaEventCreateWithFlags(&mg->ev_fork, cudaEventDisableTiming));
   BAMG_CUDA(cudaEventCreateWithFlags(&mg->ev_join, cudaEventDisableTiming));
+  BAMG_CUDA(cudaEventCreateWithFlags(&mg->ev_join0, cudaEventDisableTiming));
   return Status{};
 }
 
+static Status refresh_one(bamg_mg* mg, int l, cudaStream_t st) {
+  BAMG_TRY(mg_refresh_restriction(mg, l, st));
+  const int pr = prof_begin(mg->ctx, BAMG_PROF_REFRESH, st);
+  Status s = mg_refresh_level(mg, l, st);
+  prof_end(mg->ctx, pr, st);
+  return s;
+}
+
+// Streams of one reuse update:
+//   main:  Galerkin products, level by level; then the smoother refresh;
+//   side:  the coarsest factorisation, from the last product on;
+//   side0: (mixed form only) the finest level's refresh from the start: it
+//          reads only the fine operator, its power iteration is FP64-bound
+//          while the FP32 Galerkin products are memory-bound, so the two
+//          overlap.  (In the FP64 form both are FP64-bound and the refresh
+//          stays on the main stream, beside the factor.)
+// The refreshes share scratch (power-iteration vectors, reduction partials),
+// so the next level's refresh waits for side0.  Every path joins the side
+// streams into the caller's stream before returning.
 Status mg_update_impl(bamg_mg* mg) {
   const int nl = (int)mg->levels.size();
   const bamg_prec pp = mg->opts.precision == BAMG_FP32 ? BAMG_FP32 : BAMG_FP64;
   cudaStream_t st = mg->ctx->stream;
-  for (int l = 0; l + 1 < nl; ++l) {
-    Level& L = mg->levels[l];
-    BAMG_TRY(ptap_run(L.plan, L.A, L.P, mg->levels[l + 1].A, pp, true));
-  }
   BAMG_TRY(update_streams(mg));
+  const bool early0 = pp == BAMG_FP32 && nl > 1;
+  Status r0;
+  if (early0) {
+    BAMG_CUDA(cudaEventRecord(mg->ev_fork, st));
+    BAMG_CUDA(cudaStreamWaitEvent(mg->side0, mg->ev_fork, 0));
+    r0 = refresh_one(mg, 0, mg->side0);
+    BAMG_CUDA(cudaEventRecord(mg->ev_join0, mg->side0));
+  }
+  Status ps;
+  for (int l = 0; l + 1 < nl && ps.ok(); ++l) {
+    Level& L = mg->levels[l];
+    ps = ptap_run(L.plan, L.A, L.P, mg->levels[l + 1].A, pp, true);
+  }
+  if (!ps.ok()) {
+    if (early0) cudaStreamWaitEvent(st, mg->ev_join0, 0);
+    return ps;
+  }
   BAMG_CUDA(cudaEventRecord(mg->ev_fork, st));
   BAMG_CUDA(cudaStreamWaitEvent(mg->side, mg->ev_fork, 0));
   const Status fs = coarse_factor(mg, mg->side);
   BAMG_CUDA(cudaEventRecord(mg->ev_join, mg->side));
   auto refresh = [&]() -> Status {
-    BAMG_TRY(fs);
-    for (int l = 0; l + 1 < nl; ++l) {
-      BAMG_TRY(mg_refresh_restriction(mg, l));
-      const int pr = prof_begin(mg->ctx, BAMG_PROF_REFRESH, st);
-      BAMG_TRY(mg_refresh_level(mg, l));
-      prof_end(mg->ctx, pr, st);
+    if (early0) {
+      BAMG_CUDA(cudaStreamWaitEvent(st, mg->ev_join0, 0));
+      BAMG_TRY(r0);
     }
+    BAMG_TRY(fs);
+    for (int l = early0 ? 1 : 0; l + 1 < nl; ++l) BAMG_TRY(refresh_one(mg, l, st));
     if (pp == BAMG_FP32) {
       BAMG_TRY(bsr_ensure_fp32(mg->levels[0].A));
       for (int l = 0; l + 1 < nl; ++l) {
@@ -909,6 +943,7 @@ Status mg_update_impl(bamg_mg* mg) {
     return Status{};
   };
   const Status rs = refresh();
+  if (early0) cudaStreamWaitEvent(st, mg->ev_join0, 0);
   // joined on every path: the caller's stream never runs ahead of the factor
   BAMG_CUDA(cudaStreamWaitEvent(st, mg->ev_join, 0));
   return rs;
