@@ -41,8 +41,28 @@ __global__ void k_coo_sum(const int* __restrict__ seg, const int* __restrict__ p
   // FP64 adds run at two per clock per SM: start from the first contribution
   // instead of zero, and test for NaN / Inf on the exponent bits (integer
   // pipe) rather than with FP64 comparisons.
-  double sum = s1 > s0 ? __ldg(v + (int64_t)perm[s0] * B + e) : 0.0;
-  for (int s = s0 + 1; s < s1; ++s) sum += __ldg(v + (int64_t)perm[s] * B + e);
+  // contributions four at a time: their permutation entries, then their
+  // values, are loaded before any is added (independent loads in flight);
+  // the sum still runs in stream order
+  double sum = s1 > s0 ? __ldg(v + (int64_t)__ldg(perm + s0) * B + e) : 0.0;
+  int s = s0 + 1;
+  for (; s + 3 < s1; s += 4) {
+    const int p0 = __ldg(perm + s), p1 = __ldg(perm + s + 1), p2 = __ldg(perm + s + 2), p3 = __ldg(perm + s + 3);
+    const double v0 = __ldg(v + (int64_t)p0 * B + e), v1 = __ldg(v + (int64_t)p1 * B + e);
+    const double v2 = __ldg(v + (int64_t)p2 * B + e), v3 = __ldg(v + (int64_t)p3 * B + e);
+    sum += v0;
+    sum += v1;
+    sum += v2;
+    sum += v3;
+  }
+  if (s + 1 < s1) {
+    const int p0 = __ldg(perm + s), p1 = __ldg(perm + s + 1);
+    const double v0 = __ldg(v + (int64_t)p0 * B + e), v1 = __ldg(v + (int64_t)p1 * B + e);
+    sum += v0;
+    sum += v1;
+    s += 2;
+  }
+  if (s < s1) sum += __ldg(v + (int64_t)__ldg(perm + s) * B + e);
   const int64_t a = vidx<B>(slot_of[k], e);
   if (add) sum += vals[a];
   if ((__double_as_longlong(sum) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) set_err(err, kDevNaN);
