@@ -57,8 +57,12 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* _
   }
 }
 
-// x += d_in; r -= A d_in; if has_next: d_out = c1 d_in + c2 w Dinv r
-template <int BS, int V, typename T>
+// x += d_in; r -= A d_in; if has_next: d_out = c1 d_in + c2 w Dinv r.
+// FINAL (the last step of post-smoothing): the next direction is the last
+// one; it is added to x here ((x + d_in) + d_out, the order of a separate
+// update) instead of being stored.  A separate instance, so that the common
+// one keeps its register count.
+template <int BS, int V, typename T, bool FINAL = false>
 __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict__ sp, const int* __restrict__ col,
                                                            const T* __restrict__ vals, int64_t n, int64_t nthreads,
                                                            const T* __restrict__ d_in, T* __restrict__ d_out,
@@ -82,15 +86,21 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
     di[a] = d_in[i * BS + a];
     ri[a] = r[i * BS + a] - acc[a];
     r[i * BS + a] = ri[a];
-    x[i * BS + a] += di[a];
+    if constexpr (!FINAL) x[i * BS + a] += di[a];
   }
-  if (has_next) {
+  if (FINAL || has_next) {
     T z[BS];
     dinv_apply<BS, T>(dinv, i, ri, z);
     const T c1 = (T)scal[kCheb + 2 * k];
     const T c2 = (T)(scal[kCheb + 2 * k + 1] * (w ? (double)w[i] : 1.0));
 #pragma unroll
-    for (int a = 0; a < BS; ++a) d_out[i * BS + a] = fma(c1, di[a], c2 * z[a]);
+    for (int a = 0; a < BS; ++a) {
+      const T dn = fma(c1, di[a], c2 * z[a]);
+      if constexpr (FINAL)
+        x[i * BS + a] = (x[i * BS + a] + di[a]) + dn;
+      else
+        d_out[i * BS + a] = dn;
+    }
   }
 }
 
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restric
 // Component-split forms of the three row kernels above (6-row blocks): CTA =
 // one slice, BS * VS warps (see row_component).  The block-diagonal inverse
 // needs every component of the new residual, exchanged through shared memory.
-template <int BS, int VS, typename T>
+template <int BS, int VS, typename T, bool FINAL = false>
 __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__ sp, const int* __restrict__ col,
                                                          const T* __restrict__ vals, int64_t n,
                                                          const T* __restrict__ d_in, T* __restrict__ d_out,
@@ -148,9 +158,9 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
     di = d_in[i * BS + a];
     ri = r[i * BS + a] - acc;
     r[i * BS + a] = ri;
-    x[i * BS + a] += di;
+    if constexpr (!FINAL) x[i * BS + a] += di;
   }
-  if (!has_next) return;
+  if (!FINAL && !has_next) return;
   if (sub == 0) rs[a][lane] = ri;
   __syncthreads();
   if (!lead) return;
@@ -160,7 +170,11 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
   for (int c = 0; c < BS; ++c) z = fma(__ldg(dinv + base + 32 * (a * BS + c)), rs[c][lane], z);
   const T c1 = (T)scal[kCheb + 2 * k];
   const T c2 = (T)(scal[kCheb + 2 * k + 1] * (w ? (double)w[i] : 1.0));
-  d_out[i * BS + a] = fma(c1, di, c2 * z);
+  const T dn = fma(c1, di, c2 * z);
+  if constexpr (FINAL)
+    x[i * BS + a] = (x[i * BS + a] + di) + dn;  // last post-smoothing step (see k_cheb_step)
+  else
+    d_out[i * BS + a] = dn;
 }
 
 template <int BS, int VS, typename T>
@@ -348,22 +362,28 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k + 1 < m; ++k) {
     const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
+    const bool last = k + 2 == m;  // the last step adds the final direction to x itself
     if (split) {
       BAMG_DISPATCH_VS(split, {
-        BAMG_CUDA(launch_k(k_cheb_step_split<BS, VS, T>, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
-                                                                  d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                                  1, done));
+        auto kern = last ? k_cheb_step_split<BS, VS, T, true> : k_cheb_step_split<BS, VS, T, false>;
+        BAMG_CUDA(launch_k(kern, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
+                           d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
-                                                     d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done)); BAMG_COUNT_LAUNCH; })
+      BAMG_DISPATCH_V(lanes_for<T>(A), {
+        auto kern = last ? k_cheb_step<BS, V, T, true> : k_cheb_step<BS, V, T, false>;
+        BAMG_CUDA(launch_k(kern, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows,
+                           d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done));
+        BAMG_COUNT_LAUNCH; })
     }
     prof_end(mg->ctx, pm, st);
   }
-  const int64_t mm = L.n * BS;
-  const int pa = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_L0_VECTOR : -1, st);
-  { BAMG_CUDA(launch_k(k_axpy_done<T>, dim3((unsigned)((mm + 255) / 256)), dim3(256), st, mm, d[(m - 1) & 1], p.x, done)); BAMG_COUNT_LAUNCH; }
-  prof_end(mg->ctx, pa, st);
+  if (m == 1) {  // degree 1: no step here, the direction from the residual start is the update
+    const int64_t mm = L.n * BS;
+    const int pa = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_L0_VECTOR : -1, st);
+    { BAMG_CUDA(launch_k(k_axpy_done<T>, dim3((unsigned)((mm + 255) / 256)), dim3(256), st, mm, d[0], p.x, done)); BAMG_COUNT_LAUNCH; }
+    prof_end(mg->ctx, pa, st);
+  }
   prof_end(mg->ctx, pw, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
