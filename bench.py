@@ -546,7 +546,7 @@ def ptap_reuse(wl, torch, B):
             "timing": "symbolic + first numeric: host clock around synchronised calls; numeric: CUDA events, median of 5"}
 
 
-def mis_hierarchy(wl, torch, B, eps=0.08, seed=1):
+def mis_hierarchy(wl, torch, B, eps=0.02, seed=1):
     """The same operator with the hierarchy built from device MIS aggregates
     of the block strength graph (instead of 3x3x3 node cubes): cold setup
     time, level sizes, and the reuse step's update and CG to rtol 1e-8 (CUDA

@@ -388,7 +388,7 @@ typedef struct {
                                on opts.grid; BAMG_AGG_MIS: on every level, MIS
                                aggregates of the block strength graph (see
                                bamg_mg_setup) */
-  double mis_eps;           /* strength threshold eps of BAMG_AGG_MIS (0.08) */
+  double mis_eps;           /* strength threshold eps of BAMG_AGG_MIS (0.02) */
   uint64_t mis_seed;        /* vertex-weight seed of level l: mis_seed + l (1) */
 } bamg_mg_opts;
 typedef enum { BAMG_AGG_GEOMETRIC = 0, BAMG_AGG_MIS = 1 } bamg_aggregation;

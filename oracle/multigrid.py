@@ -61,7 +61,7 @@ class Hierarchy:
 def setup(A: BlockMatrix, coords: np.ndarray, dirichlet: np.ndarray,
           grid: tuple[int, int, int], max_coarse_dofs: int = MAX_COARSE_DOFS,
           max_levels: int = 10, degree: int = 2, aggregation: str = "geometric",
-          eps: float = 0.08, seed: int = 1) -> Hierarchy:
+          eps: float = 0.02, seed: int = 1) -> Hierarchy:
     """aggregation: "geometric" (3x3x3 node cubes on the structured grid) or
     "mis" (MIS aggregates of each level's block strength graph, Sec. 3.2 and
     Sec. 6, with the readings of strength.hierarchy_aggregates; seed + level

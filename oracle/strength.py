@@ -188,6 +188,8 @@ def hierarchy_aggregates(A: BlockMatrix, eps: float, seed: int, near_null) -> tu
                 best = a
         out[v] = best
     keep = np.array([len(m) > 0 and not d for m, d in zip(members, dissolved)], dtype=bool)
+    if not keep.any():
+        raise ValueError("no aggregate survives: every aggregate's near-null block is rank deficient")
     renum = np.cumsum(keep) - 1
     out = np.where(out >= 0, renum[np.maximum(out, 0)], -1)
     return out.astype(np.int64), int(keep.sum())

@@ -968,7 +968,7 @@ void bamg_mg_opts_default(bamg_mg_opts* o) {
   o->autotune = 1;
   o->coarse_solver = 0;
   o->aggregation = BAMG_AGG_GEOMETRIC;
-  o->mis_eps = 0.08;
+  o->mis_eps = 0.02;
   o->mis_seed = 1;
 }
 

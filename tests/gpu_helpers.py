@@ -43,7 +43,7 @@ class GpuProblem:
     optional hierarchy."""
 
     def __init__(self, ne, nu=0.3, seed=None, precision=B.BAMG_FP64, max_coarse_dofs=2100, setup=True,
-                 E_el=None, coarse_solver=0, order=1, aggregation=B.BAMG_AGG_GEOMETRIC, mis_eps=0.08, mis_seed=1):
+                 E_el=None, coarse_solver=0, order=1, aggregation=B.BAMG_AGG_GEOMETRIC, mis_eps=0.02, mis_seed=1):
         self.mesh = Mesh(ne, order)
         self.nu = nu
         self.ctx = B.bamg_ctx_create(torch.cuda.current_stream())

@@ -23,7 +23,7 @@ def problem(ne: int, nu: float = 0.3, seed: int | None = None, order: int = 1):
 
 @functools.lru_cache(maxsize=None)
 def hierarchy(ne: int, nu: float = 0.3, max_coarse_dofs: int = omg.MAX_COARSE_DOFS, order: int = 1,
-              aggregation: str = "geometric", eps: float = 0.08, seed: int = 1):
+              aggregation: str = "geometric", eps: float = 0.02, seed: int = 1):
     mesh, _, A = problem(ne, nu, order=order)
     return omg.setup(A, mesh.coords(), mesh.dirichlet(), mesh.grid, max_coarse_dofs,
                      aggregation=aggregation, eps=eps, seed=seed)

@@ -58,7 +58,7 @@ def test_mis_hierarchy_reuse_step_and_options():
         out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)
         assert out["converged"] and out["true_rnorm"] <= 1.05e-8 * out["bnorm"]
         o = B.bamg_mg_opts_default()
-        assert o.aggregation == B.BAMG_AGG_GEOMETRIC and o.mis_eps == pytest.approx(0.08) and o.mis_seed == 1
+        assert o.aggregation == B.BAMG_AGG_GEOMETRIC and o.mis_eps == pytest.approx(0.02) and o.mis_seed == 1
         o.aggregation = 7
         with pytest.raises(B.BamgError):
             B.bamg_mg_setup(gp.ctx, gp.A, gp.mesh.coords(), gp.mesh.dirichlet(), o)
