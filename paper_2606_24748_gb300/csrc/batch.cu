@@ -3,7 +3,10 @@
 //
 // The graph holds, for every problem, the prologue of its solve (r = b,
 // z = M r, p = z), then one while-loop node whose body is one CG iteration of
-// every problem, then the epilogue (x and the true residual).  A one-warp
+// every problem, then the epilogue (x and the true residual).  Inside the
+// body each problem's iteration sits in a conditional IF node whose
+// condition a one-thread kernel sets from the problem's own state, so a
+// problem that has converged launches nothing for the rest of the loop.  A one-warp
 // kernel at the end of the prologue and of each loop body decides on the
 // device whether another iteration is needed (some problem is still running)
 // and sets the loop's condition, so the whole batch runs without a host round
@@ -33,6 +36,8 @@ struct bamg_batch {
   double grtol = -1.0;
   int gmaxit = -1;
   uint64_t outer_kernels = 0, body_kernels = 0;
+  std::vector<uint64_t> step_kernels;       // kernels of one CG iteration of each problem
+  std::vector<cudaStream_t> inner;          // capture streams of the IF bodies, one per branch
   CgState** d_states = nullptr;
   CgState* d_gather = nullptr;
   int* d_loops = nullptr;
@@ -58,6 +63,11 @@ __global__ void k_batch_continue(CgState* const* states, int n, int* loops, int 
     *loops = l;
     cudaGraphSetConditional(h, (active && l < max_loops) ? 1u : 0u);
   }
+}
+
+// Condition of a problem's IF node in the loop body: still iterating.
+__global__ void k_batch_if(const CgState* s, cudaGraphConditionalHandle h) {
+  cudaGraphSetConditional(h, s->done ? 0u : 1u);
 }
 
 __global__ void k_batch_gather(CgState* const* states, int n, CgState* out) {
@@ -167,8 +177,41 @@ Status build(bamg_batch* bt, const double* const* b, double* const* x, double rt
     cp.conditional.size = 1;
     BAMG_CUDA(cudaGraphAddNode(&cond, G, last.data(), nullptr, last.size(), &cp));
     body = cp.conditional.phGraph_out[0];
+    std::vector<cudaGraphConditionalHandle> hp(n);
+    for (int p = 0; p < n; ++p) BAMG_CUDA(cudaGraphConditionalHandleCreate(&hp[p], body, 0, 0));
+    bt->step_kernels.assign(n, 0);
     BAMG_CUDA(cudaStreamBeginCaptureToGraph(bt->origin, body, nullptr, nullptr, 0, mode));
-    BAMG_TRY(fork_join(bt, events, [&](int p, cudaStream_t st) { return cg_step(bt->mgs[p], st); }));
+    BAMG_TRY(fork_join(bt, events, [&](int p, cudaStream_t st) -> Status {
+      // condition kernel, then an IF node after it on this branch, whose
+      // body is the problem's iteration captured on the branch's inner stream
+      k_batch_if<<<1, 1, 0, st>>>(bt->mgs[p]->cg, hp[p]);
+      BAMG_CUDA(cudaGetLastError());
+      cudaStreamCaptureStatus bst;
+      cudaGraph_t bg = nullptr;
+      const cudaGraphNode_t* bdeps = nullptr;
+      size_t bnd = 0;
+      BAMG_CUDA(cudaStreamGetCaptureInfo(st, &bst, nullptr, &bg, &bdeps, nullptr, &bnd));
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hp[p];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t ifn = nullptr;
+      BAMG_CUDA(cudaGraphAddNode(&ifn, bg, bdeps, nullptr, bnd, &ip));
+      BAMG_CUDA(cudaStreamUpdateCaptureDependencies(st, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+      size_t bi = 0;
+      while (bi < bt->streams.size() && bt->streams[bi] != st) ++bi;
+      cudaStream_t in = bt->inner[bi];
+      BAMG_CUDA(cudaStreamBeginCaptureToGraph(in, ifbody, nullptr, nullptr, 0, mode));
+      Status cs = cg_step(bt->mgs[p], in);
+      cudaGraph_t done_g = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(in, &done_g);
+      BAMG_TRY(cs);
+      if (ee != cudaSuccess) return cuda_status(ee, "IF body capture");
+      bt->step_kernels[p] = kernel_nodes(ifbody);
+      return Status{};
+    }));
     k_batch_continue<<<1, 32, 0, bt->origin>>>(bt->d_states, n, bt->d_loops, maxit, 0, h);
     BAMG_CUDA(cudaGetLastError());
     BAMG_CUDA(cudaStreamEndCapture(bt->origin, &out));
@@ -223,7 +266,11 @@ Status solve(bamg_batch* bt, const double* const* b, double* const* x, double rt
   BAMG_CUDA(cudaMemcpyAsync(bt->h_true, bt->d_true, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaMemcpyAsync(bt->h_loops, bt->d_loops, sizeof(int), cudaMemcpyDeviceToHost, st));
   BAMG_CUDA(cudaStreamSynchronize(st));
-  g_launches.fetch_add(bt->outer_kernels + bt->body_kernels * (uint64_t)*bt->h_loops, std::memory_order_relaxed);
+  // top-level kernels of the body ran once per loop; each problem's
+  // iteration kernels only in the iterations it was still running
+  uint64_t launched = bt->outer_kernels + bt->body_kernels * (uint64_t)*bt->h_loops;
+  for (int p = 0; p < n; ++p) launched += bt->step_kernels[p] * (uint64_t)bt->h_states[p].its;
+  g_launches.fetch_add(launched, std::memory_order_relaxed);
   for (bamg_mg* mg : bt->mgs) BAMG_TRY(check_device_error(mg->ctx));
   if (loops_out) *loops_out = *bt->h_loops;
   int broke = -1, not_conv = -1;
@@ -249,9 +296,11 @@ Status solve(bamg_batch* bt, const double* const* b, double* const* x, double rt
 Status set_branches(bamg_batch* bt, int n_branches) {
   deal(bt, n_branches);
   while (bt->streams.size() < bt->branches.size()) {
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr, s2 = nullptr;
     BAMG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     bt->streams.push_back(s);
+    BAMG_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    bt->inner.push_back(s2);
   }
   release_exec(bt);
   return Status{};
@@ -262,6 +311,7 @@ void destroy(bamg_batch* bt) {
   cudaStream_t st = bt->ctx->stream;
   cudaStreamSynchronize(st);
   for (auto s : bt->streams) cudaStreamDestroy(s);
+  for (auto s : bt->inner) cudaStreamDestroy(s);
   if (bt->origin) cudaStreamDestroy(bt->origin);
   dfree(bt->d_states, st);
   dfree(bt->d_gather, st);
