@@ -48,7 +48,7 @@ MAXIT = 500
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/traffic_cheb_step_l0_64cubed_fp64.md), with a fingerprint of the
 # kernel's sources at capture time; reported as null once they change.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.7e6, "f9e4265b83513b2a")}
+TRAFFIC = {("cheb_step_l0", 64, False): (589.8e6, "15694f44b0da4a5d")}
 TRAFFIC_SOURCES = ("paper_2606_24748_gb300/csrc/device.cuh", "paper_2606_24748_gb300/csrc/cycle.cu")
 
 

@@ -128,6 +128,8 @@ void bsr_release(bamg_bsr* A) {
   dfree(A->coo_perm, st);
   dfree(A->coo_seg, st);
   dfree(A->coo_slot, st);
+  dfree(A->coo_soff, st);
+  dfree(A->coo_sperm, st);
   A->has_pattern = false;
   A->nnzb = 0;
   A->nslices = A->nchunks = 0;

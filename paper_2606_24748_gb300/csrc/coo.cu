@@ -70,6 +70,48 @@ __global__ void k_coo_sum(const int* __restrict__ seg, const int* __restrict__ p
   if (vals32) vals32[a] = (float)sum;
 }
 
+// The same sum with one thread per storage slot (slice order) and all B
+// elements of its block: every store of a warp then writes 32 consecutive
+// slots of one element (coalesced), and each contribution is read as one run
+// of B values.  The slot's contributions are contiguous in sperm (slots in
+// slice order, each slot's in input order), so the sum order is that of
+// k_coo_sum.  Padding slots have none and are left alone.
+template <int B>
+__global__ void __launch_bounds__(128) k_coo_sum_slots(const int* __restrict__ soff, const int* __restrict__ sperm,
+                                                       const double* __restrict__ v, int64_t nslots,
+                                                       double* __restrict__ vals, float* __restrict__ vals32,
+                                                       int add, int* __restrict__ err) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslots) return;
+  const int c0 = soff[s], c1 = soff[s + 1];
+  if (c0 == c1 && !add) return;
+  double acc[B];
+  const int64_t base = (s >> 5) * (32LL * B) + (s & 31);
+  if (c0 < c1) {
+    const double* p0 = v + (int64_t)__ldg(sperm + c0) * B;
+#pragma unroll
+    for (int e = 0; e < B; ++e) acc[e] = __ldg(p0 + e);
+    for (int c = c0 + 1; c < c1; ++c) {
+      const double* p = v + (int64_t)__ldg(sperm + c) * B;
+#pragma unroll
+      for (int e = 0; e < B; ++e) acc[e] += __ldg(p + e);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < B; ++e) acc[e] = 0.0;
+  }
+  bool bad = false;
+#pragma unroll
+  for (int e = 0; e < B; ++e) {
+    double sum = acc[e];
+    if (add) sum += vals[base + 32 * e];
+    bad |= (__double_as_longlong(sum) & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+    vals[base + 32 * e] = sum;
+    if (vals32) vals32[base + 32 * e] = (float)sum;
+  }
+  if (bad) set_err(err, kDevNaN);
+}
+
 __global__ void k_coo_sum_any(const int* __restrict__ seg, const int* __restrict__ perm,
                               const double* __restrict__ v, const int* __restrict__ slot_of, int64_t nnzb,
                               int B, double* __restrict__ vals, float* __restrict__ vals32, int add,
@@ -150,6 +192,22 @@ static Status coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const i
     BAMG_TRY(upload(&A->coo_seg, seg, st));
     A->coo_perm = idx_s;
     idx_s = nullptr;
+    // the same plan in storage-slot order (slots in slice order)
+    {
+      std::vector<int> hperm;
+      BAMG_TRY(download(hperm, A->coo_perm, kept, st));
+      const int64_t nslots = A->nchunks * (int64_t)kSlice;
+      std::vector<int> kof(nslots, -1), soff(nslots + 1, 0), sperm;
+      sperm.reserve((size_t)kept);
+      for (int64_t k = 0; k < A->nnzb; ++k) kof[A->h_slot_of[k]] = (int)k;
+      for (int64_t t = 0; t < nslots; ++t) {
+        const int k = kof[t];
+        if (k >= 0) sperm.insert(sperm.end(), hperm.begin() + seg[k], hperm.begin() + seg[k + 1]);
+        soff[t + 1] = (int)sperm.size();
+      }
+      BAMG_TRY(upload(&A->coo_soff, soff, st));
+      BAMG_TRY(upload(&A->coo_sperm, sperm, st));
+    }
     BAMG_CUDA(cudaStreamSynchronize(st));
     return Status{};
   };
@@ -170,7 +228,12 @@ static Status coo_set_values(bamg_bsr* A, const double* v, int add) {
   if (nt > 0) {
     const unsigned blocks = (unsigned)((nt + 255) / 256);
     const int pm = prof_begin(A->ctx, BAMG_PROF_COO, st);
-    if (B == 9)
+    const int64_t nslots = A->nchunks * (int64_t)kSlice;
+    const unsigned sblocks = (unsigned)((nslots + 127) / 128);
+    if (B == 9 && A->coo_soff)
+      { k_coo_sum_slots<9><<<sblocks, 128, 0, st>>>(A->coo_soff, A->coo_sperm, v, nslots, A->vals, v32, add,
+                                                  A->ctx->d_err); BAMG_COUNT_LAUNCH; }
+    else if (B == 9)
       { k_coo_sum<9><<<blocks, 256, 0, st>>>(A->coo_seg, A->coo_perm, v, A->slot_of, A->nnzb, A->vals, v32, add,
                                            A->ctx->d_err); BAMG_COUNT_LAUNCH; }
     else if (B == 36)

@@ -132,6 +132,8 @@ struct bamg_bsr {
   int* coo_perm = nullptr;   // contributions in (row, col, input order) order
   int* coo_seg = nullptr;    // nnzb + 1 offsets into coo_perm
   int* coo_slot = nullptr;   // per input entry: its block's slot, -1 if ignored (element-by-element path)
+  int* coo_soff = nullptr;   // 32 * nchunks + 1: per storage slot (slice order), offset into coo_sperm
+  int* coo_sperm = nullptr;  // the contributions of each slot, slots in slice order, each in input order
   int64_t block_elems() const { return (int64_t)br * bc; }
   int64_t nslots() const { return nchunks * bamg::kSlice; }
 };
