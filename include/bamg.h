@@ -171,6 +171,15 @@ BAMG_API bamg_status bamg_bsr_coo_scatter_values(bamg_bsr* A, const double* v, i
 /* Sizes and version (any pointer may be NULL). */
 BAMG_API bamg_status bamg_bsr_info(const bamg_bsr* A, int* bs_r, int* bs_c, int64_t* nbr, int64_t* nbc,
                           int64_t* nnzb, uint64_t* version);
+/* Sliced storage of A (Sec. 4.2's blocked layout, padded to 32-row slices):
+ * *stored_slots = block slots held (nnzb plus the padding of every slice to
+ * its longest row); *rows_sorted = 1 when the rows sit in the slices by
+ * decreasing length within windows of 1,024 rows.  Operators from COO
+ * preallocation and Galerkin products are sorted when that removes at least
+ * a tenth of the slots (uneven rows, e.g. Q2's vertex and mid-edge nodes);
+ * prolongators always.  Vectors are indexed by row either way.  Either
+ * pointer may be NULL.  BAMG_ERR_STATE without a pattern. */
+BAMG_API bamg_status bamg_bsr_storage(const bamg_bsr* A, int64_t* stored_slots, int* rows_sorted);
 /* Copy the block pattern out: rowptr (nbr + 1) and colidx (nnzb), device. */
 BAMG_API bamg_status bamg_bsr_get_pattern(const bamg_bsr* A, int32_t* rowptr, int32_t* colidx);
 /* Copy the values out in pattern order: nnzb row-major blocks, device. */

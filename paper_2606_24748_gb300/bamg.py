@@ -93,6 +93,7 @@ _SIGS = {
     "bamg_bsr_coo_preallocate": [_P, _I64, _P, _P],
     "bamg_bsr_coo_set_values": [_P, _P, ctypes.c_int],
     "bamg_bsr_info": [_P, _P, _P, _P, _P, _P, _P],
+    "bamg_bsr_storage": [_P, _P, _P],
     "bamg_bsr_get_pattern": [_P, _P, _P],
     "bamg_bsr_get_values": [_P, _P],
     "bamg_bsr_set_symmetric": [_P, ctypes.c_int],
@@ -294,6 +295,12 @@ def bamg_bsr_info(A) -> dict:
                                ctypes.byref(nnzb), ctypes.byref(ver)), None)
     return {"bs_r": bs_r.value, "bs_c": bs_c.value, "nbr": nbr.value, "nbc": nbc.value, "nnzb": nnzb.value,
             "version": ver.value}
+
+
+def bamg_bsr_storage(A) -> dict:
+    slots, sorted_ = ctypes.c_int64(), ctypes.c_int()
+    _check(lib().bamg_bsr_storage(A, ctypes.byref(slots), ctypes.byref(sorted_)), None)
+    return {"stored_slots": slots.value, "rows_sorted": bool(sorted_.value)}
 
 
 def bamg_bsr_get_pattern(ctx, A, rowptr, colidx):

@@ -140,7 +140,7 @@ void bsr_release(bamg_bsr* A) {
   A->h_slot_of.clear();
 }
 
-Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, bool sort_rows) {
+Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, int sort_rows) {
   cudaStream_t st = A->ctx->stream;
   const int64_t nbr = A->nbr;
   if ((int64_t)rowptr.size() != nbr + 1) return make_status(BAMG_ERR_INVALID, "rowptr size");
@@ -151,11 +151,29 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   std::vector<int> order((size_t)A->nslices * kSlice);
   for (size_t r = 0; r < order.size(); ++r) order[r] = (int64_t)r < nbr ? (int)r : -1;
   auto len = [&](int i) { return i < 0 ? -1 : rowptr[i + 1] - rowptr[i]; };
-  if (sort_rows) {
+  auto stored_chunks = [&](const std::vector<int>& ord) {
+    int64_t c = 0;
+    for (int64_t s = 0; s < A->nslices; ++s) {
+      int w = 0;
+      for (int64_t r = s * kSlice; r < (s + 1) * kSlice; ++r) w = std::max(w, len(ord[r]));
+      c += w;
+    }
+    return c;
+  };
+  if (sort_rows != kSortNever) {
+    std::vector<int> sorted = order;
     constexpr size_t kWindow = 1024;
-    for (size_t w0 = 0; w0 < order.size(); w0 += kWindow) {
-      const size_t w1 = std::min(order.size(), w0 + kWindow);
-      std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) { return len(a) > len(b); });
+    for (size_t w0 = 0; w0 < sorted.size(); w0 += kWindow) {
+      const size_t w1 = std::min(sorted.size(), w0 + kWindow);
+      std::stable_sort(sorted.begin() + w0, sorted.begin() + w1, [&](int a, int b) { return len(a) > len(b); });
+    }
+    // auto: only where the sort removes a tenth of the stored slots or more
+    // (rows of very uneven length, e.g. Q2 vertex and mid-edge nodes); evenly
+    // filled slices keep the identity order and its contiguous vectors
+    if (sort_rows == kSortAlways || 10 * stored_chunks(sorted) <= 9 * stored_chunks(order)) {
+      order = std::move(sorted);
+    } else {
+      sort_rows = kSortNever;
     }
   }
   std::vector<int> sp(A->nslices + 1, 0);
@@ -202,7 +220,7 @@ Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&
   dfree(A->slot_row, st);
   dfree(A->vals, st);
   dfree(A->vals32, st);
-  if (sort_rows) BAMG_TRY(upload(&A->slot_row, order, st));
+  if (sort_rows != kSortNever) BAMG_TRY(upload(&A->slot_row, order, st));
   BAMG_TRY(upload(&A->rowptr, A->h_rowptr, st));
   BAMG_TRY(upload(&A->colidx, A->h_colidx, st));
   BAMG_TRY(upload(&A->slice_ptr, sp, st));
@@ -416,6 +434,14 @@ bamg_status bamg_bsr_info(const bamg_bsr* A, int* bs_r, int* bs_c, int64_t* nbr,
   if (nbc) *nbc = A->nbc;
   if (nnzb) *nnzb = A->nnzb;
   if (version) *version = A->version;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_storage(const bamg_bsr* A, int64_t* stored_slots, int* rows_sorted) {
+  if (!A) return BAMG_ERR_INVALID;
+  if (!A->has_pattern) return BAMG_ERR_STATE;
+  if (stored_slots) *stored_slots = A->nchunks * (int64_t)kSlice;
+  if (rows_sorted) *rows_sorted = A->slot_row ? 1 : 0;
   return BAMG_OK;
 }
 

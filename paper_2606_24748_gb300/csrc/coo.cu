@@ -150,7 +150,7 @@ static Status coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const i
     std::vector<int> rowptr(A->nbr + 1, 0), colidx, seg(1, 0);
     if (n == 0) {
       A->coo_n = 0;
-      BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx)));
+      BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx), kSortAuto));
       return upload(&A->coo_seg, seg, st);
     }
     BAMG_TRY(dalloc(&keys, n, st));
@@ -188,7 +188,7 @@ static Status coo_preallocate(bamg_bsr* A, int64_t n, const int32_t* bi, const i
     if (kept > 0) seg.push_back((int)kept);
     for (int64_t i = 0; i < A->nbr; ++i) rowptr[i + 1] += rowptr[i];
     A->coo_n = n;
-    BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx)));
+    BAMG_TRY(bsr_set_pattern(A, std::move(rowptr), std::move(colidx), kSortAuto));
     BAMG_TRY(upload(&A->coo_seg, seg, st));
     A->coo_perm = idx_s;
     idx_s = nullptr;

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* _
 // one keeps its register count.
 template <int BS, int V, typename T, bool FINAL = false>
 __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict__ sp, const int* __restrict__ col,
-                                                           const T* __restrict__ vals, int64_t n, int64_t nthreads,
+                                                           const T* __restrict__ vals, const int* __restrict__ srow,
+                                                           int64_t n, int64_t nthreads,
                                                            const T* __restrict__ d_in, T* __restrict__ d_out,
                                                            T* __restrict__ x, T* __restrict__ r,
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
@@ -74,12 +75,13 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
-  int64_t i;
+  int64_t pos;
   int sub;
-  row_of_thread<V>(t, i, sub);
+  row_of_thread<V>(t, pos, sub);
   T acc[BS];
-  row_product<BS, BS, V, T, T, T>(sp, col, vals, d_in, i, sub, acc);
-  if (sub != 0 || i >= n) return;
+  row_product<BS, BS, V, T, T, T>(sp, col, vals, d_in, pos, sub, acc);
+  const int64_t i = row_at(srow, pos);
+  if (sub != 0 || i < 0 || i >= n) return;
   T di[BS], ri[BS];
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
@@ -107,7 +109,8 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
 // r = b - A x; d = w Dinv r / theta   (x is read by the product: not written here)
 template <int BS, int V, typename T>
 __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restrict__ sp, const int* __restrict__ col,
-                                                            const T* __restrict__ vals, int64_t n, int64_t nthreads,
+                                                            const T* __restrict__ vals, const int* __restrict__ srow,
+                                                            int64_t n, int64_t nthreads,
                                                             const T* __restrict__ x, const T* __restrict__ b,
                                                             T* __restrict__ r, T* __restrict__ d,
                                                             const T* __restrict__ dinv, const float* __restrict__ w,
@@ -116,12 +119,13 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restric
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
-  int64_t i;
+  int64_t pos;
   int sub;
-  row_of_thread<V>(t, i, sub);
+  row_of_thread<V>(t, pos, sub);
   T acc[BS];
-  row_product<BS, BS, V, T, T, T>(sp, col, vals, x, i, sub, acc);
-  if (sub != 0 || i >= n) return;
+  row_product<BS, BS, V, T, T, T>(sp, col, vals, x, pos, sub, acc);
+  const int64_t i = row_at(srow, pos);
+  if (sub != 0 || i < 0 || i >= n) return;
   T ri[BS], z[BS];
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
@@ -139,7 +143,8 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_rinit(const int* __restric
 // needs every component of the new residual, exchanged through shared memory.
 template <int BS, int VS, typename T, bool FINAL = false>
 __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__ sp, const int* __restrict__ col,
-                                                         const T* __restrict__ vals, int64_t n,
+                                                         const T* __restrict__ vals, const int* __restrict__ srow,
+                                                         int64_t n,
                                                          const T* __restrict__ d_in, T* __restrict__ d_out,
                                                          T* __restrict__ x, T* __restrict__ r,
                                                          const T* __restrict__ dinv, const float* __restrict__ w,
@@ -150,9 +155,9 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
   __shared__ T rs[BS][32];
   const int64_t s = blockIdx.x;
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BS, sub = wp / BS;
-  const int64_t i = s * 32 + lane;
+  const int64_t i = row_at(srow, s * 32 + lane);
   const T acc = row_component<BS, BS, VS, T, T, T>(sp, col, vals, d_in, s, lane, a, sub);
-  const bool lead = sub == 0 && i < n;
+  const bool lead = sub == 0 && i >= 0 && i < n;
   T ri = T(0), di = T(0);
   if (lead) {
     di = d_in[i * BS + a];
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
   if (sub == 0) rs[a][lane] = ri;
   __syncthreads();
   if (!lead) return;
-  const int64_t base = s * (32LL * BS * BS) + lane;
+  const int64_t base = (i >> 5) * (32LL * BS * BS) + (i & 31);
   T z = T(0);
 #pragma unroll
   for (int c = 0; c < BS; ++c) z = fma(__ldg(dinv + base + 32 * (a * BS + c)), rs[c][lane], z);
@@ -179,7 +184,8 @@ __global__ void __launch_bounds__(768) k_cheb_step_split(const int* __restrict__
 
 template <int BS, int VS, typename T>
 __global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict__ sp, const int* __restrict__ col,
-                                                          const T* __restrict__ vals, int64_t n,
+                                                          const T* __restrict__ vals, const int* __restrict__ srow,
+                                                          int64_t n,
                                                           const T* __restrict__ x, const T* __restrict__ b,
                                                           T* __restrict__ r, T* __restrict__ d,
                                                           const T* __restrict__ dinv, const float* __restrict__ w,
@@ -189,9 +195,9 @@ __global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict_
   __shared__ T rs[BS][32];
   const int64_t s = blockIdx.x;
   const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31, a = wp % BS, sub = wp / BS;
-  const int64_t i = s * 32 + lane;
+  const int64_t i = row_at(srow, s * 32 + lane);
   const T acc = row_component<BS, BS, VS, T, T, T>(sp, col, vals, x, s, lane, a, sub);
-  const bool lead = sub == 0 && i < n;
+  const bool lead = sub == 0 && i >= 0 && i < n;
   T ri = T(0);
   if (lead) {
     ri = b[i * BS + a] - acc;
@@ -200,7 +206,7 @@ __global__ void __launch_bounds__(768) k_cheb_rinit_split(const int* __restrict_
   if (sub == 0) rs[a][lane] = ri;
   __syncthreads();
   if (!lead) return;
-  const int64_t base = s * (32LL * BS * BS) + lane;
+  const int64_t base = (i >> 5) * (32LL * BS * BS) + (i & 31);
   T z = T(0);
 #pragma unroll
   for (int c = 0; c < BS; ++c) z = fma(__ldg(dinv + base + 32 * (a * BS + c)), rs[c][lane], z);
@@ -321,11 +327,11 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
     if (BS == 6 && split_for<T>(A)) {
       BAMG_DISPATCH_VS(split_for<T>(A), {
         BAMG_CUDA(launch_k(k_cheb_step_split<BS, VS, T>, dim3((unsigned)A->nslices), dim3(32 * BS * VS), st, 
-            A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
+            A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
             k + 1 < m ? 1 : 0, done));
         BAMG_COUNT_LAUNCH; })
     } else {
-      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, d[k & 1],
+      BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, rows, d[k & 1],
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
                                                      k + 1 < m ? 1 : 0, done)); BAMG_COUNT_LAUNCH; })
     }
@@ -351,11 +357,11 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
   const int pr = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_RINIT_L0 : -1, st);
   if (split) {
     BAMG_DISPATCH_VS(split, {
-      BAMG_CUDA(launch_k(k_cheb_rinit_split<BS, VS, T>, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, p.x, p.b,
+      BAMG_CUDA(launch_k(k_cheb_rinit_split<BS, VS, T>, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, p.x, p.b,
                                                                  p.r, p.d0, p.dinv, L.weights, sc, done));
       BAMG_COUNT_LAUNCH; })
   } else {
-    BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_rinit<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows, p.x, p.b, p.r,
+    BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_rinit<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, rows, p.x, p.b, p.r,
                                                     p.d0, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; })
   }
   prof_end(mg->ctx, pr, st);
@@ -366,13 +372,13 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
     if (split) {
       BAMG_DISPATCH_VS(split, {
         auto kern = last ? k_cheb_step_split<BS, VS, T, true> : k_cheb_step_split<BS, VS, T, false>;
-        BAMG_CUDA(launch_k(kern, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, L.n, d[k & 1],
+        BAMG_CUDA(launch_k(kern, dim3(gs), dim3(32 * BS * VS), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, d[k & 1],
                            d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done));
         BAMG_COUNT_LAUNCH; })
     } else {
       BAMG_DISPATCH_V(lanes_for<T>(A), {
         auto kern = last ? k_cheb_step<BS, V, T, true> : k_cheb_step<BS, V, T, false>;
-        BAMG_CUDA(launch_k(kern, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, L.n, rows,
+        BAMG_CUDA(launch_k(kern, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, rows,
                            d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done));
         BAMG_COUNT_LAUNCH; })
     }
@@ -612,7 +618,8 @@ __global__ void k_cg_first(int64_t m, const double* __restrict__ r, const double
 // q = A p, alpha = rz / (p.q)
 template <int V>
 __global__ void __launch_bounds__(256, 8) k_cg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
-                                                       const double* __restrict__ vals, int64_t n, int64_t nthreads,
+                                                       const double* __restrict__ vals, const int* __restrict__ srow,
+                                                       int64_t n, int64_t nthreads,
                                                        const double* __restrict__ p, double* __restrict__ q,
                                                        CgState* s, double* partials, unsigned* counter) {
   pdl_enter();
@@ -624,12 +631,13 @@ __global__ void __launch_bounds__(256, 8) k_cg_Ap(const int* __restrict__ sp, co
   for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
-    int64_t i;
+    int64_t pos;
     int sub;
-    row_of_thread<V>(t, i, sub);
+    row_of_thread<V>(t, pos, sub);
     double acc[3];
-    row_product<3, 3, V, double, double, double>(sp, col, vals, p, i, sub, acc);
-    if (sub == 0 && i < n) {
+    row_product<3, 3, V, double, double, double>(sp, col, vals, p, pos, sub, acc);
+    const int64_t i = row_at(srow, pos);
+    if (sub == 0 && i >= 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         q[i * 3 + a] = acc[a];
@@ -713,7 +721,8 @@ __global__ void k_cg_p(int64_t m, const double* __restrict__ z, double* __restri
 // ||b - A x||^2 into s->pq (final true residual)
 template <int V>
 __global__ void __launch_bounds__(256, 8) k_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
-                                                               const double* __restrict__ vals, int64_t n,
+                                                               const double* __restrict__ vals,
+                                                               const int* __restrict__ srow, int64_t n,
                                                                int64_t nthreads, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* out_norm2,
                                                                double* partials, unsigned* counter) {
@@ -725,12 +734,13 @@ __global__ void __launch_bounds__(256, 8) k_true_residual(const int* __restrict_
   for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
-    int64_t i;
+    int64_t pos;
     int sub;
-    row_of_thread<V>(t, i, sub);
+    row_of_thread<V>(t, pos, sub);
     double acc[3];
-    row_product<3, 3, V, double, double, double>(sp, col, vals, x, i, sub, acc);
-    if (sub == 0 && i < n) {
+    row_product<3, 3, V, double, double, double>(sp, col, vals, x, pos, sub, acc);
+    const int64_t i = row_at(srow, pos);
+    if (sub == 0 && i >= 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double t = b[i * 3 + a] - acc[a];
@@ -752,7 +762,7 @@ static Status cg_iteration(bamg_mg* mg, double* r, double* z, cudaStream_t st) {
   CgState* s = mg->cg;
   const int* done = &s->done;
   const int pa = prof_begin(ctx, BAMG_PROF_CG_AP, st);
-  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_cg_Ap<V>, dim3(deal_grid(k_cg_Ap<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cp, mg->cq, s,
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_cg_Ap<V>, dim3(deal_grid(k_cg_Ap<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, rows, mg->cp, mg->cq, s,
                                                   ctx->d_partials, ctx->d_counters + 2)); BAMG_COUNT_LAUNCH; })
   prof_end(ctx, pa, st);
   const int px = prof_begin(ctx, BAMG_PROF_CG_XR, st);
@@ -875,7 +885,7 @@ Status cg_epilogue(bamg_mg* mg, const double* b, double* x, double* true_r2, cud
   if (x) BAMG_CUDA(cudaMemcpyAsync(x, mg->cx, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   const bamg_bsr* A = L0.A;
   const int64_t rows = row_threads(A);
-  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_true_residual<V>, dim3(deal_grid(k_true_residual<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, L0.n, rows, mg->cx, b,
+  BAMG_DISPATCH_V(A->vec, { BAMG_CUDA(launch_k(k_true_residual<V>, dim3(deal_grid(k_true_residual<V>, ctx->sm_count, rows)), dim3(256), st, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, rows, mg->cx, b,
                                                           true_r2, ctx->d_partials, ctx->d_counters + 7)); BAMG_COUNT_LAUNCH; })
   BAMG_CUDA(cudaGetLastError());
   return Status{};

@@ -142,6 +142,14 @@ __device__ __forceinline__ void row_of_thread(int64_t t, int64_t& row, int& sub)
   sub = (int)(t - row * V);
 }
 
+// Block row stored at row position pos.  Slices sorted by row length carry
+// the map (srow; -1 at the padding positions past the last row); otherwise
+// the position is the row.  Vectors and block-diagonal inverses stay indexed
+// by row in either case.
+__device__ __forceinline__ int64_t row_at(const int* __restrict__ srow, int64_t pos) {
+  return srow ? (int64_t)__ldg(srow + pos) : pos;
+}
+
 // Balanced deal of warp tasks (32 consecutive virtual threads) for the
 // one-wave reducing row kernels: CTA c takes a contiguous run of tasks, the
 // runs differing in length by at most one, and its warps take every W-th

@@ -371,7 +371,11 @@ void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int
 // windows of 1,024 rows (sliced ELL with sorting), so that rows of equal
 // length share slices and little padding is stored; kernels then map each
 // row position to its row through slot_row.
-Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, bool sort_rows = false);
+// Row order of the sliced storage: identity, rows sorted by decreasing length
+// within windows of 1,024 rows (slot_row maps positions to rows), or sorted
+// only where that removes at least a tenth of the stored slots.
+constexpr int kSortNever = 0, kSortAlways = 1, kSortAuto = 2;
+Status bsr_set_pattern(bamg_bsr* A, std::vector<int>&& rowptr, std::vector<int>&& colidx, int sort_rows = kSortNever);
 Status bsr_ensure_fp32(bamg_bsr* A);   // refresh vals32 if the version changed
 void bsr_release(bamg_bsr* A);
 

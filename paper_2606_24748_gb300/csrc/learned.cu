@@ -437,16 +437,19 @@ __global__ void k_round_params(const float* __restrict__ theta, float* __restric
 template <int BS, typename TM>
 __global__ void k_block_features(const int* __restrict__ rowptr, const int* __restrict__ slice_ptr,
                                  const int* __restrict__ col, const TM* __restrict__ vals,
-                                 const double* __restrict__ dinv, int64_t n, float level, float* __restrict__ X) {
+                                 const int* __restrict__ srow, const double* __restrict__ dinv, int64_t n,
+                                 int64_t npos, float level, float* __restrict__ X) {
   constexpr int B = BS * BS;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int64_t s = i >> 5;
-  const int lane = (int)(i & 31);
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= npos) return;
+  const int64_t i = row_at(srow, pos);
+  if (i < 0 || i >= n) return;
+  const int64_t s = pos >> 5;
+  const int lane = (int)(pos & 31);
   const int c0 = slice_ptr[s];
   const int len = rowptr[i + 1] - rowptr[i];
   double D[BS][BS];
-  const int64_t db = (i >> 5) * (32LL * B) + lane;
+  const int64_t db = (i >> 5) * (32LL * B) + (i & 31);
 #pragma unroll
   for (int a = 0; a < BS; ++a)
 #pragma unroll
@@ -519,18 +522,20 @@ __global__ void k_apply_dinv(int64_t n, const double* __restrict__ dinv, const d
 // q = A u per row; num_i += <r_i, q_i>, den_i += ||q_i||^2
 template <int BS, int V>
 __global__ void __launch_bounds__(kRowThreads) k_damping_accum(const int* __restrict__ sp, const int* __restrict__ col,
-                                                               const double* __restrict__ vals, int64_t n,
+                                                               const double* __restrict__ vals,
+                                                               const int* __restrict__ srow, int64_t n,
                                                                int64_t nthreads, const double* __restrict__ u,
                                                                const double* __restrict__ r, double* __restrict__ num,
                                                                double* __restrict__ den) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nthreads) return;
-  int64_t i;
+  int64_t pos;
   int sub;
-  row_of_thread<V>(t, i, sub);
+  row_of_thread<V>(t, pos, sub);
   double q[BS];
-  row_product<BS, BS, V, double, double, double>(sp, col, vals, u, i, sub, q);
-  if (sub != 0 || i >= n) return;
+  row_product<BS, BS, V, double, double, double>(sp, col, vals, u, pos, sub, q);
+  const int64_t i = row_at(srow, pos);
+  if (sub != 0 || i < 0 || i >= n) return;
   double a = 0.0, b = 0.0;
 #pragma unroll
   for (int k = 0; k < BS; ++k) {
@@ -551,16 +556,18 @@ __global__ void k_damping_finish(int64_t n, const double* __restrict__ num, cons
 
 // r = b - A x, ||r||^2 (stationary iteration)
 __global__ void __launch_bounds__(kRowThreads) k_residual_store(const int* __restrict__ sp, const int* __restrict__ col,
-                                                                const double* __restrict__ vals, int64_t n,
+                                                                const double* __restrict__ vals,
+                                                                const int* __restrict__ srow, int64_t n,
                                                                 int64_t rows_pad, const double* __restrict__ x,
                                                                 const double* __restrict__ b, double* __restrict__ r,
                                                                 double* out_norm2, double* partials, unsigned* counter) {
   double local[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad; i += stride) {
+  for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < rows_pad; pos += stride) {
     double acc[3];
-    row_product<3, 3, 1, double, double, double>(sp, col, vals, x, i, 0, acc);
-    if (i < n) {
+    row_product<3, 3, 1, double, double, double>(sp, col, vals, x, pos, 0, acc);
+    const int64_t i = row_at(srow, pos);
+    if (i >= 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const double t = b[i * 3 + a] - acc[a];
@@ -625,17 +632,18 @@ Status mg_learned_weights(bamg_mg* mg, int l, cudaStream_t st) {
   Level& L = mg->levels[l];
   if (!mg->mlp || !L.learned_w) return Status{};
   const bamg_bsr* A = L.A;
-  const unsigned g = (unsigned)((L.n + 127) / 128);
+  const int64_t npos = A->nslices * kSlice;
+  const unsigned g = (unsigned)std::max<int64_t>(1, (npos + 127) / 128);
   if (L.bs == 3) {
     if (A->vals64_stale)
-      { k_block_features<3, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, L.dinv, L.n, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
+      { k_block_features<3, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, A->slot_row, L.dinv, L.n, npos, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
     else
-      { k_block_features<3, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, L.dinv, L.n, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
+      { k_block_features<3, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.dinv, L.n, npos, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
   } else {
     if (A->vals64_stale)
-      { k_block_features<6, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, L.dinv, L.n, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
+      { k_block_features<6, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, A->slot_row, L.dinv, L.n, npos, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
     else
-      { k_block_features<6, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, L.dinv, L.n, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
+      { k_block_features<6, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.dinv, L.n, npos, (float)l, L.feat); BAMG_COUNT_LAUNCH; }
   }
   BAMG_CUDA(cudaGetLastError());
   return mlp_forward(mg->mlp, L.feat, L.n, L.learned_w, st);
@@ -773,17 +781,18 @@ bamg_status bamg_mg_block_features(bamg_mg* mg, int level, float* X) {
   Level& L = mg->levels[level];
   const bamg_bsr* A = L.A;
   cudaStream_t st = mg->ctx->stream;
-  const unsigned g = (unsigned)((L.n + 127) / 128);
+  const int64_t npos = A->nslices * kSlice;
+  const unsigned g = (unsigned)std::max<int64_t>(1, (npos + 127) / 128);
   if (L.bs == 3) {
     if (A->vals64_stale)
-      { k_block_features<3, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, L.dinv, L.n, (float)level, X); BAMG_COUNT_LAUNCH; }
+      { k_block_features<3, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, A->slot_row, L.dinv, L.n, npos, (float)level, X); BAMG_COUNT_LAUNCH; }
     else
-      { k_block_features<3, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, L.dinv, L.n, (float)level, X); BAMG_COUNT_LAUNCH; }
+      { k_block_features<3, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.dinv, L.n, npos, (float)level, X); BAMG_COUNT_LAUNCH; }
   } else {
     if (A->vals64_stale)
-      { k_block_features<6, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, L.dinv, L.n, (float)level, X); BAMG_COUNT_LAUNCH; }
+      { k_block_features<6, float><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals32, A->slot_row, L.dinv, L.n, npos, (float)level, X); BAMG_COUNT_LAUNCH; }
     else
-      { k_block_features<6, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, L.dinv, L.n, (float)level, X); BAMG_COUNT_LAUNCH; }
+      { k_block_features<6, double><<<g, 128, 0, st>>>(A->rowptr, A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.dinv, L.n, npos, (float)level, X); BAMG_COUNT_LAUNCH; }
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? BAMG_OK : fail(mg->ctx, cuda_status(e, "features"));
@@ -821,10 +830,10 @@ bamg_status bamg_mg_smoother_targets(bamg_mg* mg, const double* Bk, int k, float
         const unsigned gr = (unsigned)((rows + kRowThreads - 1) / kRowThreads);
         if (L.bs == 3) {
           { k_apply_dinv<3><<<g, 128, 0, st>>>(L.n, L.dinv, L.r, L.d0); BAMG_COUNT_LAUNCH; }
-          BAMG_DISPATCH_V(A->vec, { k_damping_accum<3, V><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L.n, rows, L.d0, L.r, num[l], den[l]); BAMG_COUNT_LAUNCH; })
+          BAMG_DISPATCH_V(A->vec, { k_damping_accum<3, V><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.n, rows, L.d0, L.r, num[l], den[l]); BAMG_COUNT_LAUNCH; })
         } else {
           { k_apply_dinv<6><<<g, 128, 0, st>>>(L.n, L.dinv, L.r, L.d0); BAMG_COUNT_LAUNCH; }
-          BAMG_DISPATCH_V(A->vec, { k_damping_accum<6, V><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L.n, rows, L.d0, L.r, num[l], den[l]); BAMG_COUNT_LAUNCH; })
+          BAMG_DISPATCH_V(A->vec, { k_damping_accum<6, V><<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L.n, rows, L.d0, L.r, num[l], den[l]); BAMG_COUNT_LAUNCH; })
         }
         s = mg_restrict_fp64(mg, l, st);
       }
@@ -881,13 +890,13 @@ bamg_status bamg_mg_stationary(bamg_mg* mg, const double* b, double* x, int its,
     const unsigned gv = (unsigned)((m + 255) / 256);
     const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + kRowThreads - 1) / kRowThreads, 1216));
     BAMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * m, st));
-    { k_residual_store<<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, x, b, mg->cr, norms, ctx->d_partials, ctx->d_counters + 8); BAMG_COUNT_LAUNCH; }
+    { k_residual_store<<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, rows, x, b, mg->cr, norms, ctx->d_partials, ctx->d_counters + 8); BAMG_COUNT_LAUNCH; }
     Status s;
     for (int k = 0; k < its && s.ok(); ++k) {
       s = mg_precond(mg, mg->cr, mg->cz, st);
       if (!s.ok()) break;
       { k_axpy<<<gv, 256, 0, st>>>(m, mg->cz, x); BAMG_COUNT_LAUNCH; }
-      { k_residual_store<<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, rows, x, b, mg->cr, norms + k + 1, ctx->d_partials, ctx->d_counters + 8); BAMG_COUNT_LAUNCH; }
+      { k_residual_store<<<gr, kRowThreads, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, rows, x, b, mg->cr, norms + k + 1, ctx->d_partials, ctx->d_counters + 8); BAMG_COUNT_LAUNCH; }
     }
     std::vector<double> h;
     if (s.ok()) s = download(h, norms, its + 1, st);

@@ -281,6 +281,7 @@ __global__ void k_start_vector(double* __restrict__ v, int64_t n) {
 template <int BS, int V, typename TM>
 __global__ void __launch_bounds__(256, 8) k_power_step(const int* __restrict__ slice_ptr,
                                                             const int* __restrict__ col, const TM* __restrict__ vals,
+                                                            const int* __restrict__ srow,
                                                             const int* __restrict__ diag_slot,
                                                             const double* __restrict__ dinv, int scalar_diag,
                                                             const float* __restrict__ wts,
@@ -297,12 +298,13 @@ __global__ void __launch_bounds__(256, 8) k_power_step(const int* __restrict__ s
   for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
-    int64_t row;
+    int64_t pos;
     int sub;
-    row_of_thread<V>(t, row, sub);
+    row_of_thread<V>(t, pos, sub);
     double acc[BS];
-    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w_in, row, sub, acc);
-    if (sub == 0 && row < n) {
+    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w_in, pos, sub, acc);
+    const int64_t row = row_at(srow, pos);
+    if (sub == 0 && row >= 0 && row < n) {
       double z[BS];
       if (scalar_diag) {
         const int64_t ds = diag_slot[row];
@@ -335,6 +337,7 @@ __global__ void __launch_bounds__(256, 8) k_power_step(const int* __restrict__ s
 template <int BS, int VS, typename TM>
 __global__ void __launch_bounds__(768) k_power_step_split(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const TM* __restrict__ vals,
+                                                          const int* __restrict__ srow,
                                                           const double* __restrict__ dinv,
                                                           const float* __restrict__ wts,
                                                           const double* __restrict__ w_in,
@@ -350,9 +353,9 @@ __global__ void __launch_bounds__(768) k_power_step_split(const int* __restrict_
     __syncthreads();  // the previous slice's readers of `as` are done
     if (sub == 0) as[a][lane] = acc * sc;
     __syncthreads();
-    const int64_t i = s * 32 + lane;
-    if (sub == 0 && i < n) {
-      const int64_t base = s * (32LL * BS * BS) + lane;
+    const int64_t i = row_at(srow, s * 32 + lane);
+    if (sub == 0 && i >= 0 && i < n) {
+      const int64_t base = (i >> 5) * (32LL * BS * BS) + (i & 31);
       double t = 0.0;
 #pragma unroll
       for (int c = 0; c < BS; ++c) t = fma(dinv[base + 32 * (a * BS + c)], as[c][lane], t);
@@ -370,6 +373,7 @@ __global__ void __launch_bounds__(768) k_power_step_split(const int* __restrict_
 template <int BS, int V, typename TM>
 __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_ptr,
                                                           const int* __restrict__ col, const TM* __restrict__ vals,
+                                                          const int* __restrict__ srow,
                                                           const int* __restrict__ diag_slot, int scalar_diag,
                                                           const float* __restrict__ wts,
                                                           const double* __restrict__ w, int64_t n, int64_t nthreads,
@@ -383,12 +387,13 @@ __global__ void __launch_bounds__(256) k_rayleigh(const int* __restrict__ slice_
   for (int64_t g = t0 + (threadIdx.x >> 5); g < t1; g += blockDim.x >> 5) {
     const int64_t t = g * 32 + (threadIdx.x & 31);
     if (t >= nthreads) continue;  // rows are whole slices: never taken
-    int64_t row;
+    int64_t pos;
     int sub;
-    row_of_thread<V>(t, row, sub);
+    row_of_thread<V>(t, pos, sub);
     double acc[BS];
-    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w, row, sub, acc);
-    if (sub == 0 && row < n) {
+    row_product<BS, BS, V, TM, double, double>(slice_ptr, col, vals, w, pos, sub, acc);
+    const int64_t row = row_at(srow, pos);
+    if (sub == 0 && row >= 0 && row < n) {
       const int64_t ds = diag_slot[row];
       double wi[BS];
 #pragma unroll
@@ -442,17 +447,17 @@ static Status power_impl(bamg_mg* mg, const bamg_bsr* A, const TM* vals, const d
     if (split) {
       const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(A->nslices, 1216));
       BAMG_DISPATCH_VS(split, {
-        k_power_step_split<BS, VS, TM><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, dinv, wts,
+        k_power_step_split<BS, VS, TM><<<gs, 32 * BS * VS, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, dinv, wts,
                                                                      w[it & 1], w[(it + 1) & 1], nin, norms + (it & 1),
                                                                      n, A->nslices, ctx->d_partials, ctx->d_counters);
         BAMG_COUNT_LAUNCH; })
       continue;
     }
-    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<deal_grid(k_power_step<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, dinv,
+    BAMG_DISPATCH_V(lanes_for<TM>(A), { k_power_step<BS, V, TM><<<deal_grid(k_power_step<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, A->diag_slot, dinv,
                                                     scalar_diag ? 1 : 0, scalar_diag ? nullptr : wts, w[it & 1], w[(it + 1) & 1], nin,
                                                     norms + (it & 1), n, rows, ctx->d_partials, ctx->d_counters); BAMG_COUNT_LAUNCH; })
   }
-  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<deal_grid(k_rayleigh<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->diag_slot, scalar_diag ? 1 : 0,
+  BAMG_DISPATCH_V(lanes_for<TM>(A), { k_rayleigh<BS, V, TM><<<deal_grid(k_rayleigh<BS, V, TM>, ctx->sm_count, rows), 256, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, A->diag_slot, scalar_diag ? 1 : 0,
                                                 scalar_diag ? nullptr : wts, w[mg->opts.power_its & 1], n, rows, ctx->d_partials,
                                                 ctx->d_counters + 1, out_scal, mg->opts.cheb_lower,
                                                 mg->opts.cheb_upper, mg->opts.cheb_degree); BAMG_COUNT_LAUNCH; })
@@ -812,7 +817,7 @@ static Status mg_setup_impl(bamg_mg* mg, bamg_bsr* A, const double* coords, cons
       std::vector<int> zrow(zc.size());
       for (int64_t i = 0; i < L.n; ++i)
         for (int z = zr[i]; z < zr[i + 1]; ++z) zrow[z] = (int)i;
-      BAMG_TRY(bsr_set_pattern(P, std::move(zr), std::move(zc), true));  // rows of 1..8 blocks: sorted slices
+      BAMG_TRY(bsr_set_pattern(P, std::move(zr), std::move(zc), kSortAlways));  // rows of 1..8 blocks: sorted slices
       BAMG_TRY(upload(&L.zrow, zrow, st));
       BAMG_TRY(upload(&L.agg, agg, st));
       BAMG_TRY(upload(&L.q, Q, st));

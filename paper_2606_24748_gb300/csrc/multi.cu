@@ -80,18 +80,20 @@ __global__ void __launch_bounds__(256) k_mcheb_init(int64_t n, int glog, int kp,
 // x += d_in; r -= A d_in; if has_next: d_out = c1 d_in + c2 w Dinv r
 template <int BS, typename T>
 __global__ void __launch_bounds__(256) k_mcheb_step(const int* __restrict__ sp, const int* __restrict__ col,
-                                                    const T* __restrict__ vals, int64_t n, int glog, int kp,
+                                                    const T* __restrict__ vals, const int* __restrict__ srow,
+                                                    int64_t n, int glog, int kp,
                                                     const T* __restrict__ d_in, T* __restrict__ d_out,
                                                     T* __restrict__ x, T* __restrict__ r,
                                                     const T* __restrict__ dinv, const float* __restrict__ w,
                                                     const double* __restrict__ scal, int k, int has_next,
                                                     const int* done) {
   BAMG_DONE_RETURN
-  int64_t i;
+  int64_t pos;
   int c0;
-  if (!row_cols(n, glog, i, c0)) return;
+  if (!row_cols(n, glog, pos, c0)) return;
   T acc[BS][4];
-  row_product4<BS, BS, T>(sp, col, vals, d_in, kp, i, c0, acc);
+  row_product4<BS, BS, T>(sp, col, vals, d_in, kp, pos, c0, acc);
+  const int64_t i = row_at(srow, pos);
   T di[BS][4];
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
@@ -125,17 +127,19 @@ __global__ void __launch_bounds__(256) k_mcheb_step(const int* __restrict__ sp, 
 // r = b - A x; d = w Dinv r / theta
 template <int BS, typename T>
 __global__ void __launch_bounds__(256) k_mcheb_rinit(const int* __restrict__ sp, const int* __restrict__ col,
-                                                     const T* __restrict__ vals, int64_t n, int glog, int kp,
+                                                     const T* __restrict__ vals, const int* __restrict__ srow,
+                                                     int64_t n, int glog, int kp,
                                                      const T* __restrict__ x, const T* __restrict__ b,
                                                      T* __restrict__ r, T* __restrict__ d,
                                                      const T* __restrict__ dinv, const float* __restrict__ w,
                                                      const double* __restrict__ scal, const int* done) {
   BAMG_DONE_RETURN
-  int64_t i;
+  int64_t pos;
   int c0;
-  if (!row_cols(n, glog, i, c0)) return;
+  if (!row_cols(n, glog, pos, c0)) return;
   T acc[BS][4];
-  row_product4<BS, BS, T>(sp, col, vals, x, kp, i, c0, acc);
+  row_product4<BS, BS, T>(sp, col, vals, x, kp, pos, c0, acc);
+  const int64_t i = row_at(srow, pos);
 #pragma unroll
   for (int a = 0; a < BS; ++a) {
     const int64_t o = (i * BS + a) * kp + c0;
@@ -294,7 +298,8 @@ __global__ void __launch_bounds__(256) k_mcg_first(int64_t m, int kp, const doub
 
 // q = A p, alpha_j = rz_j / (p_j . q_j)
 __global__ void __launch_bounds__(256) k_mcg_Ap(const int* __restrict__ sp, const int* __restrict__ col,
-                                                const double* __restrict__ vals, int64_t n, int glog, int kp,
+                                                const double* __restrict__ vals, const int* __restrict__ srow,
+                                                int64_t n, int glog, int kp,
                                                 const double* __restrict__ p, double* __restrict__ q,
                                                 CgMultiState* s, double* partials, unsigned* counter) {
   if (s->all_done) return;
@@ -303,9 +308,10 @@ __global__ void __launch_bounds__(256) k_mcg_Ap(const int* __restrict__ sp, cons
   const int64_t nt = n << glog;
   const int c0 = (int)(threadIdx.x & ((1 << glog) - 1)) * 4;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t >> glog;
+    const int64_t pos = t >> glog;
     double acc[3][4];
-    row_product4<3, 3, double>(sp, col, vals, p, kp, i, c0, acc);
+    row_product4<3, 3, double>(sp, col, vals, p, kp, pos, c0, acc);
+    const int64_t i = row_at(srow, pos);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int64_t o = (i * 3 + a) * kp + c0;
@@ -409,7 +415,8 @@ __global__ void __launch_bounds__(256) k_mcg_p(int64_t m, int kp, const double* 
 
 // ||b_j - A x_j||^2 (b read from the caller's k-column array)
 __global__ void __launch_bounds__(256) k_mcg_true_residual(const int* __restrict__ sp, const int* __restrict__ col,
-                                                           const double* __restrict__ vals, int64_t n, int glog,
+                                                           const double* __restrict__ vals,
+                                                           const int* __restrict__ srow, int64_t n, int glog,
                                                            int kp, int k, const double* __restrict__ x,
                                                            const double* __restrict__ B, CgMultiState* s,
                                                            double* partials, unsigned* counter) {
@@ -418,9 +425,10 @@ __global__ void __launch_bounds__(256) k_mcg_true_residual(const int* __restrict
   const int64_t nt = n << glog;
   const int c0 = (int)(threadIdx.x & ((1 << glog) - 1)) * 4;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t >> glog;
+    const int64_t pos = t >> glog;
     double acc[3][4];
-    row_product4<3, 3, double>(sp, col, vals, x, kp, i, c0, acc);
+    row_product4<3, 3, double>(sp, col, vals, x, kp, pos, c0, acc);
+    const int64_t i = row_at(srow, pos);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -476,7 +484,7 @@ Status msmooth_down(bamg_mg* mg, int l, int kp, const int* done, cudaStream_t st
   { k_mcheb_init<BS, T><<<g, 256, 0, st>>>(L.n, glog, kp, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; }
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k < m; ++k) {
-    k_mcheb_step<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, glog, kp, d[k & 1], d[(k + 1) & 1],
+    k_mcheb_step<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, glog, kp, d[k & 1], d[(k + 1) & 1],
                                            p.x, p.r, p.dinv, L.weights, sc, k, k + 1 < m ? 1 : 0, done);
     BAMG_COUNT_LAUNCH;
   }
@@ -493,11 +501,11 @@ Status msmooth_up(bamg_mg* mg, int l, int kp, const int* done, cudaStream_t st) 
   const unsigned g = grid_for(L.n << glog);
   const double* sc = mg->scal + (int64_t)l * kScalarsPerLevel;
   const int m = mg->opts.cheb_degree;
-  { k_mcheb_rinit<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, glog, kp, p.x, p.b, p.r, p.d0,
+  { k_mcheb_rinit<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, glog, kp, p.x, p.b, p.r, p.d0,
                                             p.dinv, L.weights, sc, done); BAMG_COUNT_LAUNCH; }
   T* d[2] = {p.d0, p.d1};
   for (int k = 0; k + 1 < m; ++k) {
-    k_mcheb_step<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, L.n, glog, kp, d[k & 1], d[(k + 1) & 1],
+    k_mcheb_step<BS, T><<<g, 256, 0, st>>>(A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, glog, kp, d[k & 1], d[(k + 1) & 1],
                                            p.x, p.r, p.dinv, L.weights, sc, k, 1, done);
     BAMG_COUNT_LAUNCH;
   }
@@ -710,7 +718,7 @@ Status mcg_iteration(bamg_mg* mg, int kp, cudaStream_t st) {
   const int glog = ilog2(kp / 4);
   CgMultiState* s = W.st;
   const int* done = &s->all_done;
-  { k_mcg_Ap<<<stride_grid(L0.n << glog), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, glog, kp, W.cp, W.cq,
+  { k_mcg_Ap<<<stride_grid(L0.n << glog), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, glog, kp, W.cp, W.cq,
                                                        s, W.partials, W.counters + 0); BAMG_COUNT_LAUNCH; }
   { k_mcg_xr<<<stride_grid(m * kp), 256, 0, st>>>(m, kp, W.cp, W.cq, W.cx, W.cr, s, W.partials, W.counters + 1); BAMG_COUNT_LAUNCH; }
   BAMG_TRY(mprecond(mg, kp, W.cr, W.cz, done, st));
@@ -798,7 +806,7 @@ Status multi_cg(bamg_mg* mg, const double* B, double* X, int k, double rtol, int
     BAMG_CUDA(cudaStreamSynchronize(st));
   }
   if (X) { k_munpack<double><<<grid_for(m * k), 256, 0, st>>>(m, k, kp, W.cx, X); BAMG_COUNT_LAUNCH; }
-  { k_mcg_true_residual<<<stride_grid(L0.n << glog), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, L0.n, glog, kp, k,
+  { k_mcg_true_residual<<<stride_grid(L0.n << glog), 256, 0, st>>>(A->slice_ptr, A->sell_col, A->vals, A->slot_row, L0.n, glog, kp, k,
                                                                   W.cx, B, s, W.partials, W.counters + 5); BAMG_COUNT_LAUNCH; }
   BAMG_CUDA(cudaMemcpyAsync(W.host, s, sizeof(CgMultiState), cudaMemcpyDeviceToHost, st));
   BAMG_TRY(check_device_error(ctx));

@@ -48,19 +48,21 @@ static Status scratch_addresses(double** partials, unsigned** counter) {
 template <int BS, int V>
 __global__ void __launch_bounds__(kRowThreads) k_residual_norm_noalloc(const int* __restrict__ sp,
                                                                        const int* __restrict__ col,
-                                                                       const double* __restrict__ vals, int64_t n,
+                                                                       const double* __restrict__ vals,
+                                                                       const int* __restrict__ srow, int64_t n,
                                                                        int64_t nthreads, const double* __restrict__ x,
                                                                        const double* __restrict__ b, double* norm,
                                                                        double* partials, unsigned* counter) {
   double local[1] = {0.0};
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < nthreads) {
-    int64_t i;
+    int64_t pos;
     int sub;
-    row_of_thread<V>(t, i, sub);
+    row_of_thread<V>(t, pos, sub);
     double acc[BS];
-    row_product<BS, BS, V, double, double, double>(sp, col, vals, x, i, sub, acc);
-    if (sub == 0 && i < n) {
+    row_product<BS, BS, V, double, double, double>(sp, col, vals, x, pos, sub, acc);
+    const int64_t i = row_at(srow, pos);
+    if (sub == 0 && i >= 0 && i < n) {
 #pragma unroll
       for (int a = 0; a < BS; ++a) {
         const double r = b[i * BS + a] - acc[a];
@@ -93,11 +95,11 @@ static Status residual_norm_noalloc(const bamg_bsr* A, const double* x, const do
   BAMG_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   if (A->br == 3) {
     BAMG_DISPATCH_V(A->vec, { k_residual_norm_noalloc<3, V><<<(unsigned)blocks, kRowThreads, 0, st>>>(
-                                  A->slice_ptr, A->sell_col, A->vals, A->nbr, nthreads, x, b, norm, partials,
+                                  A->slice_ptr, A->sell_col, A->vals, A->slot_row, A->nbr, nthreads, x, b, norm, partials,
                                   counter); BAMG_COUNT_LAUNCH; })
   } else {
     BAMG_DISPATCH_V(A->vec, { k_residual_norm_noalloc<6, V><<<(unsigned)blocks, kRowThreads, 0, st>>>(
-                                  A->slice_ptr, A->sell_col, A->vals, A->nbr, nthreads, x, b, norm, partials,
+                                  A->slice_ptr, A->sell_col, A->vals, A->slot_row, A->nbr, nthreads, x, b, norm, partials,
                                   counter); BAMG_COUNT_LAUNCH; })
   }
   BAMG_CUDA(cudaGetLastError());

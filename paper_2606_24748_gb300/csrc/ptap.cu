@@ -299,7 +299,7 @@ Status ptap_build(bamg_bsr* A, bamg_bsr* P, bool want_ac, bamg_ptap** plan_out, 
     pl->Ac = Ac;
     Ac->symmetric = pl->symmetric;
     std::vector<int> crow_copy = cr, ccol_copy = ccol;
-    BAMG_TRY(bsr_set_pattern(Ac, std::move(crow_copy), std::move(ccol_copy)));
+    BAMG_TRY(bsr_set_pattern(Ac, std::move(crow_copy), std::move(ccol_copy), kSortAuto));
     pl->ac_pid = Ac->pattern_id;
     const auto& cslot = Ac->h_slot_of;
     const auto& crp = Ac->h_rowptr;

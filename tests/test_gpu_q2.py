@@ -5,6 +5,7 @@ import pytest
 import torch
 
 from oracle import krylov
+from oracle import learned as OL
 from oracle import multigrid as omg
 from paper_2606_24748_gb300 import bamg as B
 from workloads.elasticity import body_force
@@ -42,3 +43,76 @@ def test_q2_hierarchy_and_cycle_match_oracle(ne):
         assert rel(x.cpu().numpy(), xr) <= 1e-7
     finally:
         gp.close()
+
+
+def unsorted_slots(rowptr) -> int:
+    """Slots of the plain sliced layout: every 32-row slice padded to its
+    longest row (the storage without a row sort)."""
+    lens = np.diff(rowptr)
+    pad = np.zeros(-(-lens.size // 32) * 32, dtype=np.int64)
+    pad[:lens.size] = lens
+    return int(pad.reshape(-1, 32).max(axis=1).sum()) * 32
+
+
+def test_q2_rows_sorted_by_length_in_every_row_kernel():
+    """Q2's vertex and mid-edge rows (125 and fewer blocks) alternate along x:
+    the library stores the fine operator with rows sorted by length (slot_row
+    maps positions to rows).  Every row kernel that walks it by position must
+    still write by row: the SpMV, the multi-vector cycle (bitwise equal to
+    single cycles), the allocation-free residual, the CG exit residual, the
+    mixed-precision cycle and the learned features."""
+    ne = 12
+    mesh, _, Aref = problem(ne, order=2)
+    h = hierarchy(ne, order=2)
+    gp = GpuProblem(ne, order=2)
+    gq = None
+    try:
+        st = B.bamg_bsr_storage(gp.A)
+        plain = unsorted_slots(Aref.rowptr)
+        assert st["rows_sorted"]
+        assert Aref.nnzb <= st["stored_slots"] <= 0.9 * plain
+        A1, _ = B.bamg_mg_get_level(gp.mg, 1)
+        assert B.bamg_bsr_storage(A1)["rows_sorted"]  # the 6x6 split kernels too
+        rng = np.random.default_rng(5)
+        xh = rng.standard_normal(mesh.n_dofs)
+        y = torch.empty(mesh.n_dofs, dtype=torch.float64, device="cuda")
+        B.bamg_bsr_spmv(gp.ctx, gp.A, torch.from_numpy(xh).cuda(), y)
+        assert rel(y.cpu().numpy(), Aref.scalar() @ xh) <= 1e-14
+        # multi-vector cycle against single-vector cycles, bit for bit
+        B.bamg_mg_set_lanes(gp.ctx, gp.mg, 1)
+        k = 5
+        Bh = np.ascontiguousarray(rng.standard_normal((mesh.n_dofs, k)))
+        X = torch.zeros(Bh.shape, dtype=torch.float64, device="cuda")
+        B.bamg_mg_vcycle_multi(gp.ctx, gp.mg, torch.from_numpy(Bh).cuda(), X, k)
+        for j in range(k):
+            x = torch.zeros(mesh.n_dofs, dtype=torch.float64, device="cuda")
+            B.bamg_vcycle(gp.ctx, gp.mg, torch.from_numpy(np.ascontiguousarray(Bh[:, j])).cuda(), x)
+            assert torch.equal(X[:, j], x), j
+            assert rel(x.cpu().numpy(), omg.vcycle(h, Bh[:, j])) <= TOL64, j
+        # residual norms: allocation-free entry and the CG exit
+        f = body_force(mesh)
+        fd = torch.from_numpy(f).cuda()
+        x = torch.zeros_like(fd)
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, fd, x, 1e-8, 200)
+        res = float(np.linalg.norm(f - Aref.scalar() @ x.cpu().numpy()))
+        assert abs(out["true_rnorm"] - res) <= 1e-9 * np.linalg.norm(f)
+        norm = torch.empty(1, dtype=torch.float64, device="cuda")
+        B.bamg_bsr_residual_norm_noalloc(gp.ctx, gp.A, x, fd, norm)
+        torch.cuda.synchronize()
+        assert abs(float(norm.item()) - out["true_rnorm"]) <= 1e-12 * out["true_rnorm"]
+        # learned-smoother features, row by row
+        for l in range(h.n_levels - 1):
+            L = h.levels[l]
+            Xf = torch.empty((L.A.nbr, 8), dtype=torch.float32, device="cuda")
+            B.bamg_mg_block_features(gp.ctx, gp.mg, l, Xf)
+            assert np.allclose(Xf.cpu().numpy(), OL.block_features(L.A, l, L.Dinv), rtol=1e-5, atol=1e-6), l
+        # the mixed form (FP32 cycle) reaches the same tolerance
+        gq = GpuProblem(ne, order=2, precision=B.BAMG_FP32)
+        xq = torch.zeros_like(fd)
+        outq = B.bamg_cg_solve(gq.ctx, gq.mg, fd, xq, 1e-8, 200)
+        assert outq["converged"] and abs(outq["iterations"] - out["iterations"]) <= 2
+        assert outq["true_rnorm"] <= 1.05e-8 * np.linalg.norm(f)
+    finally:
+        gp.close()
+        if gq is not None:
+            gq.close()
