@@ -47,9 +47,13 @@ RTOL = 1e-8
 MAXIT = 500
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/traffic_cheb_step_l0_64cubed_fp64.md), with a fingerprint of the
-# kernel's sources at capture time; reported as null once they change.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.8e6, "15694f44b0da4a5d")}
-TRAFFIC_SOURCES = ("paper_2606_24748_gb300/csrc/device.cuh", "paper_2606_24748_gb300/csrc/cycle.cu")
+# kernel's source at capture time; reported as null once it changes.  The
+# source is device.cuh (the row products) and the span of cycle.cu from the
+# block-diagonal apply through the end of the fused Chebyshev step.
+TRAFFIC = {("cheb_step_l0", 64, False): (589.8e6, "c3cb8b49ea4e5836")}
+TRAFFIC_SOURCES = (("paper_2606_24748_gb300/csrc/device.cuh", None, None),
+                   ("paper_2606_24748_gb300/csrc/cycle.cu", "__device__ __forceinline__ void dinv_apply",
+                    "// r = b - A x; d = w Dinv r / theta"))
 
 
 def parse():
@@ -446,9 +450,13 @@ KERNEL_TABLE_STEPS = 3  # steps of the untimed all-slot pass behind kernel_ms
 def sources_fingerprint() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    for f, start, end in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        if start is not None:
+            i = text.index(start)
+            text = text[i:text.index(end, i)]
+        h.update(text.encode())
     return h.hexdigest()[:16]
 
 

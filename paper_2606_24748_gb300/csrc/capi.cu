@@ -34,13 +34,14 @@ static cudaError_t record(cudaEvent_t e, cudaStream_t st) {
   return g_capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
 }
 
-int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st) {
+int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st, int count) {
   if (!ctx || !ctx->prof.on || slot < 0 || !((ctx->prof.mask >> slot) & 1u)) return -1;
   int idx = -1;
   ProfPair* q = prof_slot_pair(ctx, &idx);
   if (!q) return -1;
   q->slot = slot;
   q->pos = ctx->prof.pos;
+  q->count = count;
   if (record(q->a, st) != cudaSuccess) {
     cudaGetLastError();
     return -1;
@@ -69,7 +70,7 @@ void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
       p.ms[q.slot] += ms;
-      p.n[q.slot] += 1;
+      p.n[q.slot] += q.count;
     } else {
       cudaGetLastError();
     }

@@ -322,8 +322,9 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   { BAMG_CUDA(launch_k(k_cheb_init<BS, T>, dim3(gn), dim3(kRowThreads), st, L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; }
   prof_end(mg->ctx, pi, st);
   T* d[2] = {p.d0, p.d1};
+  // the m pre-smoothing steps are consecutive launches of one kernel: one bracket
+  const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st, m);
   for (int k = 0; k < m; ++k) {
-    const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st);
     if (BS == 6 && split_for<T>(A)) {
       BAMG_DISPATCH_VS(split_for<T>(A), {
         BAMG_CUDA(launch_k(k_cheb_step_split<BS, VS, T>, dim3((unsigned)A->nslices), dim3(32 * BS * VS), st, 
@@ -335,8 +336,8 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
                                                      k + 1 < m ? 1 : 0, done)); BAMG_COUNT_LAUNCH; })
     }
-    prof_end(mg->ctx, pm, st);
   }
+  prof_end(mg->ctx, pm, st);
   prof_end(mg->ctx, pw, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};
@@ -434,15 +435,18 @@ static Status transfer_prof(bamg_mg* mg, const bamg_bsr* M, const T* vals, const
 
 // Warps per component of a coarse level's smoother: the lanes autotuner times
 // the plain product, and the fused Chebyshev kernels of the same matrix can
-// prefer another split.  Time the level's own pre- and post-smoothing with 1,
-// 2 and 4 warps per component and keep the fastest.  Only for levels the
-// autotuner put in the split form; the level's vectors are scratch here.
+// prefer another form.  Time the level's own pre- and post-smoothing with 1,
+// 2 and 4 warps per component and keep the fastest; a level the autotuner
+// left in the lanes form keeps that form as a candidate too (FP32 products
+// of a 64^3 first coarse level chose 16 lanes per row, where the fused
+// smoother and the power steps were faster split).  The power steps follow
+// the level's choice.  The level's vectors are scratch here.
 template <typename T>
 static Status tune_smoother_split(bamg_mg* mg, int l) {
   Level& L = mg->levels[l];
   bamg_bsr* A = L.A;
   int& split = std::is_same<T, double>::value ? A->split : A->split32;
-  if (L.bs != 6 || A->bc != 6 || split < 1 || split > 4) return Status{};
+  if (L.bs != 6 || A->bc != 6 || split < 0 || split > 4) return Status{};
   cudaStream_t st = mg->ctx->stream;
   cudaEvent_t e0, e1;
   BAMG_CUDA(cudaEventCreate(&e0));
@@ -454,7 +458,8 @@ static Status tune_smoother_split(bamg_mg* mg, int l) {
   const int keep = split;
   float best = 1e30f;
   int best_vs = keep;
-  for (int vs : {1, 2, 4}) {
+  for (int vs : {0, 1, 2, 4}) {
+    if (vs == 0 && keep != 0) continue;  // the lanes form only where the autotuner chose it
     split = vs;
     for (int w = 0; w < 2 && s.ok(); ++w) {
       s = smooth_down<6, T>(mg, l, nullptr, st);

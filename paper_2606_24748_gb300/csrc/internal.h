@@ -55,7 +55,8 @@ inline void count_launch() {
 struct ProfPair {
   cudaEvent_t a = nullptr, b = nullptr;
   int slot = 0;
-  int pos = 0;  // CG iteration position (graph-owned pairs)
+  int pos = 0;    // CG iteration position (graph-owned pairs)
+  int count = 1;  // launches of the slot's kernel between a and b
 };
 
 struct Prof {
@@ -360,7 +361,10 @@ enum DevErr : int { kDevOk = 0, kDevNaN = 1, kDevBreakdown = 2, kDevTimeout = 3,
 Status check_device_error(bamg_ctx* ctx);  // synchronizes the stream
 
 // Profiling marks (no-ops when profiling is off).  Return / take an index.
-int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st);
+// Brackets `count` consecutive launches of the slot's kernel (back-to-back
+// launches of one kernel share a bracket: each bracket costs the kernels it
+// encloses their programmatic overlap with their neighbours).
+int prof_begin(bamg_ctx* ctx, int slot, cudaStream_t st, int count = 1);
 void prof_end(bamg_ctx* ctx, int idx, cudaStream_t st);
 void prof_harvest(bamg_ctx* ctx, std::vector<ProfPair>& pairs, size_t count, int active_ap, int active_vc);
 
