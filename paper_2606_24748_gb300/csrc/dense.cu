@@ -426,6 +426,7 @@ __global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, c
 // CTA (256 threads, 4 outputs each); with lower_only, tiles above the
 // diagonal are skipped.
 constexpr int kGemmBatch = 8;
+constexpr int kGemmSplit = 4;  // at most this many K parts per output tile
 // tri: which operand is triangular, so that whole zero tiles of the K loop
 // are skipped: 0 none, 1 A lower (K tiles <= ti), 2 A upper (>= ti),
 // 3 op(B) upper, i.e. B lower and transposed (<= tj).
@@ -437,18 +438,29 @@ struct GemmBatch {
   int tri[kGemmBatch];
 };
 
+// Split K (ksplit > 1, blockIdx.z = item * ksplit + part): each part sums
+// its share of the K tiles into a partial tile in `part`; the part that
+// arrives last at the tile's counter (an atomic count, no waiting) adds the
+// partials in part order, writes C and zeroes the counter for the next
+// launch.  The order of the sums is fixed, so results are reproducible.  A
+// chunk product has 66 to 242 output tiles for 152 SMs; the split fills them.
 template <bool kTransB>
-__global__ void __launch_bounds__(256) k_chunk_gemm(GemmBatch g, int s, double alpha, double beta, int lower_only) {
+__global__ void __launch_bounds__(256) k_chunk_gemm(GemmBatch g, int s, double alpha, double beta, int lower_only,
+                                                    int ksplit, double* __restrict__ part, unsigned* __restrict__ ctr) {
   const int ti = blockIdx.y, tj = blockIdx.x;
   if (lower_only && tj > ti) return;
-  double* __restrict__ C = g.C[blockIdx.z];
-  const double* __restrict__ A = g.A[blockIdx.z];
-  const double* __restrict__ B = g.B[blockIdx.z];
+  const int item = (int)blockIdx.z / ksplit, kp = (int)blockIdx.z - item * ksplit;
+  double* __restrict__ C = g.C[item];
+  const double* __restrict__ A = g.A[item];
+  const double* __restrict__ B = g.B[item];
   __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
+  __shared__ unsigned last;
   const int tid = threadIdx.x, c = tid % kT, r0 = tid / kT;
-  const int tri = g.tri[blockIdx.z];
-  const int k0 = tri == kTriAUpper ? ti : 0;
-  const int k1 = tri == kTriALower ? ti + 1 : (tri == kTriBtUpper ? tj + 1 : s / kT);
+  const int tri = g.tri[item];
+  const int kb = tri == kTriAUpper ? ti : 0;
+  const int ke = tri == kTriALower ? ti + 1 : (tri == kTriBtUpper ? tj + 1 : s / kT);
+  const int len = (ke - kb + ksplit - 1) / ksplit;
+  const int k0 = kb + kp * len, k1 = min(ke, k0 + len);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int kt = k0; kt < k1; ++kt) {
     __syncthreads();
@@ -464,6 +476,29 @@ __global__ void __launch_bounds__(256) k_chunk_gemm(GemmBatch g, int s, double a
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = fma(As[r0 + 8 * q][l], bv, acc[q]);
     }
+  }
+  if (ksplit > 1) {
+    const int ntl = s / kT;
+    const int64_t tile = ((int64_t)item * ntl + ti) * ntl + tj;
+    double* mine = part + ((int64_t)item * ksplit + kp) * ntl * ntl * (kT * kT) + ((int64_t)ti * ntl + tj) * (kT * kT);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mine[(r0 + 8 * q) * kT + c] = acc[q];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(ctr + tile, 1u) == (unsigned)(ksplit - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = 0.0;
+      for (int pp = 0; pp < ksplit; ++pp) {
+        const double* pt = part + ((int64_t)item * ksplit + pp) * ntl * ntl * (kT * kT) + ((int64_t)ti * ntl + tj) * (kT * kT);
+        t += __ldcg(pt + (r0 + 8 * q) * kT + c);
+      }
+      acc[q] = t;
+    }
+    if (tid == 0) ctr[tile] = 0u;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -650,7 +685,8 @@ struct GemmItem {
 
 template <bool kTransB>
 static Status gemm_batch(const std::vector<GemmItem>& items, int s, double alpha, double beta, int lower_only,
-                         cudaStream_t st) {
+                         const CoarseDense& D, int sm_count, cudaStream_t st) {
+  const int ntl = s / kT;
   for (size_t i0 = 0; i0 < items.size(); i0 += kGemmBatch) {
     GemmBatch g = {};
     const int cnt = (int)std::min<size_t>(kGemmBatch, items.size() - i0);
@@ -660,8 +696,11 @@ static Status gemm_batch(const std::vector<GemmItem>& items, int s, double alpha
       g.B[q] = items[i0 + q].B;
       g.tri[q] = items[i0 + q].tri;
     }
-    const dim3 grid((unsigned)(s / kT), (unsigned)(s / kT), (unsigned)cnt);
-    k_chunk_gemm<kTransB><<<grid, 256, 0, st>>>(g, s, alpha, beta, lower_only);
+    // about two CTAs per SM: split K when the output tiles alone are fewer
+    const int tiles = cnt * (lower_only ? ntl * (ntl + 1) / 2 : ntl * ntl);
+    const int ksplit = std::min(kGemmSplit, std::max(1, (2 * sm_count + tiles - 1) / tiles));
+    const dim3 grid((unsigned)ntl, (unsigned)ntl, (unsigned)(cnt * ksplit));
+    k_chunk_gemm<kTransB><<<grid, 256, 0, st>>>(g, s, alpha, beta, lower_only, ksplit, D.gpart, D.gctr);
     BAMG_COUNT_LAUNCH;
   }
   BAMG_CUDA(cudaGetLastError());
@@ -683,6 +722,9 @@ static Status band_factor(bamg_mg* mg, cudaStream_t st) {
     BAMG_TRY(dalloc(&D.b64, npad, st));
     BAMG_TRY(dalloc(&D.x64, npad, st));
     BAMG_TRY(dalloc(&D.dinv_tiles, 2 * (int64_t)ntl * kT * kT, st));
+    BAMG_TRY(dalloc(&D.gpart, (int64_t)kGemmBatch * kGemmSplit * ntl * ntl * kT * kT, st));
+    BAMG_TRY(dalloc(&D.gctr, (int64_t)kGemmBatch * ntl * ntl, st));
+    BAMG_CUDA(cudaMemsetAsync(D.gctr, 0, sizeof(unsigned) * kGemmBatch * ntl * ntl, st));
   }
   auto Dk = [&](int k) { return D.D + k * ss; };
   auto Wk = [&](int k) { return D.Wb + k * ss; };
@@ -716,7 +758,7 @@ static Status band_factor(bamg_mg* mg, cudaStream_t st) {
     std::vector<GemmItem> syrk, panel;
     if (kt > 0) syrk.push_back({Dk(kt), BC(kt - 1), BC(kt - 1), kTriNone});
     if (kb >= 0 && kb < nc - 1) syrk.push_back({Dk(kb), BC(kb + 1), BC(kb + 1), kTriNone});
-    if (!syrk.empty()) BAMG_TRY(gemm_batch<true>(syrk, s, -1.0, 1.0, 1, st));
+    if (!syrk.empty()) BAMG_TRY(gemm_batch<true>(syrk, s, -1.0, 1.0, 1, D, ctx->sm_count, st));
     if (kt >= 0 && kb >= 0)
       BAMG_TRY(cooperative_factor(ctx, st, Dk(kt), Wk(kt), s, ntl, D.dinv_tiles, Dk(kb), Wk(kb), dt1));
     else
@@ -726,14 +768,14 @@ static Status band_factor(bamg_mg* mg, cudaStream_t st) {
     // B_k = A_{k+1,k} W_k^T, C_k = A_{k-1,k} W_k^T (W_k lower triangular)
     if (kt >= 0) panel.push_back({BC(kt), D.Sub + kt * ss, Wk(kt), kTriBtUpper});
     if (kb >= 0) panel.push_back({BC(kb), D.Sup + (kb - 1) * ss, Wk(kb), kTriBtUpper});
-    BAMG_TRY(gemm_batch<true>(panel, s, 1.0, 0.0, 0, st));
+    BAMG_TRY(gemm_batch<true>(panel, s, 1.0, 0.0, 0, D, ctx->sm_count, st));
   }
   // middle chunk: both Schur complements, then its factor
   {
     std::vector<GemmItem> syrk;
     if (t > 0) syrk.push_back({Dk(t), BC(t - 1), BC(t - 1), kTriNone});
     if (t + 1 < nc) syrk.push_back({Dk(t), BC(t + 1), BC(t + 1), kTriNone});
-    for (auto& it : syrk) BAMG_TRY(gemm_batch<true>({it}, s, -1.0, 1.0, 1, st));  // same output: one at a time
+    for (auto& it : syrk) BAMG_TRY(gemm_batch<true>({it}, s, -1.0, 1.0, 1, D, ctx->sm_count, st));  // same output: one at a time
     BAMG_TRY(cooperative_factor(ctx, st, Dk(t), Wk(t), s, ntl, D.dinv_tiles));
     { k_transpose_dense<<<tg, 256, 0, st>>>(Wk(t), Wt(t), s); BAMG_COUNT_LAUNCH; }
   }
@@ -743,8 +785,8 @@ static Status band_factor(bamg_mg* mg, cudaStream_t st) {
   for (int k = t; k + 1 < nc; ++k) nn.push_back({D.Mtb + k * ss, Wk(k), BC(k + 1), kTriALower});  // Mt_k = W_k C_{k+1}
   for (int k = 0; k < t; ++k) nt.push_back({D.Nb + k * ss, Wt(k), BC(k), kTriAUpper});          // N_k = W_k^T B_k^T
   for (int k = t + 1; k < nc; ++k) nt.push_back({D.Ntb + k * ss, Wt(k), BC(k), kTriAUpper});     // Nt_k = W_k^T C_k^T
-  BAMG_TRY(gemm_batch<false>(nn, s, 1.0, 0.0, 0, st));
-  BAMG_TRY(gemm_batch<true>(nt, s, 1.0, 0.0, 0, st));
+  BAMG_TRY(gemm_batch<false>(nn, s, 1.0, 0.0, 0, D, ctx->sm_count, st));
+  BAMG_TRY(gemm_batch<true>(nt, s, 1.0, 0.0, 0, D, ctx->sm_count, st));
   prof_end(ctx, pm, st);
   BAMG_CUDA(cudaGetLastError());
   return Status{};

@@ -206,6 +206,8 @@ struct CoarseDense {
   int nc = 0, s = 0;
   double *D = nullptr, *Sub = nullptr, *Sup = nullptr, *Wb = nullptr, *Wtb = nullptr, *Bb = nullptr,
          *Mb = nullptr, *Nb = nullptr, *Mtb = nullptr, *Ntb = nullptr;
+  double* gpart = nullptr;   // split-K partial tiles of the chunk products
+  unsigned* gctr = nullptr;  // per-tile arrival counts of the split (zero between launches)
 };
 
 struct Level {

@@ -616,10 +616,11 @@ static void mg_release(bamg_mg* mg) {
   for (double** p : {&mg->cx, &mg->cr, &mg->cp, &mg->cq, &mg->cz, &mg->czold, &mg->scal, &mg->power_w[0],
                      &mg->power_w[1], &mg->coarse.M, &mg->coarse.Wt, &mg->coarse.b64, &mg->coarse.x64,
                      &mg->coarse.D, &mg->coarse.Sub, &mg->coarse.Sup, &mg->coarse.Wb, &mg->coarse.Wtb,
-                     &mg->coarse.Bb, &mg->coarse.Mb, &mg->coarse.Nb, &mg->coarse.Mtb, &mg->coarse.Ntb})
+                     &mg->coarse.Bb, &mg->coarse.Mb, &mg->coarse.Nb, &mg->coarse.Mtb, &mg->coarse.Ntb, &mg->coarse.gpart})
     dfree(*p, st);
   dfree(mg->coarse.rows, st);
   dfree(mg->coarse.dinv_tiles, st);
+  dfree(mg->coarse.gctr, st);
   dfree(mg->cg, st);
   if (mg->cg_host) cudaFreeHost(mg->cg_host);
   cudaStreamSynchronize(st);
