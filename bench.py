@@ -50,7 +50,7 @@ MAXIT = 500
 # kernel's source at capture time; reported as null once it changes.  The
 # source is device.cuh (the row products) and the span of cycle.cu from the
 # block-diagonal apply through the end of the fused Chebyshev step.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.8e6, "c3cb8b49ea4e5836")}
+TRAFFIC = {("cheb_step_l0", 64, False): (589.9e6, "f5d61c966d397dd7")}
 TRAFFIC_SOURCES = (("paper_2606_24748_gb300/csrc/device.cuh", None, None),
                    ("paper_2606_24748_gb300/csrc/cycle.cu", "__device__ __forceinline__ void dinv_apply",
                     "// r = b - A x; d = w Dinv r / theta"))

@@ -34,10 +34,12 @@ __device__ __forceinline__ void dinv_apply(const T* __restrict__ dinv, int64_t i
 #define BAMG_DONE_RETURN \
   if (done && *done) return;
 
-// r = b; d = w Dinv b / theta; x = 0
-template <int BS, typename T>
-__global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* __restrict__ b, T* __restrict__ r,
-                                                           T* __restrict__ d, T* __restrict__ x,
+// r = b; d = w Dinv b / theta; x = 0.  The mixed form's finest level reads
+// the FP64 right-hand side itself (TB = double) and keeps its float copy in
+// bcopy, in place of a separate conversion launch.
+template <int BS, typename T, typename TB = T>
+__global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const TB* __restrict__ b, T* __restrict__ bcopy,
+                                                           T* __restrict__ r, T* __restrict__ d, T* __restrict__ x,
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
                                                            const double* __restrict__ scal, const int* done) {
   pdl_enter();
@@ -46,7 +48,10 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_init(int64_t n, const T* _
   if (i >= n) return;
   T bi[BS], z[BS];
 #pragma unroll
-  for (int a = 0; a < BS; ++a) bi[a] = b[i * BS + a];
+  for (int a = 0; a < BS; ++a) {
+    bi[a] = (T)b[i * BS + a];
+    if (bcopy) bcopy[i * BS + a] = bi[a];
+  }
   dinv_apply<BS, T>(dinv, i, bi, z);
   const T f = (T)(scal[kInvTheta] * (w ? (double)w[i] : 1.0));
 #pragma unroll
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
                                                            T* __restrict__ x, T* __restrict__ r,
                                                            const T* __restrict__ dinv, const float* __restrict__ w,
                                                            const double* __restrict__ scal, int k, int has_next,
-                                                           const int* done) {
+                                                           double* __restrict__ xout, const int* done) {
   pdl_enter();
   BAMG_DONE_RETURN
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -98,10 +103,15 @@ __global__ void __launch_bounds__(kRowThreads) k_cheb_step(const int* __restrict
 #pragma unroll
     for (int a = 0; a < BS; ++a) {
       const T dn = fma(c1, di[a], c2 * z[a]);
-      if constexpr (FINAL)
-        x[i * BS + a] = (x[i * BS + a] + di[a]) + dn;
-      else
+      if constexpr (FINAL) {
+        const T xn = (x[i * BS + a] + di[a]) + dn;
+        if (xout)  // the mixed form's finest level: the cycle's FP64 result
+          xout[i * BS + a] = (double)xn;
+        else
+          x[i * BS + a] = xn;
+      } else {
         d_out[i * BS + a] = dn;
+      }
     }
   }
 }
@@ -307,8 +317,10 @@ LevelPtrs<float> level_ptrs<float>(Level& L) { return ptrs32(L); }
 // CTAs (two slices) halve it against 128-thread ones.
 constexpr int kChebThreads = 64;
 
+// b64 (mixed form, finest level): the FP64 right-hand side, converted by the
+// first kernel; p.b then receives its float copy.
 template <int BS, typename T>
-static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
+static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st, const double* b64 = nullptr) {
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
@@ -319,7 +331,14 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   const int m = mg->opts.cheb_degree;
   const int pw = prof_begin(mg->ctx, l == 0 ? -1 : BAMG_PROF_SMOOTH_COARSE, st);
   const int pi = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_L0_VECTOR : -1, st);
-  { BAMG_CUDA(launch_k(k_cheb_init<BS, T>, dim3(gn), dim3(kRowThreads), st, L.n, p.b, p.r, p.d0, p.x, p.dinv, L.weights, sc, done)); BAMG_COUNT_LAUNCH; }
+  if (b64) {
+    BAMG_CUDA(launch_k(k_cheb_init<BS, T, double>, dim3(gn), dim3(kRowThreads), st, L.n, b64, p.b, p.r, p.d0, p.x,
+                       p.dinv, L.weights, sc, done));
+  } else {
+    BAMG_CUDA(launch_k(k_cheb_init<BS, T>, dim3(gn), dim3(kRowThreads), st, L.n, (const T*)p.b, (T*)nullptr, p.r,
+                       p.d0, p.x, p.dinv, L.weights, sc, done));
+  }
+  BAMG_COUNT_LAUNCH;
   prof_end(mg->ctx, pi, st);
   T* d[2] = {p.d0, p.d1};
   // the m pre-smoothing steps are consecutive launches of one kernel: one bracket
@@ -334,7 +353,7 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
     } else {
       BAMG_DISPATCH_V(lanes_for<T>(A), { BAMG_CUDA(launch_k(k_cheb_step<BS, V, T>, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, rows, d[k & 1],
                                                      d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k,
-                                                     k + 1 < m ? 1 : 0, done)); BAMG_COUNT_LAUNCH; })
+                                                     k + 1 < m ? 1 : 0, (double*)nullptr, done)); BAMG_COUNT_LAUNCH; })
     }
   }
   prof_end(mg->ctx, pm, st);
@@ -343,8 +362,10 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st) 
   return Status{};
 }
 
+// x64 (mixed form, finest level, degree >= 2): the last step writes the
+// cycle's result there in FP64 instead of updating p.x.
 template <int BS, typename T>
-static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
+static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st, double* x64 = nullptr) {
   Level& L = mg->levels[l];
   auto p = level_ptrs<T>(L);
   const bamg_bsr* A = L.A;
@@ -380,7 +401,8 @@ static Status smooth_up(bamg_mg* mg, int l, const int* done, cudaStream_t st) {
       BAMG_DISPATCH_V(lanes_for<T>(A), {
         auto kern = last ? k_cheb_step<BS, V, T, true> : k_cheb_step<BS, V, T, false>;
         BAMG_CUDA(launch_k(kern, dim3(gr), dim3(kChebThreads), st, A->slice_ptr, A->sell_col, p.Avals, A->slot_row, L.n, rows,
-                           d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, done));
+                           d[k & 1], d[(k + 1) & 1], p.x, p.r, p.dinv, L.weights, sc, k, 1, last ? x64 : nullptr,
+                           done));
         BAMG_COUNT_LAUNCH; })
     }
     prof_end(mg->ctx, pm, st);
@@ -495,7 +517,7 @@ Status mg_tune_smoothers(bamg_mg* mg) {
 }
 
 template <typename T>
-Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
+Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st, const double* b64, double* x64) {
   const int nl = (int)mg->levels.size();
   for (int l = 0; l + 1 < nl; ++l) {
     Level& L = mg->levels[l];
@@ -503,7 +525,7 @@ Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
     auto p = level_ptrs<T>(L);
     auto pc = level_ptrs<T>(C);
     if (L.bs == 3) {
-      BAMG_TRY((smooth_down<3, T>(mg, l, done, st)));
+      BAMG_TRY((smooth_down<3, T>(mg, l, done, st, l == 0 ? b64 : nullptr)));
       BAMG_TRY((transfer_prof<6, 3, T>(mg, L.R, p.Rvals, p.r, pc.b, 0, done, st)));
     } else {
       BAMG_TRY((smooth_down<6, T>(mg, l, done, st)));
@@ -522,7 +544,7 @@ Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
     auto pc = level_ptrs<T>(mg->levels[l + 1]);
     if (L.bs == 3) {
       BAMG_TRY((transfer_prof<3, 6, T>(mg, L.P, p.Pvals, pc.x, p.x, 1, done, st)));
-      BAMG_TRY((smooth_up<3, T>(mg, l, done, st)));
+      BAMG_TRY((smooth_up<3, T>(mg, l, done, st, l == 0 ? x64 : nullptr)));
     } else {
       BAMG_TRY((transfer_prof<6, 6, T>(mg, L.P, p.Pvals, pc.x, p.x, 1, done, st)));
       BAMG_TRY((smooth_up<6, T>(mg, l, done, st)));
@@ -531,7 +553,7 @@ Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st) {
   return Status{};
 }
 
-template Status vcycle_on<double>(bamg_mg*, const int*, cudaStream_t);
+template Status vcycle_on<double>(bamg_mg*, const int*, cudaStream_t, const double*, double*);
 
 Status mg_smooth_down_fp64(bamg_mg* mg, int l, cudaStream_t st) {
   return mg->levels[l].bs == 3 ? smooth_down<3, double>(mg, l, nullptr, st) : smooth_down<6, double>(mg, l, nullptr, st);
@@ -542,7 +564,7 @@ Status mg_restrict_fp64(bamg_mg* mg, int l, cudaStream_t st) {
   if (L.bs == 3) return transfer<6, 3, double>(L.R, L.R->vals, L.r, mg->levels[l + 1].b, 0, nullptr, st);
   return transfer<6, 6, double>(L.R, L.R->vals, L.r, mg->levels[l + 1].b, 0, nullptr, st);
 }
-template Status vcycle_on<float>(bamg_mg*, const int*, cudaStream_t);
+template Status vcycle_on<float>(bamg_mg*, const int*, cudaStream_t, const double*, double*);
 
 // z = M r for FP64 vectors r (read) and z (written); in the mixed form the
 // cycle runs on float copies.
@@ -550,7 +572,13 @@ static Status precond(bamg_mg* mg, const double* r, double* z, const int* done, 
   Level& L0 = mg->levels[0];
   const int64_t m = L0.n * L0.bs;
   const unsigned g = (unsigned)((m + 255) / 256);
-  if (mg->opts.precision == BAMG_FP32) {
+  // the conversions to and from the float cycle ride in its first and last
+  // kernels where those are the finest level's Chebyshev kernels (3x3
+  // blocks, a coarser level, degree >= 2)
+  const bool fold = L0.bs == 3 && mg->levels.size() > 1 && mg->opts.cheb_degree >= 2;
+  if (mg->opts.precision == BAMG_FP32 && fold) {
+    BAMG_TRY(vcycle_on<float>(mg, done, st, r, z));
+  } else if (mg->opts.precision == BAMG_FP32) {
     int pc = prof_begin(mg->ctx, BAMG_PROF_L0_VECTOR, st);
     { BAMG_CUDA(launch_k(k_cast_done<double, float>, dim3(g), dim3(256), st, m, r, L0.b32, done)); BAMG_COUNT_LAUNCH; }
     prof_end(mg->ctx, pc, st);

@@ -404,7 +404,10 @@ Status coarse_apply(bamg_mg* mg, const T* b, T* x, const int* done, cudaStream_t
 template <typename T>
 Status coarse_apply_multi(bamg_mg* mg, int kp, const T* b, T* x, double* work, const int* done, cudaStream_t st);
 template <typename T>
-Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st);  // levels[0].b(32) -> levels[0].x(32)
+// levels[0].b(32) -> levels[0].x(32); with b64 / x64 (finest level of 3x3
+// blocks, degree >= 2) the FP64 input is read and the FP64 result written by
+// the finest level's first and last kernels.
+Status vcycle_on(bamg_mg* mg, const int* done, cudaStream_t st, const double* b64 = nullptr, double* x64 = nullptr);
 Status power_lambda(bamg_mg* mg, int l, bool scalar_diag, double* out_scalar_slot, cudaStream_t st);
 void mg_release_graphs(bamg_mg* mg);
 void mg_release_multi(bamg_mg* mg);               // multi-right-hand-side work area
