@@ -81,6 +81,52 @@ def test_coo_rejects_out_of_range_index():
         B.bamg_ctx_destroy(ctx)
 
 
+@pytest.mark.parametrize("case", ["empty", "all_dropped", "single", "one_long_row"])
+def test_coo_degenerate_streams(case):
+    """Blocked COO (Sec. 3.4) on the degenerate streams: no entries, entries
+    that all carry a negative index (dropped), one contribution in the last
+    row, and one row of many duplicates beside empty rows.  Pattern and
+    values as the oracle's, the product A x as the oracle's (zero where A is
+    empty), in INSERT and ADD mode."""
+    rng = np.random.default_rng(11)
+    br = bc = 3
+    nbr, nbc = 40, 40
+    if case == "empty":
+        bi = bj = np.zeros(0, dtype=np.int32)
+    elif case == "all_dropped":
+        bi = np.full(10, -1, dtype=np.int32)
+        bj = np.arange(10, dtype=np.int32)
+    elif case == "single":
+        bi = np.array([nbr - 1], dtype=np.int32)
+        bj = np.array([0], dtype=np.int32)
+    else:
+        bi = np.full(300, 5, dtype=np.int32)
+        bj = rng.integers(0, nbc, 300).astype(np.int32)
+    v = rng.standard_normal((bi.size, br, bc))
+    ref = coo_assemble_blocks(nbr, nbc, br, bc, bi, bj, v)
+    ctx = B.bamg_ctx_create(torch.cuda.current_stream())
+    A = B.bamg_bsr_create(ctx, br, bc, nbr, nbc)
+    try:
+        B.bamg_bsr_coo_preallocate(ctx, A, torch.from_numpy(bi).cuda(), torch.from_numpy(bj).cuda())
+        vt = torch.from_numpy(v.reshape(-1)).cuda()
+        for add, scale in ((0, 1.0), (1, 2.0)):
+            B.bamg_bsr_coo_set_values(ctx, A, vt, add)
+            got = read_bsr(ctx, A)
+            assert same_pattern(got, ref)
+            assert got.nnzb == ref.nnzb
+            if ref.nnzb:
+                assert rel(got.vals, scale * ref.vals) <= 1e-15
+        B.bamg_bsr_coo_set_values(ctx, A, vt, 0)
+        x = rng.standard_normal(nbc * bc)
+        y = torch.full((nbr * br,), 7.0, dtype=torch.float64, device="cuda")
+        B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).cuda(), y)
+        yref = ref.scalar() @ x
+        assert np.allclose(y.cpu().numpy(), yref, rtol=1e-14, atol=1e-14 * max(1.0, np.abs(yref).max(initial=0.0)))
+    finally:
+        B.bamg_bsr_destroy(A)
+        B.bamg_ctx_destroy(ctx)
+
+
 def test_general_galerkin_product_through_the_abi():
     from oracle.galerkin import galerkin
     rng = np.random.default_rng(11)
