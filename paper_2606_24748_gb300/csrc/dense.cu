@@ -426,7 +426,7 @@ __global__ void k_tri_mm(const double* __restrict__ Wm, int64_t ld, int64_t n, c
 // CTA (256 threads, 4 outputs each); with lower_only, tiles above the
 // diagonal are skipped.
 constexpr int kGemmBatch = 8;
-constexpr int kGemmSplit = 4;  // at most this many K parts per output tile
+constexpr int kGemmSplit = 8;  // at most this many K parts per output tile
 // tri: which operand is triangular, so that whole zero tiles of the K loop
 // are skipped: 0 none, 1 A lower (K tiles <= ti), 2 A upper (>= ti),
 // 3 op(B) upper, i.e. B lower and transposed (<= tj).
@@ -696,9 +696,9 @@ static Status gemm_batch(const std::vector<GemmItem>& items, int s, double alpha
       g.B[q] = items[i0 + q].B;
       g.tri[q] = items[i0 + q].tri;
     }
-    // about two CTAs per SM: split K when the output tiles alone are fewer
+    // about four CTAs per SM: split K when the output tiles alone are fewer
     const int tiles = cnt * (lower_only ? ntl * (ntl + 1) / 2 : ntl * ntl);
-    const int ksplit = std::min(kGemmSplit, std::max(1, (2 * sm_count + tiles - 1) / tiles));
+    const int ksplit = std::min(kGemmSplit, std::max(1, (4 * sm_count + tiles - 1) / tiles));
     const dim3 grid((unsigned)ntl, (unsigned)ntl, (unsigned)(cnt * ksplit));
     k_chunk_gemm<kTransB><<<grid, 256, 0, st>>>(g, s, alpha, beta, lower_only, ksplit, D.gpart, D.gctr);
     BAMG_COUNT_LAUNCH;
