@@ -400,6 +400,10 @@ def run_ours(args):
         "device_used": round((total_b - free_b) / 1e9, 3),
         "note": "library = its stream-ordered pool allocations (hierarchy, plans, vectors); "
                 "inputs = the value streams and vectors bench.py keeps resident through torch"}
+    stor = B.bamg_bsr_storage(wl.A)
+    result["fine_operator"] = {"lanes": B.bamg_bsr_get_lanes(wl.A), "stored_slots": stor["stored_slots"],
+                               "padding": round(1 - B.bamg_bsr_info(wl.A)["nnzb"] / stor["stored_slots"], 4),
+                               "rows_sorted": stor["rows_sorted"]}
     if args.step_only:
         wl.close()
         if dist:

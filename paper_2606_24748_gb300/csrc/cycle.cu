@@ -509,10 +509,68 @@ static Status tune_smoother_split(bamg_mg* mg, int l) {
   return s;
 }
 
+// Lanes per row of a 3x3-block level's smoother.  The lanes autotuner times
+// the plain product; on long rows (Q2: up to 125 blocks) it takes several
+// lanes per row, and the fused Chebyshev kernels then leave their per-row
+// epilogue (new residual, block-diagonal inverse, update) to one lane in
+// several.  Time the level's own pre- and post-smoothing with the product's
+// choice and with 1, 2 and 4 lanes, and keep the fastest (the CG product and
+// the power steps use the same choice).  The level's vectors are scratch.
+template <typename T>
+static Status tune_smoother_lanes(bamg_mg* mg, int l) {
+  Level& L = mg->levels[l];
+  bamg_bsr* A = L.A;
+  if (L.bs != 3 || A->bc != 3 || l + 1 >= (int)mg->levels.size()) return Status{};
+  int& vec = std::is_same<T, double>::value ? A->vec : A->vec32;
+  cudaStream_t st = mg->ctx->stream;
+  cudaEvent_t e0, e1;
+  BAMG_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return make_status(BAMG_ERR_CUDA, "event");
+  }
+  Status s;
+  const int keep = vec;
+  std::vector<int> cand = {keep};  // the product's choice first
+  for (int v : {1, 2, 4})
+    if (v != keep) cand.push_back(v);
+  float best = 1e30f;
+  int best_v = keep;
+  for (size_t ci = 0; ci < cand.size() && s.ok(); ++ci) {
+    const int v = cand[ci];
+    vec = v;
+    for (int w = 0; w < 2 && s.ok(); ++w) {
+      s = smooth_down<3, T>(mg, l, nullptr, st);
+      if (s.ok()) s = smooth_up<3, T>(mg, l, nullptr, st);
+    }
+    float t[5];
+    for (int rep = 0; rep < 5 && s.ok(); ++rep) {
+      cudaEventRecord(e0, st);
+      s = smooth_down<3, T>(mg, l, nullptr, st);
+      if (s.ok()) s = smooth_up<3, T>(mg, l, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess)
+        s = make_status(BAMG_ERR_CUDA, "smoother timing");
+    }
+    if (!s.ok()) break;
+    std::sort(t, t + 5);
+    // another choice must beat the best so far by 3% (timing noise)
+    if (ci == 0 || t[2] < 0.97f * best) {
+      best = t[2];
+      best_v = v;
+    }
+  }
+  vec = s.ok() ? best_v : keep;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
 Status mg_tune_smoothers(bamg_mg* mg) {
   const int nl = (int)mg->levels.size();
-  for (int l = 1; l + 1 < nl; ++l)
-    BAMG_TRY(mg->opts.precision == BAMG_FP32 ? tune_smoother_split<float>(mg, l) : tune_smoother_split<double>(mg, l));
+  const bool f32 = mg->opts.precision == BAMG_FP32;
+  BAMG_TRY(f32 ? tune_smoother_lanes<float>(mg, 0) : tune_smoother_lanes<double>(mg, 0));
+  for (int l = 1; l + 1 < nl; ++l) BAMG_TRY(f32 ? tune_smoother_split<float>(mg, l) : tune_smoother_split<double>(mg, l));
   return Status{};
 }
 
