@@ -183,3 +183,27 @@ def test_spmm_four_wide_matches_oracle_products():
             assert rel(Y.cpu().numpy(), As @ Xh) <= TOL64
     finally:
         gp.close()
+
+
+@pytest.mark.parametrize("ne,k", [(13, 16), (13, 8), (8, 16), (13, 12)])
+def test_spmm_fp32_matches_oracle_products(ne, k):
+    """FP32 products of 8, 12 and 16 right-hand sides (8^3 has its fine
+    operator stored with rows sorted by length): against the FP64 product of
+    the oracle, at FP32 rounding, and against the FP32 product of the same
+    values taken one column at a time."""
+    h = hierarchy(ne)
+    gp = GpuProblem(ne, precision=B.BAMG_FP32)
+    try:
+        As = h.levels[0].As
+        n = As.shape[0]
+        Xh = np.random.default_rng(k + ne).standard_normal((n, k)).astype(np.float32)
+        Y = torch.zeros(n * k, dtype=torch.float32, device="cuda")
+        B.bamg_bsr_spmm(gp.ctx, gp.A, torch.from_numpy(Xh.copy()).cuda(), Y, k, B.BAMG_FP32)
+        got = Y.cpu().numpy().reshape(n, k).astype(np.float64)
+        assert rel(got, As @ Xh.astype(np.float64)) <= 2e-6
+        for j in (0, k - 1):
+            y = torch.zeros(n, dtype=torch.float32, device="cuda")
+            B.bamg_bsr_spmv(gp.ctx, gp.A, torch.from_numpy(np.ascontiguousarray(Xh[:, j])).cuda(), y, B.BAMG_FP32)
+            assert rel(got[:, j], y.cpu().numpy().astype(np.float64)) <= 2e-6
+    finally:
+        gp.close()
