@@ -123,7 +123,7 @@ def test_stationary_iteration_equals_dense_error_operator_powers():
     got = np.array(omg.stationary(h, b, its))
     assert got.shape == ref.shape
     assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * ref[0])
-    # the factor the learned smoother is judged by follows from the same powers
+    # the factor that rates the learned smoother follows from the same powers
     assert (got[-1] / got[0]) ** (1 / its) < 1.0
 
 
