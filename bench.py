@@ -80,7 +80,7 @@ def parse():
                    help="only the timed reuse steps and their per-kernel table (for runs under a profiler)")
     p.add_argument("--no-large", action="store_true",
                    help="skip the 127^3 FP64-vs-mixed comparison (4 levels, 6.3 M dofs)")
-    p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large", "ptap"],
+    p.add_argument("--only", default="", choices=["", "multi", "batch", "peaks", "large", "ptap", "mis"],
                    help="run only that measurement (its own JSON object; used for profiling)")
     return p.parse_args()
 
@@ -1161,9 +1161,12 @@ def run_only(args):
         build()
     if args.only == "batch":
         return {"only": "batch", "batch": batch_solve(torch, B)}
-    if args.only == "ptap":
+    if args.only in ("ptap", "mis"):
         wl = Workload(B, torch, args.ne, 0.3, "fp64", n_inputs=1)
-        out = {"only": "ptap", "ptap_reuse": ptap_reuse(wl, torch, B)}
+        if args.only == "ptap":
+            out = {"only": "ptap", "ptap_reuse": ptap_reuse(wl, torch, B)}
+        else:
+            out = {"only": "mis", "mis_hierarchy": mis_hierarchy(wl, torch, B)}
         wl.close()
         return out
     if args.only in ("peaks", "large"):
