@@ -132,3 +132,47 @@ def test_booked_vcycles_equal_fine_chebyshev_launches(big):
     finally:
         B.bamg_ctx_profile_slots(big.ctx, [])
     assert launches == 3 * bench.vcycles_per_solve(out["iterations"])
+
+
+def test_mis_hierarchy_properties_at_full_size(big):
+    """The hierarchy built from device MIS aggregates of the same operator
+    (4 levels, coarse operators of 67 and 244 blocks per row, stored sorted
+    by row length): Galerkin identity and symmetry on every level, and CG to
+    rtol 1e-8 with the true residual."""
+    o = B.bamg_mg_opts_default()
+    o.grid[0] = o.grid[1] = o.grid[2] = big.mesh.m
+    o.aggregation = B.BAMG_AGG_MIS
+    mg = B.bamg_mg_setup(big.ctx, big.A, big.mesh.coords(), big.mesh.dirichlet(), o)
+    try:
+        nl = B.bamg_mg_num_levels(mg)
+        assert nl == 4
+        rng = np.random.default_rng(5)
+        for l in range(nl - 1):
+            A, P = B.bamg_mg_get_level(mg, l)
+            Ac, _ = B.bamg_mg_get_level(mg, l + 1)
+            ic, ia = B.bamg_bsr_info(Ac), B.bamg_bsr_info(A)
+            nc, nf = ic["nbr"] * ic["bs_r"], ia["nbr"] * ia["bs_r"]
+
+            def mv(M, v, m):
+                out = torch.zeros(m, dtype=torch.float64, device="cuda")
+                B.bamg_bsr_spmv(big.ctx, M, v, out)
+                return out
+
+            xc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+            yc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+            lhs, lhs_t = float(xc @ mv(Ac, yc, nc)), float(yc @ mv(Ac, xc, nc))
+            px, py = mv(P, xc, nf), mv(P, yc, nf)
+            apy = mv(A, py, nf)
+            scale = float(torch.linalg.norm(px) * torch.linalg.norm(apy))
+            assert abs(lhs - float(px @ apy)) <= 1e-12 * scale, l
+            assert abs(lhs - lhs_t) <= 1e-12 * scale, l
+        assert B.bamg_bsr_storage(B.bamg_mg_get_level(mg, 1)[0])["rows_sorted"]
+        b = torch.from_numpy(body_force(big.mesh)).cuda()
+        x = torch.zeros_like(b)
+        out = B.bamg_cg_solve(big.ctx, mg, b, x, 1e-8, 200)
+        assert out["converged"]
+        r = torch.zeros_like(b)
+        B.bamg_bsr_spmv(big.ctx, big.A, x, r)
+        assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) <= 1.05e-8
+    finally:
+        B.bamg_mg_destroy(mg)
