@@ -116,3 +116,46 @@ def test_q2_rows_sorted_by_length_in_every_row_kernel():
         gp.close()
         if gq is not None:
             gq.close()
+
+
+@pytest.mark.parametrize("precision", [B.BAMG_FP64, B.BAMG_FP32])
+def test_q2_full_size_properties(precision):
+    """32^3 Q2 elements, the bench's Q2 size (823,875 dofs, 16.97 M blocks,
+    3 levels), in the autotuned configuration: the fine operator stored
+    sorted by row length, the Galerkin identity and symmetry on every level,
+    and CG to rtol 1e-8 with the true residual."""
+    ne = 32
+    gp = GpuProblem(ne, order=2, precision=precision)
+    try:
+        nl = B.bamg_mg_num_levels(gp.mg)
+        assert nl == 3
+        assert B.bamg_bsr_storage(gp.A)["rows_sorted"]
+        rng = np.random.default_rng(32)
+
+        def mv(M, v, m):
+            out = torch.zeros(m, dtype=torch.float64, device="cuda")
+            B.bamg_bsr_spmv(gp.ctx, M, v, out)
+            return out
+
+        if precision == B.BAMG_FP64:
+            for l in range(nl - 1):
+                A, P = B.bamg_mg_get_level(gp.mg, l)
+                Ac, _ = B.bamg_mg_get_level(gp.mg, l + 1)
+                ic, ia = B.bamg_bsr_info(Ac), B.bamg_bsr_info(A)
+                nc, nf = ic["nbr"] * ic["bs_r"], ia["nbr"] * ia["bs_r"]
+                xc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+                yc = torch.from_numpy(rng.standard_normal(nc)).cuda()
+                lhs, lhs_t = float(xc @ mv(Ac, yc, nc)), float(yc @ mv(Ac, xc, nc))
+                px, py = mv(P, xc, nf), mv(P, yc, nf)
+                apy = mv(A, py, nf)
+                scale = float(torch.linalg.norm(px) * torch.linalg.norm(apy))
+                assert abs(lhs - float(px @ apy)) <= 1e-12 * scale, l
+                assert abs(lhs - lhs_t) <= 1e-12 * scale, l
+        b = torch.from_numpy(body_force(gp.mesh)).cuda()
+        x = torch.zeros_like(b)
+        out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)
+        assert out["converged"] and out["iterations"] <= 40
+        r = mv(gp.A, x, b.numel())
+        assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) <= 1.05e-8
+    finally:
+        gp.close()
