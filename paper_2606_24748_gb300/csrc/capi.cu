@@ -491,10 +491,14 @@ bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
   if (!A) return BAMG_ERR_INVALID;
   if (lanes <= 0) {
     const int vs = lanes == 0 ? 4 : -lanes;
-    if (vs != 1 && vs != 2 && vs != 4 && vs != 32 && vs != 64 && vs != 128)
-      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "split lanes must be -1, -2, -4, -32, -64 or -128"));
+    const bool block_split = is_block_split(vs);
+    if (vs != 1 && vs != 2 && vs != 4 && vs != 32 && vs != 64 && vs != 128 && !block_split)
+      return fail(A->ctx, make_status(BAMG_ERR_INVALID,
+                                      "split lanes must be -1, -2, -4, -32, -64, -128, -258, -260, -264, -272 or -288"));
     if (A->br != 6 || (A->bc != 3 && A->bc != 6))
       return fail(A->ctx, make_status(BAMG_ERR_INVALID, "the component-split form needs 6x3 or 6x6 blocks"));
+    if (block_split && A->bc != 3)
+      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "the block split needs 6x3 blocks"));
     A->split = A->split32 = vs;
     return BAMG_OK;
   }

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "bsplit.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -238,6 +239,28 @@ __global__ void __launch_bounds__(768) k_transfer_split(const int* __restrict__ 
   if (sub == 0 && i >= 0 && i < n) y[i * BR + a] = accumulate ? y[i * BR + a] + acc : acc;
 }
 
+// All-component block split (6x3 blocks, the finest restriction): CTA = one
+// slice, VB warps (see row_blocks_split).
+template <int BR, int BC, int VB, typename T>
+__global__ void __launch_bounds__(32 * VB) k_transfer_bsplit(const int* __restrict__ sp, const int* __restrict__ col,
+                                                              const T* __restrict__ vals, const int* __restrict__ srow,
+                                                              int64_t n, const T* __restrict__ v, T* __restrict__ y,
+                                                              int accumulate, const int* done) {
+  pdl_enter();
+  BAMG_DONE_RETURN
+  const int64_t s = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T out[blocks_split_outs<BR, VB>()];
+  row_blocks_split<BR, BC, VB, T, T, T>(sp, col, vals, v, s, lane, w, out);
+  const int64_t i = row_at(srow, s * 32 + lane);
+  if (i < 0 || i >= n) return;
+#pragma unroll
+  for (int k = 0; k < blocks_split_outs<BR, VB>(); ++k) {
+    const int a = w + k * VB;
+    if (a < BR) y[i * BR + a] = accumulate ? y[i * BR + a] + out[k] : out[k];
+  }
+}
+
 // Row form (see row_component_lanes): CTA = one row position.
 template <int BR, int BC, int VR, typename T>
 __global__ void __launch_bounds__(32 * BR * VR) k_transfer_rows(const int* __restrict__ sp, const int* __restrict__ col,
@@ -423,6 +446,16 @@ static Status transfer(const bamg_bsr* M, const T* vals, const T* v, T* y, int a
                        cudaStream_t st) {
   const int64_t rows = row_threads_for<T>(M);
   if (rows == 0) return Status{};
+  if constexpr (BR == 6 && BC == 3) {
+    if (split_for<T>(M) >= kSplitBlocks) {
+      BAMG_DISPATCH_VB(split_for<T>(M), {
+        BAMG_CUDA(launch_k(k_transfer_bsplit<BR, BC, VB, T>, dim3((unsigned)M->nslices), dim3(32 * VB), st,
+                           M->slice_ptr, M->sell_col, vals, M->slot_row, M->nbr, v, y, accumulate, done));
+        BAMG_COUNT_LAUNCH; })
+      BAMG_CUDA(cudaGetLastError());
+      return Status{};
+    }
+  }
   if (BR == 6 && split_for<T>(M) >= kSplitRows) {
     BAMG_DISPATCH_ROWS(split_for<T>(M), {
       BAMG_CUDA(launch_k(k_transfer_rows<BR, BC, VR, T>, dim3((unsigned)(M->nslices * kSlice)), dim3(32 * BR * VR), st,

@@ -459,6 +459,22 @@ constexpr int kSplitRows = 32;
     case 64: { constexpr int VR = 2; __VA_ARGS__; } break;  \
     default: { constexpr int VR = 1; __VA_ARGS__; } break;  \
   }
+// Split codes 256 + VB (VB = 2, 4, 8, 16, 32): the all-component block
+// split (row_blocks_split) for 6x3 blocks (the finest restriction), VB warps
+// per slice.
+constexpr int kSplitBlocks = 256;
+inline bool is_block_split(int s) {
+  return s == kSplitBlocks + 2 || s == kSplitBlocks + 4 || s == kSplitBlocks + 8 || s == kSplitBlocks + 16 ||
+         s == kSplitBlocks + 32;
+}
+#define BAMG_DISPATCH_VB(s, ...)                            \
+  switch (s) {                                             \
+    case kSplitBlocks + 32: { constexpr int VB = 32; __VA_ARGS__; } break; \
+    case kSplitBlocks + 16: { constexpr int VB = 16; __VA_ARGS__; } break; \
+    case kSplitBlocks + 8: { constexpr int VB = 8; __VA_ARGS__; } break; \
+    case kSplitBlocks + 4: { constexpr int VB = 4; __VA_ARGS__; } break; \
+    default: { constexpr int VB = 2; __VA_ARGS__; } break;  \
+  }
 // Run `body` with the compile-time warps per component VS matching s (1, 2 or 4).
 #define BAMG_DISPATCH_VS(s, ...)                            \
   switch (s) {                                             \

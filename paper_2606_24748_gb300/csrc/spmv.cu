@@ -2,6 +2,7 @@
 // (Sec. 4.2: one column index per block; FP64 or FP32 values).
 #include <algorithm>
 
+#include "bsplit.cuh"
 #include "device.cuh"
 #include "internal.h"
 
@@ -36,6 +37,23 @@ __global__ void __launch_bounds__(768) k_spmv_split(const int* __restrict__ slic
   const T acc = row_component<BR, BC, VS, T, T, T>(slice_ptr, col, vals, x, s, lane, a, sub);
   const int64_t i = srow ? (int64_t)srow[s * 32 + lane] : s * 32 + lane;
   if (sub == 0 && i >= 0 && i < nbr) y[i * BR + a] = acc;
+}
+
+// All-component block split (6x3 blocks: the finest restriction): CTA = one
+// slice, VB warps (see row_blocks_split).
+template <int BR, int BC, int VB, typename T>
+__global__ void __launch_bounds__(32 * VB) k_spmv_bsplit(const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                                          const T* __restrict__ vals, const int* __restrict__ srow,
+                                                          const T* __restrict__ x, T* __restrict__ y, int64_t nbr) {
+  const int64_t s = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T out[blocks_split_outs<BR, VB>()];
+  row_blocks_split<BR, BC, VB, T, T, T>(slice_ptr, col, vals, x, s, lane, w, out);
+  const int64_t i = row_at(srow, s * 32 + lane);
+  if (i < 0 || i >= nbr) return;
+#pragma unroll
+  for (int k = 0; k < blocks_split_outs<BR, VB>(); ++k)
+    if (w + k * VB < BR) y[i * BR + w + k * VB] = out[k];
 }
 
 // Row form (rectangular 6-row-block matrices with few, long rows).
@@ -142,6 +160,16 @@ static bool can_split(const bamg_bsr* A) { return A->br == 6 && (A->bc == 3 || A
 // warps per component.
 template <typename T>
 static Status launch_spmv_v(const bamg_bsr* A, int vec, const T* vals, const T* x, T* y, cudaStream_t st) {
+  if (vec <= -kSplitBlocks) {
+    if (A->nslices == 0) return Status{};
+    if (A->br != 6 || A->bc != 3) return make_status(BAMG_ERR_INVALID, "the block split needs 6x3 blocks");
+    BAMG_DISPATCH_VB(-vec, {
+      k_spmv_bsplit<6, 3, VB, T><<<(unsigned)A->nslices, 32 * VB, 0, st>>>(A->slice_ptr, A->sell_col, vals, A->slot_row, x, y,
+                                                                           A->nbr);
+      BAMG_COUNT_LAUNCH; })
+    BAMG_CUDA(cudaGetLastError());
+    return Status{};
+  }
   if (vec <= -kSplitRows) {
     if (A->nslices == 0) return Status{};
     const unsigned g = (unsigned)(A->nslices * kSlice);
@@ -232,9 +260,11 @@ static Status tune_lanes(bamg_bsr* A, const T* vals, int* out_vec, int* out_spli
   // widths 1, 2, ..., 32, then (6-row blocks) the component-split form with
   // 1, 2 and 4 warps per component, coded as -1, -2, -4
   // and, for rectangular ones (the restriction), the row form with 1, 2 and
-  // 4 warps per component (-32, -64, -128)
-  static const int kChoices[] = {1, 2, 4, 8, 16, 32, -1, -2, -4, -32, -64, -128};
-  const int n_choices = can_split(A) ? (A->nbr != A->nbc || A->br != A->bc ? 12 : 9) : 6;
+  // 4 warps per component (-32, -64, -128); for 6x3 blocks also the
+  // all-component block split with 8, 16 and 32 warps (-264, -272, -288)
+  static const int kChoices[] = {1, 2, 4, 8, 16, 32, -1, -2, -4, -32, -64, -128,
+                                 -(kSplitBlocks + 8), -(kSplitBlocks + 16), -(kSplitBlocks + 32)};
+  const int n_choices = !can_split(A) ? 6 : (A->br == 6 && A->bc == 3) ? 15 : (A->nbr != A->nbc || A->br != A->bc ? 12 : 9);
   for (int ci = 0; ci < n_choices; ++ci) {
     const int lv = kChoices[ci];
     for (int w = 0; w < 2 && s.ok(); ++w) s = launch_spmv_v<T>(A, lv, vals, x, y, st);

@@ -464,10 +464,14 @@ def test_component_split_hierarchy_gives_same_cycle(precision):
         gp.close()
 
 
-@pytest.mark.parametrize("precision,lanes", [(B.BAMG_FP64, -32), (B.BAMG_FP64, -128), (B.BAMG_FP32, -64)])
+@pytest.mark.parametrize("precision,lanes", [(B.BAMG_FP64, -32), (B.BAMG_FP64, -128), (B.BAMG_FP32, -64),
+                                             (B.BAMG_FP64, -258), (B.BAMG_FP64, -272), (B.BAMG_FP64, -288),
+                                             (B.BAMG_FP32, -260), (B.BAMG_FP32, -288)])
 def test_row_form_restriction_gives_same_cycle(precision, lanes):
-    """The restriction's row form (a CTA per coarse row) changes only the
-    summation order of the cycle."""
+    """The restriction's row form (a CTA per coarse row) and its block split
+    (VB warps per slice of 6x3 rows) change only the summation order of the
+    cycle.  The block split exists for 6x3 blocks only: it is set on the
+    finest restriction, and 6x6 restrictions refuse it."""
     ne = 16
     h = hierarchy(ne)
     gp = GpuProblem(ne, precision=precision)
@@ -479,6 +483,10 @@ def test_row_form_restriction_gives_same_cycle(precision, lanes):
         for l in range(B.bamg_mg_num_levels(gp.mg) - 1):
             R = B.bamg_mg_get_restriction(gp.mg, l)
             assert R is not None
+            if lanes <= -258 and l > 0:
+                with pytest.raises(RuntimeError):
+                    B.bamg_bsr_set_lanes(gp.ctx, R, lanes)
+                continue
             B.bamg_bsr_set_lanes(gp.ctx, R, lanes)
             assert B.bamg_bsr_get_lanes(R) == lanes
         y1 = torch.zeros_like(y0)
