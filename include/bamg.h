@@ -207,10 +207,10 @@ BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, b
  * -32 * VR (VR = 1, 2, 4) = one CTA per row, VR warps per component with
  * their lanes over the row's blocks (for few, very long rows; used by the
  * transfer and product kernels, the smoother kernels treat it as -1); for
- * 6x3 blocks only (the finest restriction), -(256 + VB) with VB = 2, 4 or 8
- * = the block split: VB warps per 32-row slice, each summing every output
- * component over every VB-th block of its lane's row, so that each block's
- * column index and gathered x are loaded once per lane; 0 in
+ * 6x3 blocks only (the finest restriction), -(256 + VB) with VB = 2, 4, 8,
+ * 16 or 32 = the block split: VB warps per 32-row slice, each summing every
+ * output component over every VB-th block of its lane's row, so that each
+ * block's column index and gathered x are loaded once per lane; 0 in
  * _set_lanes means -4.  _autotune times the product for every choice from a
  * flushed L2 on the context's stream and keeps the fastest, for the FP64
  * values and, when present, the FP32 copy (allocates work vectors; returns
