@@ -106,8 +106,13 @@ typedef enum {
   BAMG_PROF_CG_XR = 11,         /* CG x, r update and residual norm */
   BAMG_PROF_CG_VECTOR = 12,     /* CG step-length dots and direction update */
   BAMG_PROF_REFRESH = 13,       /* smoother refresh of a level (inverses, eigen-estimate) */
-  BAMG_PROF_COUNT = 14
+  BAMG_PROF_CHEB_PRE_L0 = 14,   /* the finest level's pre-smoothing steps alone: a sample of slot 0
+                                   with one bracket per cycle instead of two.  While it is enabled
+                                   those steps are timed here and not in slot 0.  bamg_ctx_profile
+                                   does not enable it; bamg_ctx_profile_slots does. */
+  BAMG_PROF_COUNT = 15
 } bamg_prof_slot;
+/* enable != 0: every slot but BAMG_PROF_CHEB_PRE_L0; 0 disables. */
 BAMG_API bamg_status bamg_ctx_profile(bamg_ctx* ctx, int enable);
 /* Enable timing for the slots in `mask` only (bit s = slot s; 0 disables).
  * Every bracketed launch loses its programmatic overlap with its neighbours

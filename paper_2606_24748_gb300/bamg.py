@@ -31,7 +31,7 @@ BAMG_NORM_FROBENIUS = 0
 BAMG_NORM_INFINITY = 1
 PROF_SLOTS = {"cheb_step_l0": 0, "cheb_rinit_l0": 1, "ptap_stage1_l0": 2, "ptap_stage2_l0": 3, "cg_ap": 4,
               "coo": 5, "coarse_factor": 6, "smooth_coarse": 7, "transfer": 8, "coarse_solve": 9,
-              "l0_vector": 10, "cg_xr": 11, "cg_vector": 12, "refresh": 13}
+              "l0_vector": 10, "cg_xr": 11, "cg_vector": 12, "refresh": 13, "cheb_pre_l0": 14}
 
 
 class BamgError(RuntimeError):

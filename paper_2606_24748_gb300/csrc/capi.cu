@@ -344,7 +344,7 @@ bamg_status bamg_ctx_set_wait_limit(bamg_ctx* c, int64_t polls) {
 }
 
 bamg_status bamg_ctx_profile(bamg_ctx* c, int enable) {
-  return bamg_ctx_profile_slots(c, enable ? ~0u : 0u);
+  return bamg_ctx_profile_slots(c, enable ? ~(1u << BAMG_PROF_CHEB_PRE_L0) : 0u);
 }
 
 bamg_status bamg_ctx_profile_slots(bamg_ctx* c, unsigned mask) {

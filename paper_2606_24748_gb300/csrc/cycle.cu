@@ -364,8 +364,10 @@ static Status smooth_down(bamg_mg* mg, int l, const int* done, cudaStream_t st, 
   BAMG_COUNT_LAUNCH;
   prof_end(mg->ctx, pi, st);
   T* d[2] = {p.d0, p.d1};
-  // the m pre-smoothing steps are consecutive launches of one kernel: one bracket
-  const int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st, m);
+  // the m pre-smoothing steps are consecutive launches of one kernel: one
+  // bracket, in the sampling slot when that is enabled
+  int pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_PRE_L0 : -1, st, m);
+  if (pm < 0) pm = prof_begin(mg->ctx, l == 0 ? BAMG_PROF_CHEB_STEP_L0 : -1, st, m);
   for (int k = 0; k < m; ++k) {
     if (BS == 6 && split_for<T>(A)) {
       BAMG_DISPATCH_VS(split_for<T>(A), {

@@ -302,6 +302,39 @@ def test_profiling_slots_time_only_the_chosen_kernels():
         gp.close()
 
 
+def test_sampling_slot_takes_the_pre_smoothing_pair():
+    """The sampling slot brackets the finest pre-smoothing pair of every cycle
+    (one bracket, two launches); slot 0 then keeps only the post-smoothing
+    step.  The all-slot profile leaves the sampling slot off."""
+    gp = GpuProblem(16)
+    try:
+        b = torch.from_numpy(body_force(gp.mesh)).cuda()
+
+        def solve():
+            x = torch.zeros_like(b)
+            return B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)["iterations"]
+
+        def launches(name):
+            return B.bamg_ctx_profile_read(gp.ctx, B.PROF_SLOTS[name])[1]
+
+        B.bamg_ctx_profile_slots(gp.ctx, ["cheb_step_l0"])
+        its = solve()
+        full = launches("cheb_step_l0")
+        B.bamg_ctx_profile_slots(gp.ctx, ["cheb_step_l0", "cheb_pre_l0"])
+        assert solve() == its
+        post, pre = launches("cheb_step_l0"), launches("cheb_pre_l0")
+        assert full > 0 and pre == 2 * post and pre + post == full
+        B.bamg_ctx_profile_slots(gp.ctx, ["cheb_pre_l0"])
+        assert solve() == its
+        assert launches("cheb_pre_l0") == pre and launches("cheb_step_l0") == 0
+        B.bamg_ctx_profile(gp.ctx, 1)
+        assert solve() == its
+        assert launches("cheb_pre_l0") == 0 and launches("cheb_step_l0") == full
+        B.bamg_ctx_profile(gp.ctx, 0)
+    finally:
+        gp.close()
+
+
 def test_device_memory_counts_the_library_allocations():
     """The pool counters see a hierarchy's allocations and their high-water mark."""
     ctx = B.bamg_ctx_create(torch.cuda.current_stream())
