@@ -24,6 +24,13 @@ def big():
 
 
 @pytest.fixture(scope="module")
+def big32():
+    gp = GpuProblem(NE, precision=B.BAMG_FP32)
+    yield gp
+    gp.close()
+
+
+@pytest.fixture(scope="module")
 def stream():
     mesh = Mesh(NE)
     s = coo_stream(mesh, 0.3, element_scale(mesh))
@@ -98,21 +105,47 @@ def test_galerkin_identity_on_every_level(big):
 
 
 @pytest.mark.parametrize("precision", [B.BAMG_FP64, B.BAMG_FP32])
-def test_cg_reaches_the_tolerance_with_the_true_residual(big, precision):
-    gp = big if precision == B.BAMG_FP64 else GpuProblem(NE, precision=precision)
-    try:
-        b = torch.from_numpy(body_force(gp.mesh)).cuda()
-        x = torch.zeros_like(b)
-        out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)
-        assert out["converged"] and out["iterations"] <= 40
-        r = torch.zeros_like(b)   # b - A x with the plain product, not CG's recurrence
-        B.bamg_bsr_spmv(gp.ctx, gp.A, x, r)
-        true_rel = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
-        assert true_rel <= 1.05e-8
-        assert out["true_rnorm"] / out["bnorm"] == pytest.approx(true_rel, rel=1e-6, abs=1e-12)
-    finally:
-        if gp is not big:
-            gp.close()
+def test_cg_reaches_the_tolerance_with_the_true_residual(big, big32, precision):
+    gp = big if precision == B.BAMG_FP64 else big32
+    b = torch.from_numpy(body_force(gp.mesh)).cuda()
+    x = torch.zeros_like(b)
+    out = B.bamg_cg_solve(gp.ctx, gp.mg, b, x, 1e-8, 200)
+    assert out["converged"] and out["iterations"] <= 40
+    r = torch.zeros_like(b)   # b - A x with the plain product, not CG's recurrence
+    B.bamg_bsr_spmv(gp.ctx, gp.A, x, r)
+    true_rel = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+    assert true_rel <= 1.05e-8
+    assert out["true_rnorm"] / out["bnorm"] == pytest.approx(true_rel, rel=1e-6, abs=1e-12)
+
+
+def test_finest_restriction_in_its_tuned_forms(big32):
+    """The finest restriction (9,261 rows of 6x3 blocks) in the forms the
+    autotuner chose for the mixed cycle: the FP64 product equals a host sum of
+    its own blocks on sampled rows, and the FP32 product (the block split,
+    where the tuner keeps it) stays within FP32 rounding of the FP64 one."""
+    gp = big32
+    R = B.bamg_mg_get_restriction(gp.mg, 0)
+    info = B.bamg_bsr_info(R)
+    assert (info["bs_r"], info["bs_c"]) == (6, 3)
+    nbr, nbc, nnzb = info["nbr"], info["nbc"], info["nnzb"]
+    rowptr = torch.zeros(nbr + 1, dtype=torch.int32, device="cuda")
+    colidx = torch.zeros(nnzb, dtype=torch.int32, device="cuda")
+    vals = torch.zeros(nnzb * 18, dtype=torch.float64, device="cuda")
+    B.bamg_bsr_get_pattern(gp.ctx, R, rowptr, colidx)
+    B.bamg_bsr_get_values(gp.ctx, R, vals)
+    rowptr, colidx, vals = rowptr.cpu().numpy(), colidx.cpu().numpy(), vals.cpu().numpy().reshape(-1, 6, 3)
+    x = np.random.default_rng(11).standard_normal(nbc * 3)
+    y64 = torch.zeros(nbr * 6, dtype=torch.float64, device="cuda")
+    B.bamg_bsr_spmv(gp.ctx, R, torch.from_numpy(x).cuda(), y64)
+    y32 = torch.zeros(nbr * 6, dtype=torch.float32, device="cuda")
+    B.bamg_bsr_spmv(gp.ctx, R, torch.from_numpy(x).float().cuda(), y32, B.BAMG_FP32)
+    y64, y32 = y64.cpu().numpy(), y32.double().cpu().numpy()
+    xb = x.reshape(-1, 3)
+    for I in np.random.default_rng(12).choice(nbr, 48, replace=False):
+        k0, k1 = rowptr[I], rowptr[I + 1]
+        ref = np.einsum("krc,kc->r", vals[k0:k1], xb[colidx[k0:k1]])
+        assert rel(y64[6 * I:6 * I + 6], ref) <= 1e-13
+    assert rel(y32, y64) <= 1e-5
 
 
 def test_booked_vcycles_equal_fine_chebyshev_launches(big):

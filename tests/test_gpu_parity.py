@@ -448,8 +448,12 @@ def test_lane_choice_invariance(br, bc):
         B.bamg_bsr_coo_set_values(ctx, A, torch.from_numpy(v).cuda(), 0)
         x = rng.standard_normal(nbc * bc)
         yref = ref.scalar() @ x
-        # -1, -2, -4: component split; -32, -64, -128: one CTA per row
+        # -1, -2, -4: component split; -32, -64, -128: one CTA per row;
+        # -(256 + VB): block split (6x3 only; 45 rows leave the second slice ragged)
         choices = (1, 2, 4, 8, 16, 32) + ((-1, -2, -4, -32, -64, -128) if br == 6 else ())
+        block_split = (-258, -260, -264, -272, -288)
+        if (br, bc) == (6, 3):
+            choices += block_split
         for lanes in choices:
             B.bamg_bsr_set_lanes(ctx, A, lanes)
             assert B.bamg_bsr_get_lanes(A) == lanes
@@ -463,6 +467,10 @@ def test_lane_choice_invariance(br, bc):
         assert lanes in choices and ms > 0
         with pytest.raises(B.BamgError):
             B.bamg_bsr_set_lanes(ctx, A, 3)
+        if (br, bc) != (6, 3):
+            for code in block_split:
+                with pytest.raises(B.BamgError):
+                    B.bamg_bsr_set_lanes(ctx, A, code)
         if br == 3:
             with pytest.raises(B.BamgError):
                 B.bamg_bsr_set_lanes(ctx, A, 0)
