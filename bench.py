@@ -236,19 +236,21 @@ def hierarchy_matrices(B, mg):
 
 
 def apply_tune_cache(B, ctx, mg, path):
-    """Lanes of every level matrix from `path` if it exists, else save them there."""
+    """Lanes of every level matrix, FP64 and FP32 copies (the product's and the
+    smoothers' tuned choices), from `path` if it exists, else save them there."""
     if not path:
         return
     mats = hierarchy_matrices(B, mg)
+    precs = (B.BAMG_FP64, B.BAMG_FP32)
     if os.path.exists(path):
         with open(path) as f:
             lanes = json.load(f)
         for k, M in mats:
-            if k in lanes:
-                B.bamg_bsr_set_lanes(ctx, M, lanes[k])
+            for p, v in zip(precs, lanes.get(k, [])):
+                B.bamg_bsr_set_lanes_prec(ctx, M, p, v)
     else:
         with open(path, "w") as f:
-            json.dump({k: B.bamg_bsr_get_lanes(M) for k, M in mats}, f)
+            json.dump({k: [B.bamg_bsr_get_lanes_prec(M, p) for p in precs] for k, M in mats}, f)
 
 
 class Workload:

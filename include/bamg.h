@@ -225,6 +225,13 @@ BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, b
 BAMG_API bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms);
 BAMG_API bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes);
 BAMG_API bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes);
+/* The same for one copy: prec = BAMG_FP64 (the values) or BAMG_FP32 (the
+ * float copy of the mixed cycle).  The autotuner and the hierarchy's smoother
+ * timing choose the two separately; _get_lanes and _set_lanes above read the
+ * FP64 choice and write both.  Same codes and checks; BAMG_ERR_INVALID for
+ * another precision. */
+BAMG_API bamg_status bamg_bsr_set_lanes_prec(bamg_bsr* A, int prec, int lanes);
+BAMG_API bamg_status bamg_bsr_get_lanes_prec(const bamg_bsr* A, int prec, int* lanes);
 
 /* ---- Block operator inspection and the aggregation graph (Sec. 2.2, 3.2, 6) */
 

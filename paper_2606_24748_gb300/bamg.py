@@ -102,6 +102,8 @@ _SIGS = {
     "bamg_bsr_residual_norm_noalloc": [_P, _P, _P, _P],
     "bamg_bsr_set_lanes": [_P, ctypes.c_int],
     "bamg_bsr_get_lanes": [_P, _P],
+    "bamg_bsr_set_lanes_prec": [_P, ctypes.c_int, ctypes.c_int],
+    "bamg_bsr_get_lanes_prec": [_P, ctypes.c_int, _P],
     "bamg_bsr_block_norms": [_P, _P],
     "bamg_bsr_coo_scatter_values": [_P, _P, ctypes.c_int],
     "bamg_bsr_norm": [_P, ctypes.c_int, _P],
@@ -359,6 +361,16 @@ def bamg_mis_aggregate(ctx, n: int, rowptr, col, seed: int, agg) -> tuple[int, i
 def bamg_bsr_get_lanes(A) -> int:
     v = ctypes.c_int()
     _check(lib().bamg_bsr_get_lanes(A, ctypes.byref(v)), None)
+    return v.value
+
+
+def bamg_bsr_set_lanes_prec(ctx, A, prec: int, lanes: int):
+    _check(lib().bamg_bsr_set_lanes_prec(A, int(prec), int(lanes)), ctx)
+
+
+def bamg_bsr_get_lanes_prec(A, prec: int) -> int:
+    v = ctypes.c_int()
+    _check(lib().bamg_bsr_get_lanes_prec(A, int(prec), ctypes.byref(v)), None)
     return v.value
 
 

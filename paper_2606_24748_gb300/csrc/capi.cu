@@ -487,31 +487,61 @@ bamg_status bamg_bsr_autotune(bamg_bsr* A, int* lanes, float* ms) {
   return BAMG_OK;
 }
 
-bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
-  if (!A) return BAMG_ERR_INVALID;
+// Lanes code -> lanes per row (widths only) and split code (0 for a width),
+// checked against A's blocks.
+static Status parse_lanes(const bamg_bsr* A, int lanes, int* vec, int* split) {
   if (lanes <= 0) {
     const int vs = lanes == 0 ? 4 : -lanes;
     const bool block_split = is_block_split(vs);
     if (vs != 1 && vs != 2 && vs != 4 && vs != 32 && vs != 64 && vs != 128 && !block_split)
-      return fail(A->ctx, make_status(BAMG_ERR_INVALID,
-                                      "split lanes must be -1, -2, -4, -32, -64, -128, -258, -260, -264, -272 or -288"));
+      return make_status(BAMG_ERR_INVALID,
+                         "split lanes must be -1, -2, -4, -32, -64, -128, -258, -260, -264, -272 or -288");
     if (A->br != 6 || (A->bc != 3 && A->bc != 6))
-      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "the component-split form needs 6x3 or 6x6 blocks"));
-    if (block_split && A->bc != 3)
-      return fail(A->ctx, make_status(BAMG_ERR_INVALID, "the block split needs 6x3 blocks"));
-    A->split = A->split32 = vs;
-    return BAMG_OK;
+      return make_status(BAMG_ERR_INVALID, "the component-split form needs 6x3 or 6x6 blocks");
+    if (block_split && A->bc != 3) return make_status(BAMG_ERR_INVALID, "the block split needs 6x3 blocks");
+    *split = vs;
+    return Status{};
   }
   if (lanes > 32 || (lanes & (lanes - 1)))
-    return fail(A->ctx, make_status(BAMG_ERR_INVALID, "lanes must be -4, -2, -1, 0 or a power of two in [1, 32]"));
-  A->vec = A->vec32 = lanes;
-  A->split = A->split32 = 0;
+    return make_status(BAMG_ERR_INVALID, "lanes must be -4, -2, -1, 0 or a power of two in [1, 32]");
+  *vec = lanes;
+  *split = 0;
+  return Status{};
+}
+
+// A split code leaves the copy's lanes per row as they were (the kernels
+// without a split form keep using them); a width clears the split.
+bamg_status bamg_bsr_set_lanes(bamg_bsr* A, int lanes) {
+  if (!A) return BAMG_ERR_INVALID;
+  int vec = 0, split = 0;
+  const Status s = parse_lanes(A, lanes, &vec, &split);
+  if (!s.ok()) return fail(A->ctx, s);
+  if (!split) A->vec = A->vec32 = vec;
+  A->split = A->split32 = split;
   return BAMG_OK;
 }
 
 bamg_status bamg_bsr_get_lanes(const bamg_bsr* A, int* lanes) {
   if (!A || !lanes) return BAMG_ERR_INVALID;
   *lanes = A->split ? -A->split : A->vec;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_set_lanes_prec(bamg_bsr* A, int prec, int lanes) {
+  if (!A || (prec != BAMG_FP64 && prec != BAMG_FP32)) return BAMG_ERR_INVALID;
+  int& vec = prec == BAMG_FP64 ? A->vec : A->vec32;
+  int& split = prec == BAMG_FP64 ? A->split : A->split32;
+  int v = 0, sp = 0;
+  const Status s = parse_lanes(A, lanes, &v, &sp);
+  if (!s.ok()) return fail(A->ctx, s);
+  if (!sp) vec = v;
+  split = sp;
+  return BAMG_OK;
+}
+
+bamg_status bamg_bsr_get_lanes_prec(const bamg_bsr* A, int prec, int* lanes) {
+  if (!A || !lanes || (prec != BAMG_FP64 && prec != BAMG_FP32)) return BAMG_ERR_INVALID;
+  *lanes = prec == BAMG_FP64 ? (A->split ? -A->split : A->vec) : (A->split32 ? -A->split32 : A->vec32);
   return BAMG_OK;
 }
 

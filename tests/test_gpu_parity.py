@@ -465,6 +465,17 @@ def test_lane_choice_invariance(br, bc):
             assert rel(y32.double().cpu().numpy(), yref) <= 1e-5, lanes
         lanes, ms = B.bamg_bsr_autotune(ctx, A)
         assert lanes in choices and ms > 0
+        assert B.bamg_bsr_get_lanes_prec(A, B.BAMG_FP64) == lanes
+        assert B.bamg_bsr_get_lanes_prec(A, B.BAMG_FP32) in choices
+        # one copy at a time: the FP32 choice moves, the FP64 one stays
+        other = next(c for c in choices if c != lanes)
+        B.bamg_bsr_set_lanes_prec(ctx, A, B.BAMG_FP32, other)
+        assert B.bamg_bsr_get_lanes_prec(A, B.BAMG_FP32) == other and B.bamg_bsr_get_lanes(A) == lanes
+        y32 = torch.zeros(nbr * br, dtype=torch.float32, device="cuda")
+        B.bamg_bsr_spmv(ctx, A, torch.from_numpy(x).float().cuda(), y32, B.BAMG_FP32)
+        assert rel(y32.double().cpu().numpy(), yref) <= 1e-5
+        with pytest.raises(B.BamgError):
+            B.bamg_bsr_set_lanes_prec(ctx, A, 2, 1)
         with pytest.raises(B.BamgError):
             B.bamg_bsr_set_lanes(ctx, A, 3)
         if (br, bc) != (6, 3):
