@@ -29,3 +29,43 @@ def test_step_bytes_count_one_vcycle_per_iteration():
     t21, p21, _ = bench.step_bytes(lv, 1000, 21, False)
     assert p20["vcycles"] == 20 * vc
     assert t21 - t20 == vc + (p21["cg"] - p20["cg"])
+
+
+class _FakeLanes:
+    """Stand-in for the binding's hierarchy accessors and per-copy lanes."""
+    BAMG_FP64, BAMG_FP32 = 0, 1
+
+    def __init__(self, levels):
+        self.levels = levels       # list of (A, P, R) names, P and R None on the coarsest
+        self.lanes = {}
+
+    def bamg_mg_num_levels(self, mg):
+        return len(self.levels)
+
+    def bamg_mg_get_level(self, mg, l):
+        return self.levels[l][0], self.levels[l][1]
+
+    def bamg_mg_get_restriction(self, mg, l):
+        return self.levels[l][2]
+
+    def bamg_bsr_get_lanes_prec(self, M, p):
+        return self.lanes.get((M, p), 1)
+
+    def bamg_bsr_set_lanes_prec(self, ctx, M, p, v):
+        self.lanes[(M, p)] = v
+
+
+def test_tune_cache_keeps_both_copies(tmp_path):
+    """The tune cache saves every level matrix's FP64 and FP32 lanes and puts
+    them back, copy by copy."""
+    levels = [("A0", "P0", "R0"), ("A1", "P1", "R1"), ("A2", None, None)]
+    src = _FakeLanes(levels)
+    src.lanes = {("R0", 0): -4, ("R0", 1): -288, ("A1", 0): 16, ("A1", 1): -4, ("P0", 0): 2}
+    path = str(tmp_path / "tune.json")
+    bench.apply_tune_cache(src, None, None, path)          # no file yet: saves
+    dst = _FakeLanes(levels)
+    bench.apply_tune_cache(dst, None, None, path)          # file present: restores
+    for M in ("A0", "P0", "R0", "A1", "P1", "R1", "A2"):
+        for p in (0, 1):
+            assert dst.lanes[(M, p)] == src.bamg_bsr_get_lanes_prec(M, p)
+    assert dst.lanes[("R0", 1)] == -288 and dst.lanes[("R0", 0)] == -4
