@@ -907,6 +907,8 @@ static void cg_graphs_release(bamg_mg* mg) {
   for (auto g : mg->cg_graphs)
     if (g) cudaGraphExecDestroy(g);
   mg->cg_graphs.clear();
+  if (mg->cg_loop) cudaGraphExecDestroy(mg->cg_loop);
+  mg->cg_loop = nullptr;
   for (auto& v : mg->cg_pairs)
     for (auto& q : v) {
       cudaEventDestroy(q.a);
@@ -918,15 +920,99 @@ static void cg_graphs_release(bamg_mg* mg) {
 
 constexpr int kCgChunk = 4;  // iterations launched between convergence checks
 
+// Condition of the device CG loop, set after the prologue (reset = 1) and at
+// the end of every iteration: run another iteration while the solve is
+// still going and fewer than maxit iterations have run (a bound that holds
+// whatever the state says).
+__global__ void k_cg_continue(CgState* s, int reset, cudaGraphConditionalHandle h) {
+  const int l = reset ? 0 : s->loops + 1;
+  s->loops = l;
+  cudaGraphSetConditional(h, (!s->done && l < s->maxit) ? 1u : 0u);
+}
+
+static uint64_t graph_kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  uint64_t kn = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  return kn;
+}
+
+// The unprofiled solve's iterations as one graph: the loop decision, then a
+// while node whose body is one CG iteration and the next decision.
+static Status cg_loop_graph(bamg_mg* mg, double* r, double* z, cudaStream_t cs) {
+  const auto mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t G = nullptr;
+  BAMG_CUDA(cudaGraphCreate(&G, 0));
+  Status s;
+  auto run = [&]() -> Status {
+    cudaGraphConditionalHandle h;
+    BAMG_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault));
+    BAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, mode));
+    k_cg_continue<<<1, 1, 0, cs>>>(mg->cg, 1, h);
+    cudaError_t e = cudaGetLastError();
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+    std::vector<cudaGraphNode_t> last(deps, deps + nd);
+    cudaGraph_t out = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &out);
+    if (e != cudaSuccess) return cuda_status(e, "CG loop decision");
+    if (ee != cudaSuccess) return cuda_status(ee, "CG loop capture");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond = nullptr;
+    BAMG_CUDA(cudaGraphAddNode(&cond, G, last.data(), nullptr, last.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BAMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode));
+    Status is = cg_iteration(mg, r, z, cs);
+    if (is.ok()) {
+      k_cg_continue<<<1, 1, 0, cs>>>(mg->cg, 0, h);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) is = cuda_status(e, "CG loop decision");
+    }
+    const cudaError_t be = cudaStreamEndCapture(cs, &out);
+    BAMG_TRY(is);
+    if (be != cudaSuccess) return cuda_status(be, "CG loop body capture");
+    mg->cg_loop_body_kernels = graph_kernel_nodes(body);
+    BAMG_CUDA(cudaGraphInstantiate(&mg->cg_loop, G, 0));
+    return Status{};
+  };
+  g_capturing = true;
+  s = run();
+  g_capturing = false;
+  cudaGraphDestroy(G);
+  if (!s.ok()) {
+    if (mg->cg_loop) cudaGraphExecDestroy(mg->cg_loop);
+    mg->cg_loop = nullptr;
+  }
+  return s;
+}
+
 // Capture one CG iteration into a graph; with profiling on, one graph per
 // position in a chunk so that each owns its timing events.
 static Status cg_graph(bamg_mg* mg, double* r, double* z) {
   bamg_ctx* ctx = mg->ctx;
-  if (!mg->cg_graphs.empty() && mg->cg_graph_epoch == ctx->prof.epoch) return Status{};
+  if ((!mg->cg_graphs.empty() || mg->cg_loop) && mg->cg_graph_epoch == ctx->prof.epoch) return Status{};
   cg_graphs_release(mg);
   const int ng = ctx->prof.on ? kCgChunk : 1;
   cudaStream_t cs = nullptr;
   BAMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  if (!ctx->prof.on) {
+    const Status ls = cg_loop_graph(mg, r, z, cs);
+    cudaStreamDestroy(cs);
+    mg->cg_graph_epoch = ctx->prof.epoch;
+    return ls;
+  }
   mg->cg_pairs.resize(ng);
   mg->cg_pairs_used.assign(ng, 0);
   if (ctx->prof.on)
@@ -1023,12 +1109,16 @@ static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int
   CgState* s = mg->cg;
   BAMG_TRY(cg_graph(mg, cg_r(mg), cg_z(mg)));
   BAMG_TRY(cg_prologue(mg, b, rtol, maxit, st));
-  BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-  BAMG_CUDA(cudaStreamSynchronize(st));
+  const bool device_loop = mg->cg_loop != nullptr;
+  if (device_loop) BAMG_CUDA(cudaGraphLaunch(mg->cg_loop, st));
+  if (!device_loop) {
+    BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    BAMG_CUDA(cudaStreamSynchronize(st));
+  }
   int launched = 0;
-  int its_before = mg->cg_host->its;
+  int its_before = device_loop ? 0 : mg->cg_host->its;
   const int ng = (int)mg->cg_graphs.size();
-  while (launched < maxit && !mg->cg_host->done) {
+  while (!device_loop && launched < maxit && !mg->cg_host->done) {
     const int c = std::min(kCgChunk, maxit - launched);
     for (int k = 0; k < c; ++k) {
       BAMG_CUDA(cudaGraphLaunch(mg->cg_graphs[k % ng], st));
@@ -1052,6 +1142,8 @@ static Status cg_solve(bamg_mg* mg, const double* b, double* x, double rtol, int
   BAMG_CUDA(cudaMemcpyAsync(mg->cg_host, s, sizeof(CgState), cudaMemcpyDeviceToHost, st));
   BAMG_TRY(check_device_error(ctx));
   const CgState& h = *mg->cg_host;
+  if (device_loop)  // the loop's decisions and its bodies' kernels
+    g_launches.fetch_add(1 + (uint64_t)h.loops * mg->cg_loop_body_kernels, std::memory_order_relaxed);
   if (info) {
     info->iterations = h.its;
     info->converged = h.converged;

@@ -240,7 +240,7 @@ struct Level {
 
 struct CgState {
   double bnorm2, rtol2, rz, pq, alpha, beta, rnorm2, pad;
-  int its, maxit, done, converged, breakdown, pad2[3];
+  int its, maxit, done, converged, breakdown, loops, pad2[2];  // loops: bodies run by the device loop
 };
 
 // Many right-hand sides at once: at most kMaxRhs vectors, stored RHS-minor
@@ -297,6 +297,10 @@ struct bamg_mg {
   std::vector<size_t> cg_pairs_used;
   uint64_t cg_graph_epoch = ~0ull;
   uint64_t cg_graph_kernels = 0;
+  // unprofiled solves: one graph whose while node runs the iterations on the
+  // device (no host round trip until the solve ends)
+  cudaGraphExec_t cg_loop = nullptr;
+  uint64_t cg_loop_body_kernels = 0;
   double* power_w[2] = {nullptr, nullptr};
   bamg::MultiWork* multi = nullptr;  // multi-right-hand-side work area
   // second stream of the reuse update: the coarsest factorisation runs on it,
