@@ -748,7 +748,7 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
     copy_stream = torch.cuda.Stream()
     ready = [torch.cuda.Event(), torch.cuda.Event()]
     main = torch.cuda.current_stream()
-    state = {"n": 0, "spans": []}
+    state = {"n": 0, "spans": [], "waits": [], "host_s": 0.0}
 
     def fetch(k):
         src, dst = host_in[k % n_host].view(-1), dev_in[k % 2].view(-1)
@@ -763,13 +763,19 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
         state["spans"].append((e0, e1))
 
     def run(k, last):
+        t0 = time.perf_counter()
         if k == 0 or state["n"] == 0:
             fetch(k)
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(main)
         main.wait_event(ready[k % 2])
+        w1.record(main)
+        state["waits"].append((w0, w1))
         B.bamg_bsr_coo_set_values(wl.ctx, wl.A, dev_in[k % 2], 0)
         if not last:
             copy_stream.wait_stream(main)   # the other buffers' last readers were the previous step
             fetch(k + 1)
+        state["host_s"] += time.perf_counter() - t0
         B.bamg_mg_update(wl.ctx, wl.mg)
         out = B.bamg_cg_solve(wl.ctx, wl.mg, dev_b[k % 2], wl.x, RTOL, MAXIT)
         host_x.copy_(wl.x, non_blocking=True)
@@ -783,10 +789,11 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
         state["n"] = 0
         run(k, True)
     state["n"] = 0
-    state["spans"] = []
+    state["spans"], state["waits"], state["host_s"] = [], [], 0.0
     ms, outs = timed(torch, dist, step, K)
     ms_step = slowest_rank_ms(torch, dist, ms / K)
     copy_ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in state["spans"]]))
+    wait_ms = [w0.elapsed_time(w1) for w0, w1 in state["waits"]]
     its = [o["iterations"] for o in outs]
     bytes_step = float(np.mean([step_bytes(wl.levels, wl.n_coo, i, wl.mixed)[0] for i in its]))
     h2d = int(host_in[0].numel() * 8 + host_b.numel() * 8)
@@ -795,6 +802,12 @@ def e2e(wl, torch, B, dist, K, W, world, per_step):
             "h2d_bytes_per_step": h2d,
             "h2d_ms_per_step": round(copy_ms, 3),
             "h2d_gbs": round(h2d / copy_ms / 1e6, 1),
+            # where an end-to-end step loses time against the device step: the
+            # main stream waiting for the step's inputs (the first step's copy
+            # is never overlapped), and the host enqueueing the copies
+            "copy_wait_ms": {"first_step": round(wait_ms[0], 3),
+                             "later_steps_mean": round(float(np.mean(wait_ms[1:])), 3) if K > 1 else None},
+            "host_enqueue_ms_per_step": round(state["host_s"] * 1e3 / K, 3),
             "overlap": "next step's value stream and b copied on a second stream during the current step",
             "d2h_bytes_per_step": int(host_x.numel() * 8)}
 
