@@ -217,7 +217,8 @@ BAMG_API bamg_status bamg_bsr_spmm(bamg_bsr* A, const void* X, void* Y, int k, b
  * output component over every VB-th block of its lane's row, so that each
  * block's column index and gathered x are loaded once per lane; 0 in
  * _set_lanes means -4.  _autotune times the product for every choice from a
- * flushed L2 on the context's stream and keeps the fastest, for the FP64
+ * flushed L2 on the context's stream and keeps the fastest (a choice must
+ * beat the best one before it by 3%, against timing noise), for the FP64
  * values and, when present, the FP32 copy (allocates work vectors; returns
  * the FP64 choice and its time in ms, either may be NULL).  Results do not
  * depend on the choice beyond summation order.  _set_lanes applies to both
