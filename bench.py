@@ -45,12 +45,15 @@ METRIC = "PtAP+V-cycle HBM GB/s; CG time to rtol 1e-8, FP64 vs mixed/learned"
 FP64_PEAK_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 RTOL = 1e-8
 MAXIT = 500
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (profiles/traffic_cheb_step_l0_64cubed_fp64.md), with a fingerprint of the
-# kernel's source at capture time; reported as null once it changes.  The
-# source is device.cuh (the row products) and the span of cycle.cu from the
-# block-diagonal apply through the end of the fused Chebyshev step.
-TRAFFIC = {("cheb_step_l0", 64, False): (589.9e6, "f5d61c966d397dd7")}
+# DRAM bytes per launch of the dominant kernel from one ncu capture each
+# (profiles/traffic_cheb_step_l0_64cubed_fp64.md, _mixed.md): the mean of the
+# two pre-smoothing steps, the launches the timed steps sample.  Each carries
+# a fingerprint of the kernel's source at capture time and is reported as
+# null once it changes.  The source is device.cuh (the row products) and the
+# span of cycle.cu from the block-diagonal apply through the end of the fused
+# Chebyshev step.
+TRAFFIC = {("cheb_step_l0", 64, False): (587.2e6, "f5d61c966d397dd7"),
+           ("cheb_step_l0", 64, True): (307.6e6, "f5d61c966d397dd7")}
 TRAFFIC_SOURCES = (("paper_2606_24748_gb300/csrc/device.cuh", None, None),
                    ("paper_2606_24748_gb300/csrc/cycle.cu", "__device__ __forceinline__ void dinv_apply",
                     "// r = b - A x; d = w Dinv r / theta"))
