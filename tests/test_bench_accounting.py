@@ -69,3 +69,30 @@ def test_tune_cache_keeps_both_copies(tmp_path):
         for p in (0, 1):
             assert dst.lanes[(M, p)] == src.bamg_bsr_get_lanes_prec(M, p)
     assert dst.lanes[("R0", 1)] == -288 and dst.lanes[("R0", 0)] == -4
+
+
+class _FakeWorkload:
+    def __init__(self, mixed):
+        import types
+        self.mixed = mixed
+        self.mesh = types.SimpleNamespace(ne=64)
+        self.levels = [{"A": {"nbr": 274625, "nnzb": 7189057}, "P": None}, {"A": {"nbr": 9261, "nnzb": 226981}}]
+
+
+def test_roofline_takes_the_sampled_slot_and_the_form_s_traffic():
+    """The roofline times the sampled pre-smoothing pair when that slot ran,
+    books the mean bytes of those two steps, and reports the DRAM traffic
+    recorded for the same form."""
+    from paper_2606_24748_gb300 import bytes_model as bm
+    nnzb, n = 7189057, 274625
+    alu = {"fp64_peak_tflops": bench.FP64_PEAK_DERIVED_TFLOPS, "fp64_probe_tflops": None}
+    for mixed in (False, True):
+        prof = {k: (0.0, 0) for k in ("cheb_step_l0", "ptap_stage1_l0", "ptap_stage2_l0", "cg_ap")}
+        prof["cheb_pre_l0"] = (46 * 0.1, 46)
+        r = bench.roofline(_FakeWorkload(mixed), prof, None, alu)
+        s = 4 if mixed else 8
+        want = (bm.cheb_step_bytes(nnzb, n, 3, s, True) + bm.cheb_step_bytes(nnzb, n, 3, s, False)) / 2
+        assert r["kernel"] == "cheb_step_l0" and r["launches"] == 46
+        assert r["bytes_per_launch"] == int(want)
+        assert r["traffic"] == int(bench.TRAFFIC[("cheb_step_l0", 64, mixed)][0])
+        assert r["bound"] == ("hbm" if mixed else "alu")
